@@ -1,0 +1,99 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that a pin catches each.
+
+Each mutation is applied with monkeypatch to a copy of one oracle function; the
+corresponding pin from the other oracle tests must then fail.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import dirac, force, evenodd
+import test_oracle_operator as t_op
+import test_oracle_clover as t_cl
+import test_oracle_force as t_fo
+
+
+def _fails(fn, *args):
+    try:
+        fn(*args)
+    except AssertionError:
+        return True
+    return False
+
+
+def test_backward_hop_without_dagger_is_caught(monkeypatch):
+    orig_dagger = dirac.dagger
+
+    def hopping_nodag(U, psi, t_bc):
+        dims = psi.shape[3], psi.shape[2], psi.shape[1], psi.shape[0]
+        s = dirac.boundary_sign(dims, t_bc)
+        out = np.zeros_like(psi, dtype=complex)
+        for mu in range(4):
+            Umu = U[..., mu, :, :] * s[..., mu, None, None]
+            out += dirac.spin_mul(dirac.ONE4 - dirac.GAMMA[mu], dirac.colour_mul(Umu, dirac.shift(psi, mu, 1)))
+            out += dirac.spin_mul(dirac.ONE4 + dirac.GAMMA[mu],
+                                  dirac.colour_mul(dirac.shift(Umu, mu, -1), dirac.shift(psi, mu, -1)))
+        return out
+    monkeypatch.setattr(dirac, "hopping", hopping_nodag)
+    assert _fails(t_op.test_gamma5_hermiticity_and_adjoint, (4, 2, 6, 4), 1)
+    assert orig_dagger is dirac.dagger
+
+
+def test_wrong_projector_sign_is_caught(monkeypatch):
+    orig = dirac.hopping
+
+    def hopping_swapped(U, psi, t_bc):
+        # (1 + g) forward and (1 - g) backward
+        g5 = dirac.GAMMA.copy()
+        monkeypatch.setattr(dirac, "GAMMA", -g5)
+        try:
+            return orig(U, psi, t_bc)
+        finally:
+            monkeypatch.setattr(dirac, "GAMMA", g5)
+    monkeypatch.setattr(dirac, "hopping", hopping_swapped)
+    assert _fails(t_op.test_free_field_plane_wave, (4, 6, 2, 8))
+
+
+def test_field_strength_normalisation_is_caught(monkeypatch):
+    orig = dirac.field_strength
+    monkeypatch.setattr(dirac, "field_strength", lambda U, mu, nu: 2.0 * orig(U, mu, nu))
+    assert _fails(t_cl.test_uniform_abelian_flux_closed_form)
+
+
+def test_misplaced_leaf_is_caught(monkeypatch):
+    orig = dirac.leaf_paths
+
+    def leaves_wrong(mu, nu):
+        p = orig(mu, nu)
+        # replace the third leaf by a copy of the first: the sum of four leaves is wrong
+        return [p[0], p[1], p[0], p[3]]
+    monkeypatch.setattr(dirac, "leaf_paths", leaves_wrong)
+    assert _fails(t_cl.test_random_abelian_field_strength_from_plaquette_angles)
+
+
+def test_missing_kappa2_on_odd_clover_force_is_caught(monkeypatch):
+    orig = force.solution_fields
+
+    def fields_wrong(op, X_e):
+        X, Y, W = orig(op, X_e)
+        return X, Y, Y  # W should carry kappa^2 on the odd sites
+    monkeypatch.setattr(force, "solution_fields", fields_wrong)
+    assert _fails(t_fo.test_force_against_finite_differences, 1.0)
+
+
+def test_transposed_insertion_is_caught(monkeypatch):
+    orig = force.insert
+
+    def insert_transposed(G, U, path, C):
+        orig(G, U, path, np.swapaxes(C, -1, -2))
+    monkeypatch.setattr(force, "insert", insert_transposed)
+    assert _fails(t_fo.test_force_against_finite_differences, 0.0)
+
+
+def test_schur_sign_is_caught(monkeypatch):
+    def mhat_plus(self, x_e):
+        t_o = self.site(self.A_oo_inv, self.D_oe(x_e))
+        return self.site(self.A_ee, x_e) + self.kappa ** 2 * self.D_eo(t_o)
+    monkeypatch.setattr(evenodd.SchurOperator, "Mhat", mhat_plus)
+    import test_oracle_solve as t_so
+    assert _fails(t_so.test_schur_complement_matches_dense_full_solve, (2, 2, 2, 2), 0.5, 1)
