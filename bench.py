@@ -1,0 +1,397 @@
+"""Benchmark of the clover-Wilson hot path on GB300.
+
+One step = one pass of the whole hot path over one synthetic lattice of the
+paper's 16^4 size (kappa 0.12, c_sw 1.0, eps 0.2, seed 2, 1 RHS):
+  1. qcd_load_gauge  -- pack the canonical links (device) into the SoA copies
+  2. qcd_clover_build -- clover term and its FP64 6x6 inverse
+  3. qcd_cg_solve     -- mixed FP32/FP64-reliable CG on Mhat^dag Mhat to a true
+                         FP64 relative residual 1e-8
+  4. qcd_fermion_force -- dS/dU from that solution (clover derivative included)
+value = device time per step (CUDA events on the library's stream, L2 flushed
+between steps).  The JSON line also carries the plain FP64 GPU solve time, the
+Dslash GFLOPS / GB/s of the kernels inside the solve, the roofline of the
+dominant kernel, an end-to-end number with host buffers, and the FP64 numpy
+oracle timed on a bounded sample on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank solves its own replica of the workload (the
+path has no exchange step on one lattice per GPU); value = N lattices / the
+slowest rank's time.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GFLOPS & HBM GB/s; time to 1e-8 CG solve, mixed vs FP64, 1 GB300"
+WORKLOAD = "c1_16^4"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_params(name):
+    from paper_0910_0262_gb300 import synth
+    w = dict(synth.WORKLOADS[name])
+    w["kappa"], w["csw"], w["t_bc"] = synth.KAPPA, synth.CSW, synth.T_BC
+    return w
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def max_over_ranks(x, device=None):
+    """Largest value of x over all ranks (the slowest replica sets the job's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_seed(seed, rank):
+    """Each rank solves its own lattice: same recipe, seed offset by the rank."""
+    return seed + 1000 * rank
+
+
+# ------------------------------------------------------------------- ours --
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+    from paper_0910_0262_gb300 import synth, build
+    from paper_0910_0262_gb300 import qcd as Q
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload_params(args.workload)
+    dims = w["dims"]
+    U_np, b_np = synth.make_problem(dims, w["eps"], replica_seed(w["seed"], rank), w["nrhs"])
+    U = torch.from_numpy(U_np).to(dev)
+    b = torch.from_numpy(b_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    op = Q.CloverWilson(dims, w["t_bc"], stream=stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+    X, Y, Z, T = dims
+    F = torch.empty((T, Z, Y, X, 4, 3, 3), dtype=torch.complex128, device=dev)
+    x = torch.zeros_like(b)
+    mixed = dict(tol=1e-8, inner_prec=32, reliable_every=50, reliable_delta=0.1, max_iter=20000)
+    prm = Q.solver_params(**mixed)
+    nrhs = w["nrhs"]
+    stats = (Q.SolverStats * nrhs)()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        Q.qcd_load_gauge(op.ctx, Q._ptr(U), 1, Q.QCD_GAUGE_RECON12)
+        if ev:
+            ev[1].record(stream)
+        Q.qcd_clover_build(op.ctx, w["kappa"], w["csw"])
+        if ev:
+            ev[2].record(stream)
+        s = Q.qcd_cg_solve(op.ctx, Q._ptr(x), Q._ptr(b), nrhs, prm, stats)
+        if s != Q.QCD_OK:
+            raise RuntimeError("mixed solve did not converge")
+        if ev:
+            ev[3].record(stream)
+        Q.qcd_fermion_force(op.ctx, Q._ptr(F), Q._ptr(x), nrhs, Q.QCD_FORCE_INPUT_IS_SOLUTION, None, None)
+        if ev:
+            ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    Q.qcd_profile(op.ctx, 1)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - t0
+    prof = Q.qcd_profile_read(op.ctx)
+    Q.qcd_profile(op.ctx, 0)
+    clocks = sampler.stop()
+    parts = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs])  # ms
+    step_ms = parts.sum(axis=1)
+    ms_per_step = float(np.mean(step_ms))
+    iters = stats[0].iters
+    resid = max(stats[r].true_rel_resid for r in range(nrhs))
+
+    if world > 1:
+        ms_per_step = max_over_ranks(ms_per_step, dev)
+
+    # plain FP64 GPU solve on the same lattice, for the mixed-vs-FP64 comparison
+    fp64 = Q.solver_params(tol=1e-8, inner_prec=64, max_iter=20000)
+    st64 = (Q.SolverStats * nrhs)()
+    Q.qcd_profile(op.ctx, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times64 = []
+    for _ in range(max(2, min(args.steps, 3))):
+        flush.zero_()
+        e0.record(stream)
+        Q.qcd_cg_solve(op.ctx, Q._ptr(x), Q._ptr(b), nrhs, fp64, st64)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        times64.append(e0.elapsed_time(e1))
+    prof64 = Q.qcd_profile_read(op.ctx)
+    Q.qcd_profile(op.ctx, 0)
+
+    result = dict(metric=METRIC, value=ms_per_step * 1.0, unit="ms per hot-path step (16^4, solve to 1e-8)")
+    solve_mixed = float(np.mean(parts[:, 2]))
+    solve64 = float(np.mean(times64))
+
+    def kstats(prof_list, prefix):
+        rows = [p for p in prof_list if p["name"].startswith(prefix)]
+        ms = sum(p["total_ms"] for p in rows)
+        n = sum(p["launches"] for p in rows)
+        by = sum(p["bytes"] for p in rows)
+        fl = sum(p["flops"] for p in rows)
+        return dict(launches=n, avg_us=1e3 * ms / max(n, 1), gbs=by / (ms * 1e-3) / 1e9 if ms else 0.0,
+                    gflops=fl / (ms * 1e-3) / 1e9 if ms else 0.0, bytes_per_launch=by / max(n, 1))
+
+    d32 = kstats(prof, "dslash_p32")
+    d64 = kstats(prof64, "dslash_p64")
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    total_launches = next((p["launches"] for p in prof if p["name"] == "launches_total"), None)
+    result.update({
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 reliable",
+        "data": "synthetic (seeded near-unit SU(3) links, Gaussian source)",
+        "config": {"workload": args.workload, "dims": list(dims), "nrhs": nrhs, "kappa": w["kappa"],
+                   "csw": w["csw"], "eps": w["eps"], "seed": w["seed"], "tol": 1e-8,
+                   "inner": "fp32, 12-real links, reliable update every 50 its or 0.1 drop",
+                   "l2": "flushed (256 MiB write) before every step, outside the step's events",
+                   "parallelism": f"replicas x{world}"},
+        "parts_ms": {"load_gauge": float(np.mean(parts[:, 0])), "clover_build": float(np.mean(parts[:, 1])),
+                     "cg_solve_mixed": solve_mixed, "fermion_force": float(np.mean(parts[:, 3]))},
+        "solve": {"mixed_ms": solve_mixed, "fp64_ms": solve64, "speedup_mixed_vs_fp64": solve64 / solve_mixed,
+                  "mixed_iters": iters, "fp64_iters": st64[0].iters, "reliable_updates": stats[0].reliable_updates,
+                  "true_rel_resid_mixed": resid, "true_rel_resid_fp64": st64[0].true_rel_resid},
+        "dslash": {"fp32_in_solve": d32, "fp64_in_solve": d64},
+        "gpu_launches": total_launches,
+        "clocks": clocks,
+        "wall_s_timed_region": wall,
+    })
+    # roofline of the dominant kernel: the FP32 hopping kernels inside the solve
+    result["roofline"] = {"kernel": "dslash_kernel<32,12,*> (FP32 hopping + fused clover epilogue)",
+                          "bound": "hbm", "achieved": d32["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                          "frac": d32["gbs"] / hbm_peak, "traffic": None,
+                          "note": "16^4 working set is L2-resident inside a solve; see profiles/"}
+    if not args.no_e2e:
+        result["e2e"] = run_e2e(op, U_np, b_np, w, stream, dev)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(w, iters)
+    op.close()
+    return result
+
+
+def run_e2e(op, U_np, b_np, w, stream, dev):
+    """The same step through the public API from pinned host buffers: links and source copied in,
+    solution and force read back, all inside the timed region."""
+    import torch
+    from paper_0910_0262_gb300 import qcd as Q
+    U_h = torch.from_numpy(U_np).pin_memory()
+    b_h = torch.from_numpy(b_np).pin_memory()
+    x_h = torch.empty_like(b_h).pin_memory()
+    X, Y, Z, T = w["dims"]
+    F_h = torch.empty((T, Z, Y, X, 4, 3, 3), dtype=torch.complex128).pin_memory()
+    kw = dict(tol=1e-8, inner_prec=32, reliable_every=50, reliable_delta=0.1, max_iter=20000)
+    times = []
+    for k in range(4):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        op.load_gauge(U_h, recon12=True)           # host pointer: the library copies it in
+        op.clover_build(w["kappa"], w["csw"])
+        b = b_h.to(dev, non_blocking=True)
+        x, st, ok = op.cg_solve(b, **kw)
+        F, _ = op.fermion_force(x, input_is_solution=True)
+        x_h.copy_(x)
+        F_h.copy_(F)
+        torch.cuda.synchronize(dev)
+        if k:
+            times.append((time.perf_counter() - t0) * 1e3)
+    return {"value": float(np.mean(times)), "unit": "ms per hot-path step (16^4, solve to 1e-8)",
+            "h2d_bytes_per_step": int(U_h.numel() * 16 + b_h.numel() * 16),
+            "d2h_bytes_per_step": int(x_h.numel() * 16 + F_h.numel() * 16)}
+
+
+# ------------------------------------------------------------ CPU oracle --
+def cpu_baseline(w, gpu_iters, cg_sample_iters=4):
+    """The numpy FP64 oracle on the host: clover term + inverse, cg_sample_iters CG iterations
+    (each one Mhat^dag Mhat plus BLAS) and the force, then scaled to a full step with the
+    iteration count of the GPU mixed solve."""
+    from paper_0910_0262_gb300 import synth
+    from oracle import evenodd, force as oforce
+    U, b = synth.make_problem(w["dims"], w["eps"], w["seed"], w["nrhs"])
+    t0 = time.perf_counter()
+    op = evenodd.SchurOperator(U, w["kappa"], w["csw"], w["t_bc"])
+    t_clover = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = b[0].copy()
+    p = r.copy()
+    xx = np.zeros_like(r)
+    rr = np.vdot(r, r).real
+    for _ in range(cg_sample_iters):
+        Ap = op.MdagM(p)
+        a = rr / np.vdot(p, Ap).real
+        xx += a * p
+        r -= a * Ap
+        rn = np.vdot(r, r).real
+        p = r + (rn / rr) * p
+        rr = rn
+    t_it = (time.perf_counter() - t0) / cg_sample_iters
+    t0 = time.perf_counter()
+    oforce.lie_force(U, oforce.gradient(op, xx))
+    t_force = time.perf_counter() - t0
+    est = t_clover + t_it * gpu_iters + t_force
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return {"value": est * 1e3, "unit": "ms per hot-path step (16^4, solve to 1e-8)", "cores": 1,
+            "cores_available": cores, "kind": "oracle",
+            "sample": f"clover+inverse once, {cg_sample_iters} CG iterations ({t_it:.2f} s each, scaled to the "
+                      f"{gpu_iters} iterations of the solve), force once; numpy FP64, one thread"}
+
+
+# -------------------------------------------------------------- reference --
+def run_reference(args, world, rank):
+    """The oracle arm: each step is a bounded sample of the same workload on the host cores."""
+    w = workload_params(args.workload)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(w, gpu_iters=WORKLOAD_ITERS, cg_sample_iters=1)
+        if k >= args.warmup:
+            vals.append(r["value"])
+    v = float(np.mean(vals))
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": r["unit"], "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "dims": list(w["dims"])},
+            "cpu_baseline": {"value": v, "unit": r["unit"], "cores": 1, "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# CG iterations the 16^4 mixed solve takes (used to scale the oracle's per-iteration sample in the
+# reference arm, which has no GPU solve to count them)
+WORKLOAD_ITERS = 300
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, world, rank)))
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    res = run_ours(args, world, rank, local)
+    if world > 1:
+        res["value"] = res["ms_per_step"]
+    if rank == 0:
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

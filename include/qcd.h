@@ -1,0 +1,191 @@
+/*
+ * qcd.h -- C ABI of libqcd: the even-odd preconditioned clover-Wilson Dirac
+ * operator, its CG solve and the fermion force, on one NVIDIA GB300 (sm_103a).
+ *
+ * Source of the method.  Shi, Kindratenko and Gottlieb, "Cell processor
+ * implementation of a MILC lattice QCD application", Sec. 1: the application is
+ * MILC 7.4's clover_dynamical -- dynamical clover-improved Wilson fermions in
+ * the hybrid-molecular-dynamics R algorithm (su3_rmd).  Its compute loops
+ * iterate over the 4-D lattice reading data at a site and at its neighbours
+ * (Sec. 3); the paper prints no formula, so the operator is the standard one:
+ *
+ *   (M psi)(x) = A(x) psi(x) - kappa sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu)
+ *                                           + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ]
+ *   A(x) = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x),  sigma = (i/2)[g_mu, g_nu]
+ *   F_{mu nu} = traceless part of (Q_{mu nu} - Q_{mu nu}^dag) / (8i), Q = sum of 4 leaves
+ *   Mhat = A_ee - kappa^2 D_eo A_oo^-1 D_oe   (even sites),  Mhat^dag = g5 Mhat g5
+ *
+ * DeGrand-Rossi gamma basis (g5 = diag(1,1,-1,-1)); directions mu = 0..3 are
+ * x, y, z, t; periodic in x, y, z; the time boundary factor t_bc multiplies
+ * U_t on the last time slice in the hopping term only.
+ *
+ * Canonical layouts (all complex numbers are interleaved (re, im) doubles):
+ *   gauge  U[t][z][y][x][mu][3][3]           complex128, V*4*9 complex
+ *   spinor on even sites [nrhs][V/2][spin 4][colour 3], complex128
+ *          (even sites = (x+y+z+t) even, in increasing lexicographic index
+ *          x + X (y + Y (z + Z t)); odd-site fields likewise)
+ *   force  F[t][z][y][x][mu][3][3]           complex128
+ *
+ * Ownership and ordering.  Every pointer argument is owned by the caller and
+ * the library never frees it.  Unless stated otherwise pointers are device
+ * pointers on the device that was current at qcd_create.  All work is ordered
+ * on the CUDA stream given to qcd_create.  qcd_load_gauge, qcd_clover_build,
+ * qcd_cg_solve and qcd_fermion_force synchronise that stream before returning
+ * (they report device-side status); qcd_dslash returns after enqueueing.
+ *
+ * Errors.  Every call returns a qcd_status; on failure qcd_last_error() gives a
+ * message for the calling thread.  No C++ exception crosses the ABI.  Argument
+ * errors are detected on the host before any launch.
+ */
+#ifndef QCD_H
+#define QCD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qcd_ctx qcd_ctx;
+
+typedef enum {
+  QCD_OK = 0,
+  QCD_ERR_ARG = 1,           /* bad argument (null pointer, odd extent, unknown op, ...) */
+  QCD_ERR_CUDA = 2,          /* a CUDA runtime call failed */
+  QCD_ERR_NOMEM = 3,         /* device allocation failed */
+  QCD_ERR_STATE = 4,         /* call out of order (no gauge field, no clover term) */
+  QCD_ERR_NOT_POSDEF = 5,    /* a clover block is not positive definite */
+  QCD_ERR_NOT_CONVERGED = 6, /* CG hit max_iter; best x and stats are still written */
+  QCD_ERR_NAN = 7,           /* non-finite input or a non-finite reduction */
+  QCD_ERR_TIMEOUT = 8        /* reserved: a bounded device-side wait gave up */
+} qcd_status;
+
+/* qcd_load_gauge flags */
+#define QCD_GAUGE_RECON12 1 /* store the FP32/FP16 link copies as rows 0,1 only (needs SU(3) links) */
+
+/* qcd_dslash ops (precision = compute/storage precision of the operation) */
+#define QCD_OP_DSLASH_EO 0  /* out_e = D_eo in_o   (dagger: out_e = (D_oe)^dag in_o) */
+#define QCD_OP_DSLASH_OE 1  /* out_o = D_oe in_e   (dagger: out_o = (D_eo)^dag in_e) */
+#define QCD_OP_MHAT 2       /* out_e = Mhat in_e   (dagger: Mhat^dag) */
+#define QCD_OP_MDAGM 3      /* out_e = Mhat^dag Mhat in_e */
+#define QCD_OP_CLOVER 4     /* out_e = A_ee in_e */
+#define QCD_OP_CLOVER_INV 5 /* out_o = A_oo^-1 in_o */
+
+/* precisions */
+#define QCD_PREC_DOUBLE 64
+#define QCD_PREC_SINGLE 32
+#define QCD_PREC_HALF 16 /* FP16 spinors with one FP32 scale per site, FP32 arithmetic */
+
+typedef struct {
+  double tol;            /* target true relative residual |b - Mhat^dag Mhat x| / |b| (e.g. 1e-8) */
+  int max_iter;          /* cap on CG iterations per right-hand side */
+  int inner_prec;        /* 64: plain FP64 CG; 32 / 16: mixed precision with FP64 reliable updates */
+  int reliable_every;    /* mixed: reliable update at least every this many iterations (e.g. 50) */
+  double reliable_delta; /* mixed: reliable update once |r| < delta * |r at the last update| (e.g. 0.1) */
+  int use_x0;            /* 1: x holds the initial guess; 0: start from x = 0 */
+} qcd_solver_params;
+
+typedef struct {
+  int iters;              /* CG iterations */
+  int reliable_updates;   /* FP64 residual replacements (including the final check) */
+  double true_rel_resid;  /* |b - Mhat^dag Mhat x| / |b| recomputed in FP64 at exit */
+  double b_dot_x;         /* Re <b, x>: the action S = phi^dag (Mhat^dag Mhat)^-1 phi when b = phi */
+  double seconds;         /* wall time of the call (whole batch) */
+} qcd_solver_stats;
+
+/* qcd_fermion_force flags */
+#define QCD_FORCE_INPUT_IS_SOLUTION 1 /* phi_or_x holds X = (Mhat^dag Mhat)^-1 phi: no solve */
+#define QCD_FORCE_GRADIENT 2          /* write G = dS/dRe U + i dS/dIm U instead of the Lie-algebra force */
+
+/*
+ * Create a context for a lattice of extents dims = {X, Y, Z, T}; all must be
+ * even and >= 2 and V = XYZT must satisfy 8 V < 2^31.  t_bc is +1 (periodic) or
+ * -1 (antiperiodic) in time.  cuda_stream is a cudaStream_t (NULL: the legacy
+ * default stream).  The context owns its device buffers (packed links, clover
+ * term, solver work vectors), allocated on the device current at this call.
+ * Returns QCD_ERR_ARG for bad extents, QCD_ERR_CUDA if no device is usable.
+ */
+qcd_status qcd_create(qcd_ctx** ctx, const int dims[4], double t_bc, void* cuda_stream);
+
+/* Release every buffer the context owns.  NULL is accepted. */
+qcd_status qcd_destroy(qcd_ctx* ctx);
+
+/*
+ * Load gauge links U in the canonical layout (V*4*9 complex128).  on_device = 1:
+ * U is a device pointer; 0: a host pointer (copied).  Packs them into the
+ * per-parity structure-of-arrays copies in FP64, FP32 and FP16 (the paper pads
+ * MILC's su3_matrix for the Cell's DMA, Sec. 3; this layout needs no padding).
+ * flags: QCD_GAUGE_RECON12.  Invalidates a previously built clover term.
+ * Returns QCD_ERR_NAN if U holds a non-finite value.
+ */
+qcd_status qcd_load_gauge(qcd_ctx* ctx, const double* U, int on_device, int flags);
+
+/*
+ * Build the clover term A (both parities) from the loaded links and invert it
+ * on every site in FP64 (Cholesky of each 6x6 chiral block); keeps FP64 and FP32
+ * copies.  Returns QCD_ERR_STATE without links, QCD_ERR_NOT_POSDEF if a block
+ * is not positive definite.
+ */
+qcd_status qcd_clover_build(qcd_ctx* ctx, double kappa, double csw);
+
+/*
+ * Apply one operator (QCD_OP_*) to nrhs canonical fields (V/2 sites each):
+ * in and out are device complex128 arrays [nrhs][V/2][4][3] on the parities the
+ * op names; they must not overlap.  precision (64/32/16) selects the internal
+ * storage and arithmetic; the result is returned in FP64.  nrhs >= 1.
+ * Returns QCD_ERR_STATE if the op needs links/clover that are not loaded.
+ */
+qcd_status qcd_dslash(qcd_ctx* ctx, double* out, const double* in, int op, int dagger, int precision, int nrhs);
+
+/*
+ * Solve Mhat^dag Mhat x = b for nrhs right-hand sides (device complex128
+ * [nrhs][V/2][4][3]; x is read as the initial guess when params->use_x0).
+ * inner_prec 64 runs plain FP64 CG; 32 or 16 runs the inner iteration in that
+ * precision with FP64 reliable updates (x accumulated in FP64, the residual
+ * recomputed in FP64 every reliable_every iterations or when |r| falls by
+ * reliable_delta).  Every RHS stops when its true FP64 relative residual is
+ * <= tol.  stats (may be NULL) receives nrhs entries.
+ * Returns QCD_ERR_NOT_CONVERGED (x and stats written) at max_iter,
+ * QCD_ERR_NAN on a non-finite reduction, QCD_ERR_STATE without a clover term.
+ */
+qcd_status qcd_cg_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, const qcd_solver_params* params,
+                        qcd_solver_stats* stats);
+
+/*
+ * Fermion force of S = sum_i phi_i^dag (Mhat^dag Mhat)^-1 phi_i, summed over the
+ * nrhs pseudofermions.  phi_or_x: device complex128 [nrhs][V/2][4][3], either
+ * phi (a solve with params is run first; stats as in qcd_cg_solve, may be NULL)
+ * or, with QCD_FORCE_INPUT_IS_SOLUTION, the solutions X.  F: device complex128
+ * [t][z][y][x][mu][3][3]; by default the traceless anti-Hermitian force
+ * F_mu(x) = sum_a i T_a dS/d eps_a for U_mu(x) -> exp(i eps_a T_a) U_mu(x)
+ * (T_a = lambda_a/2), including the clover-term derivative; with
+ * QCD_FORCE_GRADIENT the Wirtinger gradient G = dS/dRe U + i dS/dIm U.
+ * Error behaviour as qcd_cg_solve.
+ */
+qcd_status qcd_fermion_force(qcd_ctx* ctx, double* F, const double* phi_or_x, int nrhs, int flags,
+                             const qcd_solver_params* params, qcd_solver_stats* stats);
+
+/*
+ * Per-kernel timing with CUDA events on the context's stream.  enable = 1 resets
+ * the counters and starts recording an event pair around every launch of the
+ * tracked kernels (hopping kernels by epilogue, BLAS updates); 0 stops.
+ */
+qcd_status qcd_profile(qcd_ctx* ctx, int enable);
+
+typedef struct {
+  char name[40];         /* kernel class */
+  int launches;
+  double total_ms;       /* sum of event-measured durations */
+  double bytes;          /* algorithmic bytes summed over the launches */
+  double flops;          /* conventional flops summed over the launches */
+} qcd_kernel_stat;
+
+/* Copy up to max_entries kernel classes into out (synchronises the stream). */
+qcd_status qcd_profile_read(qcd_ctx* ctx, qcd_kernel_stat* out, int max_entries, int* n_entries);
+
+/* Message describing the last failed call on this thread ("" if none). */
+const char* qcd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCD_H */

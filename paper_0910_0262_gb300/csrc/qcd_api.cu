@@ -1,0 +1,836 @@
+// C ABI of libqcd (declared in include/qcd.h): context, workspace, operator
+// application and the CG driver.
+//
+// The paper's runtime wraps every compute loop in a PPE-side function that
+// fills a task structure, signals the SPEs and waits for completion (Sec. 3).
+// Here a call enqueues kernels on one CUDA stream; the CG iteration keeps its
+// scalars in device memory (alpha, beta, |r|^2 are produced by the reducing
+// kernels themselves), so the host only looks at the solver state once per
+// chunk of iterations and when a reliable update is due.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qcd.h"
+#include "qcd_dslash.cuh"
+#include "qcd_kernels.h"
+#include "qcd_force.h"
+
+using namespace qcd;
+
+namespace {
+
+thread_local std::string g_err;
+
+qcd_status fail(qcd_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CUDA_TRY(call)                                                                        \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(QCD_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+enum Slot {
+  S_IN, S_OUT, S_T, S_Y, S_IN_N, S_OUT_N, S_T_N, S_Y_N,   // qcd_dslash
+  S_CANON,                                               // canonical staging
+  S_B_HI, S_X_HI, S_AP_HI, S_T_HI, S_Y_HI,               // FP64 solver fields
+  S_X_LO, S_R_LO, S_P, S_AP, S_TL, S_YL,                 // inner solver fields
+  S_X_LO_N, S_R_LO_N, S_P_N, S_AP_N, S_TL_N, S_YL_N,
+  S_F_X, S_F_Y, S_F_CL,                                  // force work fields
+  S_COUNT
+};
+
+struct Buf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct ProfClass {
+  std::string name;
+  int launches = 0;
+  double ms = 0, bytes = 0, flops = 0;
+};
+struct ProfPending {
+  cudaEvent_t a, b;
+  int cls;
+  double bytes, flops;
+};
+
+}  // namespace
+
+struct qcd_ctx {
+  Geom g{};
+  cudaStream_t st = nullptr;
+  int device = 0;
+  // links
+  void* g64 = nullptr;
+  void* g32 = nullptr;
+  void* g16 = nullptr;
+  int recon = 18;
+  bool have_gauge = false;
+  // clover
+  void* A64 = nullptr;
+  void* Ainv64 = nullptr;
+  void* A32 = nullptr;
+  void* Ainv32 = nullptr;
+  bool have_clover = false;
+  double kappa = 0, csw = 0;
+  // device status words: [0] clover not positive definite, [1] non-finite input
+  int* flags = nullptr;
+  int* h_flags = nullptr;
+  // reductions and CG state
+  double* partials = nullptr;
+  unsigned* counter = nullptr;
+  double* results = nullptr;
+  CGState* cg = nullptr;
+  CGControl* ctl = nullptr;
+  CGState* h_cg = nullptr;
+  CGControl* h_ctl = nullptr;
+  double* h_results = nullptr;
+  int max_partials = 0;
+  Buf ws[S_COUNT];
+  // profiling
+  bool prof_on = false;
+  std::vector<ProfClass> prof;
+  std::vector<ProfPending> pending;
+  std::vector<cudaEvent_t> ev_free;
+};
+
+namespace {
+
+const int MAX_RHS = 8;
+
+size_t spinor_bytes(const Geom& g, int prec, int nrhs) {
+  const size_t per = prec == 64 ? 192 : (prec == 32 ? 96 : 48);
+  return per * (size_t)g.Vh * nrhs;
+}
+
+qcd_status ws_get(qcd_ctx* c, int slot, size_t bytes, void** out) {
+  Buf& b = c->ws[slot];
+  if (b.bytes < bytes) {
+    if (b.ptr) {
+      cudaStreamSynchronize(c->st);
+      cudaFree(b.ptr);
+      b.ptr = nullptr;
+      b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.ptr, bytes);
+    if (e != cudaSuccess) {
+      b.ptr = nullptr;
+      cudaGetLastError();
+      return fail(QCD_ERR_NOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    b.bytes = bytes;
+  }
+  *out = b.ptr;
+  return QCD_OK;
+}
+
+// --------------------------------------------------------------- profiling --
+int prof_class(qcd_ctx* c, const std::string& name) {
+  for (size_t i = 0; i < c->prof.size(); i++)
+    if (c->prof[i].name == name) return (int)i;
+  ProfClass pc;
+  pc.name = name;
+  c->prof.push_back(pc);
+  return (int)c->prof.size() - 1;
+}
+
+cudaEvent_t prof_event(qcd_ctx* c) {
+  if (!c->ev_free.empty()) {
+    cudaEvent_t e = c->ev_free.back();
+    c->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct ProfScope {
+  qcd_ctx* c;
+  cudaEvent_t a = nullptr;
+  int cls = -1;
+  double bytes, flops;
+  ProfScope(qcd_ctx* c_, const char* name, double bytes_, double flops_) : c(c_), bytes(bytes_), flops(flops_) {
+    if (!c->prof_on) return;
+    cls = prof_class(c, name);
+    a = prof_event(c);
+    cudaEventRecord(a, c->st);
+  }
+  ~ProfScope() {
+    if (!c->prof_on || cls < 0) return;
+    cudaEvent_t b = prof_event(c);
+    cudaEventRecord(b, c->st);
+    c->pending.push_back(ProfPending{a, b, cls, bytes, flops});
+  }
+};
+
+// collect finished event pairs (the caller has synchronised the stream)
+void prof_collect(qcd_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    ProfClass& pc = c->prof[p.cls];
+    pc.launches += 1;
+    pc.ms += ms;
+    pc.bytes += p.bytes;
+    pc.flops += p.flops;
+    c->ev_free.push_back(p.a);
+    c->ev_free.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
+// ------------------------------------------------------ operator helpers --
+int real_bytes(int prec) { return prec == 64 ? 8 : (prec == 32 ? 4 : 2); }
+
+void dslash_cost(const qcd_ctx* c, int prec, int epi, int nrhs, double* bytes, double* flops) {
+  const double Vh = c->g.Vh;
+  const int R = prec == 64 ? 18 : c->recon;
+  const double bl = real_bytes(prec);
+  const double bc = prec == 64 ? 8 : 4;
+  const double bs = 24.0 * real_bytes(prec) + (prec == 16 ? 4 : 0);
+  double site = 8.0 * R * bl + (epi != EPI_NONE ? 72.0 * bc : 0.0);
+  double rhs = bs * (epi == EPI_XPAY ? 3.0 : 2.0);
+  *bytes = Vh * site + Vh * nrhs * rhs;
+  *flops = Vh * nrhs * (1320.0 + (epi != EPI_NONE ? 504.0 : 0.0) + (epi == EPI_XPAY ? 48.0 : 0.0));
+}
+
+const void* gauge_ptr(const qcd_ctx* c, int prec) { return prec == 64 ? c->g64 : (prec == 32 ? c->g32 : c->g16); }
+
+const void* clover_ptr(const qcd_ctx* c, int prec, bool inverse, int parity) {
+  if (prec == 64) {
+    const double2* base = static_cast<const double2*>(inverse ? c->Ainv64 : c->A64);
+    return base + (size_t)parity * 36 * c->g.Vh;
+  }
+  const float4* base = static_cast<const float4*>(inverse ? c->Ainv32 : c->A32);
+  return base + (size_t)parity * 18 * c->g.Vh;
+}
+
+DslashArgs base_args(const qcd_ctx* c, int prec, int parity, int nrhs) {
+  DslashArgs a;
+  memset(&a, 0, sizeof a);
+  a.g = c->g;
+  a.p = parity;
+  a.nrhs = nrhs;
+  a.gauge = gauge_ptr(c, prec);
+  return a;
+}
+
+void run_dslash(qcd_ctx* c, int prec, int epi, const DslashArgs& a) {
+  double bytes, flops;
+  dslash_cost(c, prec, epi, a.nrhs, &bytes, &flops);
+  char name[40];
+  snprintf(name, sizeof name, "dslash_p%d_r%d_%s", prec, prec == 64 ? 18 : c->recon,
+           epi == EPI_NONE ? "plain" : (epi == EPI_CLOVER_INV ? "cloverinv" : "xpay"));
+  ProfScope ps(c, name, bytes, flops);
+  launch_dslash(prec, prec == 64 ? 18 : c->recon, epi, a, c->st);
+}
+
+ReduceArgs reduce_args(qcd_ctx* c, int mode) {
+  ReduceArgs r;
+  r.partials = c->partials;
+  r.counter = c->counter;
+  r.result = c->results;
+  r.mode = mode;
+  r.cg = c->cg;
+  r.ctl = c->ctl;
+  return r;
+}
+
+// out = Mhat in (dagger: Mhat^dag) on even sites, t: odd temporary.
+// red (may be null) reduces |out|^2 per RHS.
+void apply_mhat(qcd_ctx* c, int prec, int nrhs, bool dagger, const void* in, const float* in_n, void* out,
+                float* out_n, void* t, float* t_n, const ReduceArgs* red, const int* halt) {
+  const double k2 = c->kappa * c->kappa;
+  DslashArgs a = base_args(c, prec, 1, nrhs);
+  a.in = in;
+  a.in_norm = in_n;
+  a.out = t;
+  a.out_norm = t_n;
+  a.clover = clover_ptr(c, prec, true, 1);
+  a.in_g5 = dagger;
+  a.halt = halt;
+  run_dslash(c, prec, EPI_CLOVER_INV, a);
+  DslashArgs b = base_args(c, prec, 0, nrhs);
+  b.in = t;
+  b.in_norm = t_n;
+  b.out = out;
+  b.out_norm = out_n;
+  b.x = in;
+  b.x_norm = in_n;
+  b.clover = clover_ptr(c, prec, false, 0);
+  b.a = -k2;
+  b.x_g5 = dagger;
+  b.out_g5 = dagger;
+  b.halt = halt;
+  if (red) {
+    b.do_norm = 1;
+    b.red = *red;
+  }
+  run_dslash(c, prec, EPI_XPAY, b);
+}
+
+// out = Mhat^dag Mhat in; y: even temporary, t: odd temporary; pap reduces |Mhat in|^2
+void apply_mdagm(qcd_ctx* c, int prec, int nrhs, const void* in, const float* in_n, void* out, float* out_n, void* t,
+                 float* t_n, void* y, float* y_n, const ReduceArgs* pap, const int* halt) {
+  apply_mhat(c, prec, nrhs, false, in, in_n, y, y_n, t, t_n, pap, halt);
+  apply_mhat(c, prec, nrhs, true, y, y_n, out, out_n, t, t_n, nullptr, halt);
+}
+
+qcd_status check_ctx(qcd_ctx* c) {
+  if (!c) return fail(QCD_ERR_ARG, "null context");
+  CUDA_TRY(cudaSetDevice(c->device));
+  return QCD_OK;
+}
+
+qcd_status sync_and_check(qcd_ctx* c, const char* what) {
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QCD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  if (c->prof_on) prof_collect(c);
+  return QCD_OK;
+}
+
+bool valid_prec(int p) { return p == 64 || p == 32 || p == 16; }
+
+// largest supported batch (1, 2, 4 or 8) not above n
+int batch_of(int n) {
+  int b = 1;
+  while (b * 2 <= n && b * 2 <= MAX_RHS) b *= 2;
+  return b;
+}
+
+}  // namespace
+
+// ===================================================================== ABI ==
+extern "C" {
+
+const char* qcd_last_error(void) { return g_err.c_str(); }
+
+qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* stream) {
+  if (!out || !dims) return fail(QCD_ERR_ARG, "null argument");
+  *out = nullptr;
+  for (int k = 0; k < 4; k++)
+    if (dims[k] < 2 || dims[k] % 2) return fail(QCD_ERR_ARG, "extent %d = %d must be even and >= 2", k, dims[k]);
+  if (t_bc != 1.0 && t_bc != -1.0) return fail(QCD_ERR_ARG, "t_bc must be +1 or -1");
+  const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+  if (V * 8 >= (1LL << 31)) return fail(QCD_ERR_ARG, "lattice too large (V = %lld)", V);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(QCD_ERR_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+  qcd_ctx* c = new qcd_ctx();
+  c->device = dev;
+  c->st = static_cast<cudaStream_t>(stream);
+  c->g.X = dims[0];
+  c->g.Y = dims[1];
+  c->g.Z = dims[2];
+  c->g.T = dims[3];
+  c->g.Vh = (int)(V / 2);
+  c->g.XY = dims[0] * dims[1];
+  c->g.XYZ = dims[0] * dims[1] * dims[2];
+  c->g.t_bc = t_bc;
+  c->max_partials = (c->g.Vh * MAX_RHS + 63) / 64 + 64;
+  bool ok = cudaMalloc(&c->flags, 4 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&c->partials, sizeof(double) * (size_t)c->max_partials * MAX_RHS) == cudaSuccess &&
+            cudaMalloc(&c->counter, sizeof(unsigned)) == cudaSuccess &&
+            cudaMalloc(&c->results, sizeof(double) * MAX_RHS) == cudaSuccess &&
+            cudaMalloc(&c->cg, sizeof(CGState) * MAX_RHS) == cudaSuccess &&
+            cudaMalloc(&c->ctl, sizeof(CGControl)) == cudaSuccess &&
+            cudaMallocHost(&c->h_flags, 4 * sizeof(int)) == cudaSuccess &&
+            cudaMallocHost(&c->h_cg, sizeof(CGState) * MAX_RHS) == cudaSuccess &&
+            cudaMallocHost(&c->h_ctl, sizeof(CGControl)) == cudaSuccess &&
+            cudaMallocHost(&c->h_results, sizeof(double) * MAX_RHS) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    qcd_destroy(c);
+    return fail(QCD_ERR_NOMEM, "context allocation failed");
+  }
+  cudaMemset(c->counter, 0, sizeof(unsigned));
+  cudaMemset(c->flags, 0, 4 * sizeof(int));
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    qcd_destroy(c);
+    return fail(QCD_ERR_CUDA, "context init: %s", cudaGetErrorString(e));
+  }
+  *out = c;
+  return QCD_OK;
+}
+
+qcd_status qcd_destroy(qcd_ctx* c) {
+  if (!c) return QCD_OK;
+  cudaSetDevice(c->device);
+  if (c->st) cudaStreamSynchronize(c->st);
+  else cudaDeviceSynchronize();
+  void* dev[] = {c->g64, c->g32, c->g16, c->A64, c->Ainv64, c->A32, c->Ainv32, c->flags,
+                 c->partials, c->counter, c->results, c->cg, c->ctl};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  for (auto& b : c->ws)
+    if (b.ptr) cudaFree(b.ptr);
+  void* host[] = {c->h_flags, c->h_cg, c->h_ctl, c->h_results};
+  for (void* p : host)
+    if (p) cudaFreeHost(p);
+  for (auto& p : c->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : c->ev_free) cudaEventDestroy(e);
+  delete c;
+  return QCD_OK;
+}
+
+qcd_status qcd_load_gauge(qcd_ctx* c, const double* U, int on_device, int flags) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!U) return fail(QCD_ERR_ARG, "null gauge pointer");
+  if (flags & ~QCD_GAUGE_RECON12) return fail(QCD_ERR_ARG, "unknown gauge flags 0x%x", flags);
+  const Geom& g = c->g;
+  const size_t n_links = (size_t)g.Vh * 2 * 4;
+  const size_t canon_bytes = n_links * 9 * sizeof(double2);
+  c->recon = (flags & QCD_GAUGE_RECON12) ? 12 : 18;
+  if (!c->g64) {
+    CUDA_TRY(cudaMalloc(&c->g64, canon_bytes));
+    CUDA_TRY(cudaMalloc(&c->g32, n_links * 9 * sizeof(float2)));
+    CUDA_TRY(cudaMalloc(&c->g16, n_links * 9 * sizeof(uint32_t)));
+  }
+  const double2* src = reinterpret_cast<const double2*>(U);
+  if (!on_device) {
+    void* stage;
+    if ((s = ws_get(c, S_CANON, canon_bytes, &stage))) return s;
+    CUDA_TRY(cudaMemcpyAsync(stage, U, canon_bytes, cudaMemcpyHostToDevice, c->st));
+    src = static_cast<const double2*>(stage);
+  }
+  CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->st));
+  launch_check_finite(reinterpret_cast<const double*>(src), n_links * 18, c->flags + 1, c->st);
+  launch_pack_gauge(g, src, c->g64, c->g32, c->recon, c->g16, c->recon, c->st);
+  CUDA_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  if ((s = sync_and_check(c, "load_gauge"))) return s;
+  c->have_clover = false;
+  if (c->h_flags[1]) {
+    c->have_gauge = false;
+    return fail(QCD_ERR_NAN, "gauge field holds a non-finite value");
+  }
+  c->have_gauge = true;
+  return QCD_OK;
+}
+
+qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!c->have_gauge) return fail(QCD_ERR_STATE, "clover_build before load_gauge");
+  if (!(kappa == kappa) || !(csw == csw)) return fail(QCD_ERR_ARG, "kappa/csw not finite");
+  const Geom& g = c->g;
+  if (!c->A64) {
+    CUDA_TRY(cudaMalloc(&c->A64, (size_t)2 * 36 * g.Vh * sizeof(double2)));
+    CUDA_TRY(cudaMalloc(&c->Ainv64, (size_t)2 * 36 * g.Vh * sizeof(double2)));
+    CUDA_TRY(cudaMalloc(&c->A32, (size_t)2 * 18 * g.Vh * sizeof(float4)));
+    CUDA_TRY(cudaMalloc(&c->Ainv32, (size_t)2 * 18 * g.Vh * sizeof(float4)));
+  }
+  CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->st));
+  {
+    ProfScope ps(c, "clover_build", 0, 0);
+    launch_clover_build(g, c->g64, kappa, csw, c->A64, c->Ainv64, c->A32, c->Ainv32, c->flags, c->st);
+  }
+  CUDA_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  if ((s = sync_and_check(c, "clover_build"))) return s;
+  if (c->h_flags[0]) {
+    c->have_clover = false;
+    return fail(QCD_ERR_NOT_POSDEF, "a clover block is not positive definite (kappa=%g, csw=%g)", kappa, csw);
+  }
+  c->kappa = kappa;
+  c->csw = csw;
+  c->have_clover = true;
+  return QCD_OK;
+}
+
+qcd_status qcd_dslash(qcd_ctx* c, double* out, const double* in, int op, int dagger, int prec, int nrhs) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!out || !in) return fail(QCD_ERR_ARG, "null field pointer");
+  if (op < QCD_OP_DSLASH_EO || op > QCD_OP_CLOVER_INV) return fail(QCD_ERR_ARG, "unknown op %d", op);
+  if (!valid_prec(prec)) return fail(QCD_ERR_ARG, "precision must be 64, 32 or 16");
+  if (nrhs < 1) return fail(QCD_ERR_ARG, "nrhs must be >= 1");
+  if (!c->have_gauge) return fail(QCD_ERR_STATE, "dslash before load_gauge");
+  const bool needs_clover = op >= QCD_OP_MHAT;
+  if (needs_clover && !c->have_clover) return fail(QCD_ERR_STATE, "op %d needs clover_build", op);
+  const Geom& g = c->g;
+  const size_t canon = (size_t)g.Vh * 12 * sizeof(double2);
+  if ((const char*)out < (const char*)in + canon * nrhs && (const char*)in < (const char*)out + canon * nrhs)
+    return fail(QCD_ERR_ARG, "in and out overlap");
+  int done = 0;
+  while (done < nrhs) {
+    const int nb = batch_of(nrhs - done);
+    const double2* cin = reinterpret_cast<const double2*>(in) + (size_t)done * g.Vh * 12;
+    double2* cout = reinterpret_cast<double2*>(out) + (size_t)done * g.Vh * 12;
+    void *vin, *vout, *vt, *vy, *nin = nullptr, *nout = nullptr, *nt = nullptr, *ny = nullptr;
+    const size_t fb = spinor_bytes(g, prec, nb), nbytes = sizeof(float) * (size_t)g.Vh * nb;
+    if ((s = ws_get(c, S_IN, fb, &vin)) || (s = ws_get(c, S_OUT, fb, &vout)) || (s = ws_get(c, S_T, fb, &vt)) ||
+        (s = ws_get(c, S_Y, fb, &vy)))
+      return s;
+    if (prec == 16) {
+      if ((s = ws_get(c, S_IN_N, nbytes, &nin)) || (s = ws_get(c, S_OUT_N, nbytes, &nout)) ||
+          (s = ws_get(c, S_T_N, nbytes, &nt)) || (s = ws_get(c, S_Y_N, nbytes, &ny)))
+        return s;
+    }
+    float *fin = (float*)nin, *fout = (float*)nout, *ft = (float*)nt, *fy = (float*)ny;
+    launch_spinor_to_native(prec, g, cin, vin, fin, nb, c->st);
+    switch (op) {
+      case QCD_OP_DSLASH_EO:
+      case QCD_OP_DSLASH_OE: {
+        DslashArgs a = base_args(c, prec, op == QCD_OP_DSLASH_EO ? 0 : 1, nb);
+        a.in = vin;
+        a.in_norm = fin;
+        a.out = vout;
+        a.out_norm = fout;
+        a.in_g5 = a.out_g5 = dagger ? 1 : 0;
+        run_dslash(c, prec, EPI_NONE, a);
+        break;
+      }
+      case QCD_OP_MHAT:
+        apply_mhat(c, prec, nb, dagger != 0, vin, fin, vout, fout, vt, ft, nullptr, nullptr);
+        break;
+      case QCD_OP_MDAGM:
+        apply_mdagm(c, prec, nb, vin, fin, vout, fout, vt, ft, vy, fy, nullptr, nullptr);
+        break;
+      case QCD_OP_CLOVER:
+        launch_clover_apply(prec, g, clover_ptr(c, prec, false, 0), vin, fin, vout, fout, nb, c->st);
+        break;
+      case QCD_OP_CLOVER_INV:
+        launch_clover_apply(prec, g, clover_ptr(c, prec, true, 1), vin, fin, vout, fout, nb, c->st);
+        break;
+    }
+    launch_spinor_to_canon(prec, g, vout, fout, cout, nb, c->st);
+    done += nb;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QCD_ERR_CUDA, "dslash launch: %s", cudaGetErrorString(e));
+  return QCD_OK;
+}
+
+}  // extern "C"
+
+// ============================================================ CG driver ==
+namespace {
+
+struct SolverFields {
+  int pr, pp;  // precision of x_lo/r_lo and of p/Ap/temporaries
+  double2 *b_hi, *x_hi, *ap_hi, *t_hi, *y_hi;
+  void *x_lo, *r_lo, *p, *ap, *t, *y;
+  float *x_lo_n, *r_lo_n, *p_n, *ap_n, *t_n, *y_n;
+};
+
+qcd_status solver_fields(qcd_ctx* c, int inner, int nrhs, SolverFields* f) {
+  const Geom& g = c->g;
+  f->pp = inner;
+  f->pr = inner == 64 ? 64 : 32;
+  qcd_status s;
+  void* v;
+  const size_t hi = spinor_bytes(g, 64, nrhs), lo_r = spinor_bytes(g, f->pr, nrhs), lo_p = spinor_bytes(g, f->pp, nrhs);
+#define GET(slot, bytes, dst, type)                       \
+  if ((s = ws_get(c, slot, bytes, &v))) return s; \
+  dst = static_cast<type>(v);
+  GET(S_B_HI, hi, f->b_hi, double2*);
+  GET(S_X_HI, hi, f->x_hi, double2*);
+  GET(S_AP_HI, hi, f->ap_hi, double2*);
+  GET(S_T_HI, hi, f->t_hi, double2*);
+  GET(S_Y_HI, hi, f->y_hi, double2*);
+  GET(S_X_LO, lo_r, f->x_lo, void*);
+  GET(S_R_LO, lo_r, f->r_lo, void*);
+  GET(S_P, lo_p, f->p, void*);
+  GET(S_AP, lo_p, f->ap, void*);
+  GET(S_TL, lo_p, f->t, void*);
+  GET(S_YL, lo_p, f->y, void*);
+  f->x_lo_n = f->r_lo_n = f->p_n = f->ap_n = f->t_n = f->y_n = nullptr;
+  if (f->pp == 16) {
+    const size_t nb = sizeof(float) * (size_t)g.Vh * nrhs;
+    GET(S_P_N, nb, f->p_n, float*);
+    GET(S_AP_N, nb, f->ap_n, float*);
+    GET(S_TL_N, nb, f->t_n, float*);
+    GET(S_YL_N, nb, f->y_n, float*);
+  }
+#undef GET
+  return QCD_OK;
+}
+
+void update_cost(const Geom& g, int pr, int pp, int nrhs, double* bytes) {
+  const double sr = 24.0 * real_bytes(pr), sp = 24.0 * real_bytes(pp) + (pp == 16 ? 4 : 0);
+  *bytes = (double)g.Vh * nrhs * (4 * sr + 2 * sp);
+}
+
+// one reliable update: x_hi += x_lo, r = b - A x_hi in FP64, p = r + beta p
+void reliable_update(qcd_ctx* c, const SolverFields& f, int nrhs) {
+  const Geom& g = c->g;
+  launch_accumulate_x(f.pr, g, nrhs, f.x_hi, f.x_lo, f.x_lo_n, c->st);
+  apply_mdagm(c, 64, nrhs, f.x_hi, nullptr, f.ap_hi, nullptr, f.t_hi, nullptr, f.y_hi, nullptr, nullptr, nullptr);
+  ReduceArgs red = reduce_args(c, FIN_CG_TRUE);
+  launch_true_residual(f.pr, g, nrhs, f.b_hi, f.ap_hi, f.r_lo, f.r_lo_n, red, c->st);
+  launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->st);
+  cudaMemsetAsync(&c->ctl->halt, 0, sizeof(int), c->st);
+}
+
+qcd_status read_state(qcd_ctx* c, int nrhs) {
+  cudaMemcpyAsync(c->h_cg, c->cg, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(CGControl), cudaMemcpyDeviceToHost, c->st);
+  return sync_and_check(c, "cg state");
+}
+
+// Solve for one batch of nrhs (1, 2, 4 or 8) canonical fields.
+qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qcd_solver_params* prm,
+                    qcd_solver_stats* stats) {
+  const Geom& g = c->g;
+  SolverFields f;
+  qcd_status s = solver_fields(c, prm->inner_prec, nrhs, &f);
+  if (s) return s;
+  // b_hi and |b|^2
+  launch_spinor_to_native(64, g, b, f.b_hi, nullptr, nrhs, c->st);
+  launch_norm2(g, nrhs, f.b_hi, reduce_args(c, FIN_STORE), c->st);
+  CUDA_TRY(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
+  if ((s = sync_and_check(c, "cg init"))) return s;
+  bool any = false;
+  for (int r = 0; r < nrhs; r++) {
+    if (!std::isfinite(c->h_results[r])) return fail(QCD_ERR_NAN, "source %d holds a non-finite value", r);
+    CGState st;
+    memset(&st, 0, sizeof st);
+    st.bnorm2 = c->h_results[r];
+    st.tol2 = prm->tol * prm->tol * st.bnorm2;
+    st.active = st.bnorm2 > 0.0 ? 1 : 0;
+    st.reliable_updates = -1;
+    any |= st.active != 0;
+    c->h_cg[r] = st;
+  }
+  CGControl ctl;
+  memset(&ctl, 0, sizeof ctl);
+  const bool mixed = prm->inner_prec != 64;
+  ctl.reliable_every = mixed ? (prm->reliable_every > 0 ? prm->reliable_every : 50) : (1 << 30);
+  ctl.delta2 = mixed ? prm->reliable_delta * prm->reliable_delta : 0.0;
+  *c->h_ctl = ctl;
+  CUDA_TRY(cudaMemcpyAsync(c->cg, c->h_cg, sizeof(CGState) * nrhs, cudaMemcpyHostToDevice, c->st));
+  CUDA_TRY(cudaMemcpyAsync(c->ctl, c->h_ctl, sizeof(CGControl), cudaMemcpyHostToDevice, c->st));
+  // x_hi, x_lo = 0, p = 0, Ap_hi = A x0
+  if (prm->use_x0) launch_spinor_to_native(64, g, x, f.x_hi, nullptr, nrhs, c->st);
+  else launch_zero(f.x_hi, spinor_bytes(g, 64, nrhs), c->st);
+  launch_zero(f.x_lo, spinor_bytes(g, f.pr, nrhs), c->st);
+  launch_zero(f.p, spinor_bytes(g, f.pp, nrhs), c->st);
+  if (f.p_n) launch_zero(f.p_n, sizeof(float) * (size_t)g.Vh * nrhs, c->st);
+  if (prm->use_x0)
+    apply_mdagm(c, 64, nrhs, f.x_hi, nullptr, f.ap_hi, nullptr, f.t_hi, nullptr, f.y_hi, nullptr, nullptr, nullptr);
+  else
+    launch_zero(f.ap_hi, spinor_bytes(g, 64, nrhs), c->st);
+  launch_true_residual(f.pr, g, nrhs, f.b_hi, f.ap_hi, f.r_lo, f.r_lo_n, reduce_args(c, FIN_CG_TRUE), c->st);
+  launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->st);
+  if ((s = read_state(c, nrhs))) return s;
+
+  const int* halt = &c->ctl->halt;
+  ReduceArgs red_pap = reduce_args(c, FIN_CG_PAP);
+  ReduceArgs red_rr = reduce_args(c, FIN_CG_RR);
+  double ub;
+  update_cost(g, f.pr, f.pp, nrhs, &ub);
+  int chunk = 8;
+  qcd_status result = QCD_OK;
+  while (true) {
+    bool active = false;
+    int max_it = 0;
+    for (int r = 0; r < nrhs; r++) {
+      active |= c->h_cg[r].active != 0;
+      if (c->h_cg[r].iters > max_it) max_it = c->h_cg[r].iters;
+    }
+    if (c->h_ctl->nan) {
+      result = fail(QCD_ERR_NAN, "non-finite value or breakdown in CG");
+      break;
+    }
+    if (!active) break;
+    if (max_it >= prm->max_iter) {
+      result = fail(QCD_ERR_NOT_CONVERGED, "CG did not converge in %d iterations", prm->max_iter);
+      break;
+    }
+    if (c->h_ctl->halt) {
+      reliable_update(c, f, nrhs);
+      if ((s = read_state(c, nrhs))) return s;
+      continue;
+    }
+    const int n = chunk < prm->max_iter - max_it ? chunk : prm->max_iter - max_it;
+    for (int k = 0; k < n; k++) {
+      apply_mdagm(c, f.pp, nrhs, f.p, f.p_n, f.ap, f.ap_n, f.t, f.t_n, f.y, f.y_n, &red_pap, halt);
+      {
+        ProfScope ps(c, "cg_update", ub, 0);
+        launch_cg_update(f.pr, f.pp, g, nrhs, f.x_lo, f.x_lo_n, f.r_lo, f.r_lo_n, f.p, f.p_n, f.ap, f.ap_n, red_rr,
+                         halt, c->st);
+      }
+      launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, halt, c->st);
+    }
+    if ((s = read_state(c, nrhs))) return s;
+    if (chunk < 32) chunk *= 2;
+  }
+  // not converged: fold the progress into x and recompute the true residual for the stats
+  if (result == QCD_ERR_NOT_CONVERGED) reliable_update(c, f, nrhs);
+  // fold the last low-precision increment into x and write out
+  launch_accumulate_x(f.pr, g, nrhs, f.x_hi, f.x_lo, f.x_lo_n, c->st);
+  launch_spinor_to_canon(64, g, f.x_hi, nullptr, x, nrhs, c->st);
+  launch_redot(g, nrhs, f.b_hi, f.x_hi, reduce_args(c, FIN_STORE), c->st);
+  CUDA_TRY(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
+  if ((s = read_state(c, nrhs))) return s;
+  if (stats) {
+    for (int r = 0; r < nrhs; r++) {
+      const CGState& st = c->h_cg[r];
+      stats[r].iters = st.iters;
+      stats[r].reliable_updates = st.reliable_updates;
+      stats[r].true_rel_resid = st.bnorm2 > 0 ? sqrt(st.true_rr / st.bnorm2) : 0.0;
+      stats[r].b_dot_x = c->h_results[r];
+    }
+  }
+  return result;
+}
+
+qcd_status check_params(const qcd_solver_params* p) {
+  if (!p) return fail(QCD_ERR_ARG, "null solver params");
+  if (!(p->tol > 0.0) || p->max_iter < 1) return fail(QCD_ERR_ARG, "tol must be > 0 and max_iter >= 1");
+  if (!valid_prec(p->inner_prec)) return fail(QCD_ERR_ARG, "inner_prec must be 64, 32 or 16");
+  if (p->inner_prec != 64 && !(p->reliable_delta >= 0.0 && p->reliable_delta < 1.0))
+    return fail(QCD_ERR_ARG, "reliable_delta must be in [0, 1)");
+  return QCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qcd_status qcd_cg_solve(qcd_ctx* c, double* x, const double* b, int nrhs, const qcd_solver_params* prm,
+                        qcd_solver_stats* stats) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!x || !b) return fail(QCD_ERR_ARG, "null field pointer");
+  if (nrhs < 1) return fail(QCD_ERR_ARG, "nrhs must be >= 1");
+  if ((s = check_params(prm))) return s;
+  if (!c->have_clover) return fail(QCD_ERR_STATE, "cg_solve before clover_build");
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t fs = (size_t)c->g.Vh * 12;
+  qcd_status worst = QCD_OK;
+  int done = 0;
+  while (done < nrhs) {
+    const int nb = batch_of(nrhs - done);
+    s = cg_batch(c, reinterpret_cast<double2*>(x) + done * fs, reinterpret_cast<const double2*>(b) + done * fs, nb,
+                 prm, stats ? stats + done : nullptr);
+    if (s == QCD_ERR_NOT_CONVERGED) worst = s;
+    else if (s) return s;
+    done += nb;
+  }
+  const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats)
+    for (int r = 0; r < nrhs; r++) stats[r].seconds = sec;
+  return worst;
+}
+
+qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int nrhs, int flags,
+                             const qcd_solver_params* prm, qcd_solver_stats* stats) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!F || !phi_or_x) return fail(QCD_ERR_ARG, "null pointer");
+  if (nrhs < 1) return fail(QCD_ERR_ARG, "nrhs must be >= 1");
+  if (flags & ~(QCD_FORCE_INPUT_IS_SOLUTION | QCD_FORCE_GRADIENT)) return fail(QCD_ERR_ARG, "unknown force flags");
+  if (!c->have_clover) return fail(QCD_ERR_STATE, "fermion_force before clover_build");
+  const Geom& g = c->g;
+  const size_t fs = (size_t)g.Vh * 12;
+  // X (canonical, FP64) for all RHS
+  const double2* X = reinterpret_cast<const double2*>(phi_or_x);
+  if (!(flags & QCD_FORCE_INPUT_IS_SOLUTION)) {
+    if ((s = check_params(prm))) return s;
+    void* v;
+    if ((s = ws_get(c, S_CANON, fs * nrhs * sizeof(double2), &v))) return s;
+    CUDA_TRY(cudaMemsetAsync(v, 0, fs * nrhs * sizeof(double2), c->st));
+    qcd_solver_params p2 = *prm;
+    p2.use_x0 = 0;
+    s = qcd_cg_solve(c, static_cast<double*>(v), phi_or_x, nrhs, &p2, stats);
+    if (s && s != QCD_ERR_NOT_CONVERGED) return s;
+    X = static_cast<const double2*>(v);
+  }
+  // native FP64 X_e, Y_e = Mhat X_e, X_o = A^-1 D_oe X_e, Y_o = g5 A^-1 D_oe g5 Y_e; batches of <= 8 RHS
+  const size_t hi1 = spinor_bytes(g, 64, 1);
+  void *xf, *yf, *clf;
+  if ((s = ws_get(c, S_F_X, 2 * hi1 * nrhs, &xf)) || (s = ws_get(c, S_F_Y, 2 * hi1 * nrhs, &yf)) ||
+      (s = ws_get(c, S_F_CL, force_clover_bytes(g), &clf)))
+    return s;
+  double2* Xe = static_cast<double2*>(xf);
+  double2* Xo = Xe + (size_t)nrhs * 12 * g.Vh;
+  double2* Ye = static_cast<double2*>(yf);
+  double2* Yo = Ye + (size_t)nrhs * 12 * g.Vh;
+  launch_spinor_to_native(64, g, X, Xe, nullptr, nrhs, c->st);
+  int done = 0;
+  while (done < nrhs) {
+    const int nb = batch_of(nrhs - done);
+    const size_t off = (size_t)done * 12 * g.Vh;
+    // Y_e = Mhat X_e with X_o = A_oo^-1 D_oe X_e left in the odd temporary
+    apply_mhat(c, 64, nb, false, Xe + off, nullptr, Ye + off, nullptr, Xo + off, nullptr, nullptr, nullptr);
+    // Y_o = A_oo^-1 D_eo^dag Y_e = g5 A_oo^-1 D_oe g5 Y_e
+    DslashArgs a = base_args(c, 64, 1, nb);
+    a.in = Ye + off;
+    a.out = Yo + off;
+    a.clover = clover_ptr(c, 64, true, 1);
+    a.in_g5 = 1;
+    a.out_g5 = 1;
+    run_dslash(c, 64, EPI_CLOVER_INV, a);
+    done += nb;
+  }
+  {
+    ProfScope ps(c, "force", 0, 0);
+    launch_force(g, c->kappa, c->csw, nrhs, c->g64, Xe, Xo, Ye, Yo, static_cast<double2*>(clf),
+                 reinterpret_cast<double2*>(F), (flags & QCD_FORCE_GRADIENT) != 0, c->st);
+  }
+  return sync_and_check(c, "fermion_force");
+}
+
+qcd_status qcd_profile(qcd_ctx* c, int enable) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if ((s = sync_and_check(c, "profile"))) return s;
+  prof_collect(c);
+  if (enable) {
+    c->prof.clear();
+    g_kernel_launches = 0;
+  }
+  c->prof_on = enable != 0;
+  return QCD_OK;
+}
+
+qcd_status qcd_profile_read(qcd_ctx* c, qcd_kernel_stat* out, int max_entries, int* n_entries) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!n_entries || (max_entries > 0 && !out)) return fail(QCD_ERR_ARG, "null output");
+  CUDA_TRY(cudaStreamSynchronize(c->st));
+  prof_collect(c);
+  int n = 0;
+  for (auto& p : c->prof) {
+    if (n >= max_entries) break;
+    memset(&out[n], 0, sizeof(qcd_kernel_stat));
+    snprintf(out[n].name, sizeof out[n].name, "%s", p.name.c_str());
+    out[n].launches = p.launches;
+    out[n].total_ms = p.ms;
+    out[n].bytes = p.bytes;
+    out[n].flops = p.flops;
+    n++;
+  }
+  if (n < max_entries) {
+    // pseudo-entry: every kernel the library launched since qcd_profile(ctx, 1)
+    memset(&out[n], 0, sizeof(qcd_kernel_stat));
+    snprintf(out[n].name, sizeof out[n].name, "launches_total");
+    out[n].launches = (int)g_kernel_launches;
+    n++;
+  }
+  *n_entries = n;
+  return QCD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,228 @@
+// Clover term A(x) = 1 - kappa c_sw sum_{mu<nu} sigma_{mu nu} F_{mu nu}(x) and its inverse.
+//
+// Standard Sheikholeslami-Wohlert definition (the paper's application is MILC's
+// clover_dynamical, Sec. 1): Q_{mu nu}(x) is the sum of the four plaquette
+// leaves around x in the (mu, nu) plane, F = traceless part of (Q - Q^dag)/(8i).
+// In the DeGrand-Rossi basis sigma_{mu nu} is block diagonal in chirality, so A
+// is two Hermitian 6x6 blocks.  With the 2x2 spin blocks of sigma written as
+// Pauli matrices, block b (b = 0: spins 0,1; b = 1: spins 2,3) is
+//   A_b = 1 - kappa c_sw [[ B3, B1 - i B2 ], [ B1 + i B2, -B3 ]]
+//   b = 0: B1 = F_yz - F_xt, B2 = F_xz + F_yt, B3 = F_xy - F_zt
+//   b = 1: B1 = F_yz + F_xt, B2 = F_xz - F_yt, B3 = F_xy + F_zt.
+// The inverse is formed once per gauge field in FP64 by a Cholesky factorisation
+// A_b = L L^dag and A_b^-1 = L^-dag L^-1; a non-positive pivot raises a flag.
+#include "qcd_kernels.h"
+#include "qcd_su3.cuh"
+
+namespace qcd {
+
+namespace {
+
+// traceless part of (Q - Q^dag) / (8 i), with Q the four-leaf sum in the (mu, nu) plane
+__device__ M3 field_strength(const Geom& g, const double2* g64, const int c[4], int mu, int nu) {
+  int xm[4] = {c[0], c[1], c[2], c[3]};
+  auto at = [&](int dm, int dn, int dir) {
+    int q[4] = {xm[0], xm[1], xm[2], xm[3]};
+    q[mu] += dm;
+    q[nu] += dn;
+    return link_at(g, g64, q[0], q[1], q[2], q[3], dir);
+  };
+  M3 Q;
+  // U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+  M3 l = mul_nd(mul_nd(mul(at(0, 0, mu), at(1, 0, nu)), at(0, 1, mu)), at(0, 0, nu));
+  Q = l;
+  // U_nu(x) U_mu(x-mu+nu)^dag U_nu(x-mu)^dag U_mu(x-mu)
+  l = mul(mul_nd(mul_nd(at(0, 0, nu), at(-1, 1, mu)), at(-1, 0, nu)), at(-1, 0, mu));
+#pragma unroll
+  for (int k = 0; k < 9; k++) Q.e[k] = Q.e[k] + l.e[k];
+  // U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
+  M3 t1 = at(-1, 0, mu), t2 = at(-1, -1, nu);
+  M3 a;  // t1^dag t2^dag = (t2 t1)^dag
+  {
+    M3 b = mul(t2, t1);
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+      for (int j = 0; j < 3; j++) a.e[3 * i + j] = conj(b.e[3 * j + i]);
+  }
+  l = mul(mul(a, at(-1, -1, mu)), at(0, -1, nu));
+#pragma unroll
+  for (int k = 0; k < 9; k++) Q.e[k] = Q.e[k] + l.e[k];
+  // U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^dag
+  l = mul_nd(mul(mul_dn(at(0, -1, nu), at(0, -1, mu)), at(1, -1, nu)), at(0, 0, mu));
+#pragma unroll
+  for (int k = 0; k < 9; k++) Q.e[k] = Q.e[k] + l.e[k];
+  M3 F;
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      C d = Q.e[3 * i + j] - conj(Q.e[3 * j + i]);
+      F.e[3 * i + j] = cmk(d.im * 0.125, -d.re * 0.125);  // d / (8 i)
+    }
+  const double tr = (F.e[0].re + F.e[4].re + F.e[8].re) / 3.0;
+  F.e[0].re -= tr;
+  F.e[4].re -= tr;
+  F.e[8].re -= tr;
+  return F;
+}
+
+__device__ __forceinline__ int tri(int i, int j) { return i * (i - 1) / 2 + j; }
+
+// Cholesky-based inverse of a Hermitian positive definite 6x6 matrix given as
+// (diag d, strictly-lower L).  Returns false on a non-positive pivot.
+__device__ bool invert6(const double d[6], const C L[15], double di[6], C Li[15]) {
+  C a[6][6];
+  for (int i = 0; i < 6; i++) {
+    a[i][i] = cmk(d[i], 0.0);
+    for (int j = 0; j < i; j++) {
+      a[i][j] = L[tri(i, j)];
+      a[j][i] = conj(L[tri(i, j)]);
+    }
+  }
+  C l[6][6];
+  double ld[6];
+  for (int j = 0; j < 6; j++) {
+    double s = a[j][j].re;
+    for (int k = 0; k < j; k++) s -= norm2(l[j][k]);
+    if (!(s > 0.0)) return false;
+    ld[j] = sqrt(s);
+    l[j][j] = cmk(ld[j], 0.0);
+    for (int i = j + 1; i < 6; i++) {
+      C v = a[i][j];
+      for (int k = 0; k < j; k++) v = v - l[i][k] * conj(l[j][k]);
+      l[i][j] = cmk(v.re / ld[j], v.im / ld[j]);
+    }
+  }
+  // m = L^-1 (lower triangular)
+  C m[6][6];
+  for (int j = 0; j < 6; j++) {
+    for (int i = 0; i < j; i++) m[i][j] = cmk(0.0, 0.0);
+    m[j][j] = cmk(1.0 / ld[j], 0.0);
+    for (int i = j + 1; i < 6; i++) {
+      C s = cmk(0.0, 0.0);
+      for (int k = j; k < i; k++) s = s + l[i][k] * m[k][j];
+      m[i][j] = cmk(-s.re / ld[i], -s.im / ld[i]);
+    }
+  }
+  // A^-1 = m^dag m
+  for (int i = 0; i < 6; i++) {
+    for (int j = 0; j <= i; j++) {
+      C s = cmk(0.0, 0.0);
+      for (int k = i; k < 6; k++) s = cfmac(m[k][i], m[k][j], s);
+      if (i == j) di[i] = s.re;
+      else Li[tri(i, j)] = s;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void store_block64(double2* base, int Vh, int h, int b, const double d[6], const C L[15]) {
+  double2* q = base + (size_t)(b * 18) * Vh + h;
+  for (int k = 0; k < 3; k++) q[(size_t)k * Vh] = make_double2(d[2 * k], d[2 * k + 1]);
+  for (int k = 0; k < 15; k++) q[(size_t)(3 + k) * Vh] = make_double2(L[k].re, L[k].im);
+}
+
+__device__ __forceinline__ void store_block32(float4* base, int Vh, int h, int b, const double d[6], const C L[15]) {
+  float f[36];
+  for (int k = 0; k < 6; k++) f[k] = (float)d[k];
+  for (int k = 0; k < 15; k++) {
+    f[6 + 2 * k] = (float)L[k].re;
+    f[7 + 2 * k] = (float)L[k].im;
+  }
+  float4* q = base + (size_t)(b * 9) * Vh + h;
+  for (int k = 0; k < 9; k++) q[(size_t)k * Vh] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+}
+
+__global__ void __launch_bounds__(128) clover_build_kernel(Geom g, const double2* __restrict__ g64, double kappa,
+                                                           double csw, double2* A64, double2* Ainv64, float4* A32,
+                                                           float4* Ainv32, int* notposdef) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= 2 * g.Vh) return;
+  const int p = tid / g.Vh, h = tid - p * g.Vh;
+  const Site s = site_of(g, p, h);
+  const int c[4] = {s.x, s.y, s.z, s.t};
+  // F_{mu nu} for the six planes: xy xz xt yz yt zt
+  M3 F[6];
+  int k = 0;
+  for (int mu = 0; mu < 4; mu++)
+    for (int nu = mu + 1; nu < 4; nu++) F[k++] = field_strength(g, g64, c, mu, nu);
+  const M3 &Fxy = F[0], &Fxz = F[1], &Fxt = F[2], &Fyz = F[3], &Fyt = F[4], &Fzt = F[5];
+  const double kc = kappa * csw;
+  for (int b = 0; b < 2; b++) {
+    const double sg = b == 0 ? -1.0 : 1.0;
+    C B1[9], B2[9], B3[9];
+    for (int e = 0; e < 9; e++) {
+      B1[e] = Fyz.e[e] + sg * Fxt.e[e];
+      B2[e] = Fxz.e[e] - sg * Fyt.e[e];
+      B3[e] = Fxy.e[e] + sg * Fzt.e[e];
+    }
+    // H = [[B3, B1 - i B2], [B1 + i B2, -B3]], A_b = 1 - kc H
+    double d[6];
+    C L[15];
+    for (int i = 0; i < 6; i++) {
+      const int ii = i % 3;
+      d[i] = 1.0 - kc * (i < 3 ? B3[4 * ii].re : -B3[4 * ii].re);
+      for (int j = 0; j < i; j++) {
+        const int jj = j % 3;
+        C hv;
+        if (i < 3) hv = B3[3 * ii + jj];
+        else if (j < 3) hv = B1[3 * ii + jj] + times_i(B2[3 * ii + jj]);
+        else hv = -B3[3 * ii + jj];
+        L[tri(i, j)] = cmk(-kc * hv.re, -kc * hv.im);
+      }
+    }
+    double di[6];
+    C Li[15];
+    if (!invert6(d, L, di, Li)) {
+      *notposdef = 1;
+      for (int i = 0; i < 6; i++) di[i] = 0.0;
+      for (int i = 0; i < 15; i++) Li[i] = cmk(0.0, 0.0);
+    }
+    double2* A64p = A64 + (size_t)p * 36 * g.Vh;
+    double2* I64p = Ainv64 + (size_t)p * 36 * g.Vh;
+    store_block64(A64p, g.Vh, h, b, d, L);
+    store_block64(I64p, g.Vh, h, b, di, Li);
+    if (A32) store_block32(A32 + (size_t)p * 18 * g.Vh, g.Vh, h, b, d, L);
+    if (Ainv32) store_block32(Ainv32 + (size_t)p * 18 * g.Vh, g.Vh, h, b, di, Li);
+  }
+}
+
+template <int P>
+__global__ void clover_apply_kernel(Geom g, const void* clov, const void* in, const float* in_norm, void* out,
+                                    float* out_norm, int nrhs) {
+  using R = typename Real<P>::T;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= g.Vh * nrhs) return;
+  const int r = tid % nrhs, h = tid / nrhs;
+  cx<R> s[12], o[12];
+  SpinorIO<P>::load(in, in_norm, g.Vh, r, h, s);
+  constexpr int CP = P == 64 ? 64 : 32;
+  CloverIO<CP>::apply(clov, g.Vh, h, 0, s, o);
+  CloverIO<CP>::apply(clov, g.Vh, h, 1, s + 6, o + 6);
+  SpinorIO<P>::store(out, out_norm, g.Vh, r, h, o);
+}
+
+}  // namespace
+
+void launch_clover_build(const Geom& g, const void* g64, double kappa, double csw, void* A64, void* Ainv64, void* A32,
+                         void* Ainv32, int* notposdef, cudaStream_t st) {
+  g_kernel_launches += 1;
+  const int B = 128;
+  const int nb = (2 * g.Vh + B - 1) / B;
+  clover_build_kernel<<<nb, B, 0, st>>>(g, static_cast<const double2*>(g64), kappa, csw, static_cast<double2*>(A64),
+                                        static_cast<double2*>(Ainv64), static_cast<float4*>(A32),
+                                        static_cast<float4*>(Ainv32), notposdef);
+}
+
+void launch_clover_apply(int prec, const Geom& g, const void* clover, const void* in, const float* in_norm, void* out,
+                         float* out_norm, int nrhs, cudaStream_t st) {
+  g_kernel_launches += 1;
+  const int B = 128;
+  const int nb = (g.Vh * nrhs + B - 1) / B;
+  if (prec == 64) clover_apply_kernel<64><<<nb, B, 0, st>>>(g, clover, in, in_norm, out, out_norm, nrhs);
+  else if (prec == 32) clover_apply_kernel<32><<<nb, B, 0, st>>>(g, clover, in, in_norm, out, out_norm, nrhs);
+  else clover_apply_kernel<16><<<nb, B, 0, st>>>(g, clover, in, in_norm, out, out_norm, nrhs);
+}
+
+}  // namespace qcd

@@ -1,0 +1,227 @@
+// Wilson hopping term with spin projection, and its fused clover epilogues.
+//
+//   (D psi)(x) = sum_mu [ (1 - g_mu) U_mu(x) psi(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi(x-mu) ]
+//
+// (standard Wilson-clover definition; the paper's application, Sec. 1, is MILC's
+// clover_dynamical).  In the DeGrand-Rossi basis (1 -+ g_mu) has rank two: the
+// lower two spin rows are fixed multiples of the upper two, so each neighbour is
+// projected to a half spinor (2 spins x 3 colours), multiplied by the SU(3) link
+// and expanded again.  This is the "neighbouring site" input class the paper's
+// DMA engine streams (Sec. 3); here it is a coalesced structure-of-arrays gather.
+#pragma once
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+enum Epilogue {
+  EPI_NONE = 0,        // out = D in
+  EPI_CLOVER_INV = 1,  // out = C (D in)            (C = A^-1 of the output parity)
+  EPI_XPAY = 2,        // out = C x + a (D in)      (C = A of the output parity)
+};
+
+struct DslashArgs {
+  Geom g;
+  int p;                   // output parity
+  int nrhs;                // right-hand sides (thread index mod nrhs)
+  const void* gauge;       // gauge field of this precision (both parities)
+  const void* in;          // input field (parity 1-p)
+  const float* in_norm;
+  void* out;               // output field (parity p)
+  float* out_norm;
+  const void* x;           // EPI_XPAY local term (parity p)
+  const float* x_norm;
+  const void* clover;      // clover block field of parity p (A or A^-1)
+  double a;                // EPI_XPAY coefficient on the hopping sum
+  int in_g5;               // apply gamma_5 to the input before hopping
+  int x_g5;                // apply gamma_5 to x before the clover multiply
+  int out_g5;              // apply gamma_5 to the result
+  int do_norm;             // reduce |out|^2 per RHS
+  ReduceArgs red;
+  const int* halt;         // non-null: return immediately when *halt != 0
+};
+
+// Spin projection (1 + sgn g_mu) psi -> half spinor h (spin rows 0 and 1).
+// sgn = -1: forward term (1 - g_mu); sgn = +1: backward term (1 + g_mu).
+template <int MU, int SGN, typename R>
+__device__ __forceinline__ void project(const cx<R> s[12], cx<R> h[6]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const cx<R> s0 = s[a], s1 = s[3 + a], s2 = s[6 + a], s3 = s[9 + a];
+    if (MU == 0) {  // g_x: rows (i s3, i s2, -i s1, -i s0)
+      h[a] = SGN < 0 ? s0 + times_mi(s3) : s0 + times_i(s3);
+      h[3 + a] = SGN < 0 ? s1 + times_mi(s2) : s1 + times_i(s2);
+    } else if (MU == 1) {  // g_y: rows (-s3, s2, s1, -s0)
+      h[a] = SGN < 0 ? s0 + s3 : s0 - s3;
+      h[3 + a] = SGN < 0 ? s1 - s2 : s1 + s2;
+    } else if (MU == 2) {  // g_z: rows (i s2, -i s3, -i s0, i s1)
+      h[a] = SGN < 0 ? s0 + times_mi(s2) : s0 + times_i(s2);
+      h[3 + a] = SGN < 0 ? s1 + times_i(s3) : s1 + times_mi(s3);
+    } else {  // g_t: rows (s2, s3, s0, s1)
+      h[a] = SGN < 0 ? s0 - s2 : s0 + s2;
+      h[3 + a] = SGN < 0 ? s1 - s3 : s1 + s3;
+    }
+  }
+}
+
+// Expand the multiplied half spinor back to four spins and accumulate.
+template <int MU, int SGN, typename R>
+__device__ __forceinline__ void accumulate(const cx<R> h[6], cx<R> acc[12]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    const cx<R> h0 = h[a], h1 = h[3 + a];
+    acc[a] = acc[a] + h0;
+    acc[3 + a] = acc[3 + a] + h1;
+    if (MU == 0) {
+      acc[6 + a] = acc[6 + a] + (SGN < 0 ? times_i(h1) : times_mi(h1));
+      acc[9 + a] = acc[9 + a] + (SGN < 0 ? times_i(h0) : times_mi(h0));
+    } else if (MU == 1) {
+      acc[6 + a] = SGN < 0 ? acc[6 + a] - h1 : acc[6 + a] + h1;
+      acc[9 + a] = SGN < 0 ? acc[9 + a] + h0 : acc[9 + a] - h0;
+    } else if (MU == 2) {
+      acc[6 + a] = acc[6 + a] + (SGN < 0 ? times_i(h0) : times_mi(h0));
+      acc[9 + a] = acc[9 + a] + (SGN < 0 ? times_mi(h1) : times_i(h1));
+    } else {
+      acc[6 + a] = SGN < 0 ? acc[6 + a] - h0 : acc[6 + a] + h0;
+      acc[9 + a] = SGN < 0 ? acc[9 + a] - h1 : acc[9 + a] + h1;
+    }
+  }
+}
+
+// out_a = sum_b U_ab v_b (both half-spinor rows)
+template <typename R>
+__device__ __forceinline__ void su3_mul(const cx<R> u[9], const cx<R> v[6], cx<R> w[6]) {
+#pragma unroll
+  for (int s = 0; s < 2; s++) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<R> acc = u[3 * a] * v[3 * s];
+      acc = cfma(u[3 * a + 1], v[3 * s + 1], acc);
+      acc = cfma(u[3 * a + 2], v[3 * s + 2], acc);
+      w[3 * s + a] = acc;
+    }
+  }
+}
+
+// out_a = sum_b conj(U_ba) v_b
+template <typename R>
+__device__ __forceinline__ void su3_adj_mul(const cx<R> u[9], const cx<R> v[6], cx<R> w[6]) {
+#pragma unroll
+  for (int s = 0; s < 2; s++) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<R> acc = cmk(R(0), R(0));
+      acc = cfmac(u[a], v[3 * s], acc);
+      acc = cfmac(u[3 + a], v[3 * s + 1], acc);
+      acc = cfmac(u[6 + a], v[3 * s + 2], acc);
+      w[3 * s + a] = acc;
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_g5(cx<R> s[12]) {
+#pragma unroll
+  for (int c = 6; c < 12; c++) s[c] = -s[c];
+}
+
+template <int P, int RECON, int MU>
+__device__ __forceinline__ void hop_direction(const DslashArgs& A, const Site& s, int r, cx<typename Real<P>::T> acc[12]) {
+  using R = typename Real<P>::T;
+  const Geom& g = A.g;
+  const int q = 1 - A.p;
+  cx<R> u[9], sp[12], h[6], w[6];
+  // forward: (1 - g_mu) U_mu(x) psi(x + mu)
+  {
+    const int nb = neighbor_fwd(g, s, MU) >> 1;
+    GaugeIO<P, RECON>::load(A.gauge, g.Vh, A.p, MU, s.i >> 1, u);
+    SpinorIO<P>::load(A.in, A.in_norm, g.Vh, r, nb, sp);
+    if (A.in_g5) apply_g5(sp);
+    project<MU, -1>(sp, h);
+    su3_mul(u, h, w);
+    if (MU == 3 && s.t == g.T - 1) {
+      const R sg = R(g.t_bc);
+#pragma unroll
+      for (int k = 0; k < 6; k++) w[k] = sg * w[k];
+    }
+    accumulate<MU, -1>(w, acc);
+  }
+  // backward: (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)
+  {
+    const int nb = neighbor_bwd(g, s, MU) >> 1;
+    GaugeIO<P, RECON>::load(A.gauge, g.Vh, q, MU, nb, u);
+    SpinorIO<P>::load(A.in, A.in_norm, g.Vh, r, nb, sp);
+    if (A.in_g5) apply_g5(sp);
+    project<MU, +1>(sp, h);
+    su3_adj_mul(u, h, w);
+    if (MU == 3 && s.t == 0) {
+      const R sg = R(g.t_bc);
+#pragma unroll
+      for (int k = 0; k < 6; k++) w[k] = sg * w[k];
+    }
+    accumulate<MU, +1>(w, acc);
+  }
+}
+
+template <int P>
+struct CloverPrec;
+template <>
+struct CloverPrec<64> { static constexpr int CP = 64; };
+template <>
+struct CloverPrec<32> { static constexpr int CP = 32; };
+template <>
+struct CloverPrec<16> { static constexpr int CP = 32; };
+
+template <int P, typename R>
+__device__ __forceinline__ void clover_apply(const void* clov, int Vh, int h, const cx<R> in[12], cx<R> out[12]) {
+  CloverIO<CloverPrec<P>::CP>::apply(clov, Vh, h, 0, in, out);
+  CloverIO<CloverPrec<P>::CP>::apply(clov, Vh, h, 1, in + 6, out + 6);
+}
+
+template <int P, int RECON, int EPI, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs A) {
+  using R = typename Real<P>::T;
+  if (A.halt && *A.halt) return;
+  const int gid = blockIdx.x * BLOCK + threadIdx.x;
+  const int r = gid % A.nrhs;
+  const int hh = gid / A.nrhs;
+  const bool valid = hh < A.g.Vh;
+  double nrm = 0.0;
+  if (valid) {
+    const Site s = site_of(A.g, A.p, hh);
+    cx<R> acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
+    hop_direction<P, RECON, 0>(A, s, r, acc);
+    hop_direction<P, RECON, 1>(A, s, r, acc);
+    hop_direction<P, RECON, 2>(A, s, r, acc);
+    hop_direction<P, RECON, 3>(A, s, r, acc);
+    cx<R> res[12];
+    if (EPI == EPI_NONE) {
+#pragma unroll
+      for (int c = 0; c < 12; c++) res[c] = acc[c];
+    } else if (EPI == EPI_CLOVER_INV) {
+      clover_apply<P>(A.clover, A.g.Vh, hh, acc, res);
+    } else {
+      cx<R> xs[12], cxs[12];
+      SpinorIO<P>::load(A.x, A.x_norm, A.g.Vh, r, hh, xs);
+      if (A.x_g5) apply_g5(xs);
+      clover_apply<P>(A.clover, A.g.Vh, hh, xs, cxs);
+      const R a = R(A.a);
+#pragma unroll
+      for (int c = 0; c < 12; c++) {
+        res[c].re = fma(a, acc[c].re, cxs[c].re);
+        res[c].im = fma(a, acc[c].im, cxs[c].im);
+      }
+    }
+    if (A.out_g5) apply_g5(res);
+    SpinorIO<P>::store(A.out, A.out_norm, A.g.Vh, r, hh, res);
+    if (A.do_norm) {
+#pragma unroll
+      for (int c = 0; c < 12; c++) nrm += double(res[c].re) * res[c].re + double(res[c].im) * res[c].im;
+    }
+  }
+  if (A.do_norm) grid_reduce<BLOCK>(nrm, A.nrhs, A.red);
+}
+
+}  // namespace qcd

@@ -1,0 +1,305 @@
+// Fermion force dS/dU for S = phi^dag (Mhat^dag Mhat)^-1 phi, including the
+// derivative of the clover term.
+//
+// The paper's R algorithm (Sec. 1, su3_rmd) evolves the links with this force;
+// the paper gives no formula.  With X = (Mhat^dag Mhat)^-1 phi and Y = Mhat X,
+//   dS = -2 Re[W^dag dA X] + 2 kappa^2 Re[Y^dag dD X]
+// on full-lattice fields X = (X_e, X_o), Y = (Y_e, Y_o), W = (Y_e, kappa^2 Y_o),
+// X_o = A_oo^-1 D_oe X_e, Y_o = A_oo^-1 D_eo^dag Y_e.  Every term has the form
+// Re tr(C dP) for a product P of links; G = dS/dRe U + i dS/dIm U collects, for
+// P = A U B, (B C A)^dag and, for P = A U^dag B, B C A.
+//
+// Two kernels, all in FP64:
+//  1. clover_coeff: per site and plane, C_{mu nu}(x) = -i (kappa c_sw / 4)(S + S^dag)
+//     with S the traceless part of sum_s [sigma_{mu nu} X(x)]_s W(x)_s^dag (summed
+//     over right-hand sides).
+//  2. link_force: per link, the hopping term and the clover leaves through it.
+//     A link l sits in two plaquettes of each of its three planes; each plaquette
+//     contributes one leaf at each of its four corners, and every such leaf is a
+//     cyclic rotation l s1 s2 s3 of the plaquette.  The four corner terms of one
+//     plaquette sum to the staple s1 s2 s3 with the corner's C inserted at each
+//     corner:  c0 s1 s2 s3 + s1 c1 s2 s3 + s1 s2 c2 s3 + s1 s2 s3 c3.
+//     The result is either G or F = -1/2 P_TA(U G^dag).
+#include "qcd_dslash.cuh"
+#include "qcd_force.h"
+#include "qcd_su3.cuh"
+
+namespace qcd {
+
+namespace {
+
+constexpr int FB = 128;
+
+// sigma_{mu nu} X: spin s of the result is coef[s] * X[perm[s]] (DeGrand-Rossi;
+// planes in the order xy xz xt yz yt zt; coef code 0: 1, 1: -1, 2: i, 3: -i)
+__constant__ int SIG_PERM[6][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {1, 0, 3, 2},
+                                   {1, 0, 3, 2}, {1, 0, 3, 2}, {0, 1, 2, 3}};
+__constant__ int SIG_COEF[6][4] = {{0, 1, 0, 1}, {3, 2, 3, 2}, {1, 1, 0, 0},
+                                   {0, 0, 0, 0}, {3, 2, 2, 3}, {1, 0, 0, 1}};
+
+__device__ __forceinline__ C coef_mul(int code, C v) {
+  switch (code) {
+    case 0: return v;
+    case 1: return -v;
+    case 2: return times_i(v);
+    default: return times_mi(v);
+  }
+}
+
+__device__ __forceinline__ void load_spinor64(const double2* f, int Vh, int r, int h, C s[12]) {
+  SpinorIO<64>::load(f, nullptr, Vh, r, h, s);
+}
+
+__device__ __forceinline__ void store_m3(double2* buf, int plane, size_t V, int i, const M3& m) {
+  double2* q = buf + (size_t)plane * 9 * V + i;
+#pragma unroll
+  for (int k = 0; k < 9; k++) q[(size_t)k * V] = make_double2(m.e[k].re, m.e[k].im);
+}
+
+__device__ __forceinline__ M3 load_m3(const double2* buf, int plane, size_t V, int i) {
+  const double2* q = buf + (size_t)plane * 9 * V + i;
+  M3 m;
+#pragma unroll
+  for (int k = 0; k < 9; k++) {
+    double2 v = __ldg(q + (size_t)k * V);
+    m.e[k] = cmk(v.x, v.y);
+  }
+  return m;
+}
+
+__device__ __forceinline__ void lex_coords(const Geom& g, int i, int c[4]) {
+  c[0] = i % g.X;
+  int rest = i / g.X;
+  c[1] = rest % g.Y;
+  rest /= g.Y;
+  c[2] = rest % g.Z;
+  c[3] = rest / g.Z;
+}
+
+__device__ __forceinline__ int lex_index(const Geom& g, int x, int y, int z, int t) {
+  x = wrap(x, g.X);
+  y = wrap(y, g.Y);
+  z = wrap(z, g.Z);
+  t = wrap(t, g.T);
+  return x + g.X * (y + g.Y * (z + g.Z * t));
+}
+
+// 1. C_{mu nu}(x) for the 6 planes at every site
+__global__ void __launch_bounds__(FB) clover_coeff_kernel(Geom g, double kappa, double csw, int nrhs,
+                                                          const double2* Xe, const double2* Xo, const double2* Ye,
+                                                          const double2* Yo, double2* Cbuf) {
+  const int i = blockIdx.x * FB + threadIdx.x;
+  const int V = 2 * g.Vh;
+  if (i >= V) return;
+  int c[4];
+  lex_coords(g, i, c);
+  const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const int h = i >> 1;
+  const double k2 = kappa * kappa;
+  M3 S[6];
+#pragma unroll
+  for (int pl = 0; pl < 6; pl++)
+#pragma unroll
+    for (int k = 0; k < 9; k++) S[pl].e[k] = cmk(0.0, 0.0);
+  for (int r = 0; r < nrhs; r++) {
+    C X[12], W[12];
+    load_spinor64(p == 0 ? Xe : Xo, g.Vh, r, h, X);
+    load_spinor64(p == 0 ? Ye : Yo, g.Vh, r, h, W);
+    if (p == 1) {
+#pragma unroll
+      for (int k = 0; k < 12; k++) W[k] = k2 * W[k];
+    }
+#pragma unroll
+    for (int pl = 0; pl < 6; pl++) {
+#pragma unroll
+      for (int s = 0; s < 4; s++) {
+        const int ps = SIG_PERM[pl][s], cs = SIG_COEF[pl][s];
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+          const C v = coef_mul(cs, X[3 * ps + a]);
+#pragma unroll
+          for (int b = 0; b < 3; b++) S[pl].e[3 * a + b] = cfma(v, conj(W[3 * s + b]), S[pl].e[3 * a + b]);
+        }
+      }
+    }
+  }
+  const double f = kappa * csw / 4.0;
+#pragma unroll
+  for (int pl = 0; pl < 6; pl++) {
+    const double tr = (S[pl].e[0].re + S[pl].e[4].re + S[pl].e[8].re) / 3.0;
+    const double ti = (S[pl].e[0].im + S[pl].e[4].im + S[pl].e[8].im) / 3.0;
+    S[pl].e[0] = S[pl].e[0] - cmk(tr, ti);
+    S[pl].e[4] = S[pl].e[4] - cmk(tr, ti);
+    S[pl].e[8] = S[pl].e[8] - cmk(tr, ti);
+    M3 Cm;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        const C h2 = S[pl].e[3 * a + b] + conj(S[pl].e[3 * b + a]);
+        Cm.e[3 * a + b] = cmk(f * h2.im, -f * h2.re);  // -i f h2
+      }
+    store_m3(Cbuf, pl, V, i, Cm);
+  }
+}
+
+__device__ __forceinline__ void plane_dirs(int pl, int& mu, int& nu) {
+  const int M[6] = {0, 0, 0, 1, 1, 2}, N[6] = {1, 2, 3, 2, 3, 3};
+  mu = M[pl];
+  nu = N[pl];
+}
+
+// sum_s v_s w_s^dag over four spins: M[a][b] = sum_s v[s][a] conj(w[s][b])
+__device__ __forceinline__ void outer_acc(const C v[12], const C w[12], double scale, M3& m) {
+#pragma unroll
+  for (int s = 0; s < 4; s++)
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      const C va = scale * v[3 * s + a];
+#pragma unroll
+      for (int b = 0; b < 3; b++) m.e[3 * a + b] = cfma(va, conj(w[3 * s + b]), m.e[3 * a + b]);
+    }
+}
+
+// (1 + sgn g_mu) v as a full four-spinor
+template <int MU, int SGN>
+__device__ __forceinline__ void spin_project_full(const C v[12], C out[12]) {
+  C h[6];
+  project<MU, SGN>(v, h);
+#pragma unroll
+  for (int k = 0; k < 12; k++) out[k] = cmk(0.0, 0.0);
+  accumulate<MU, SGN>(h, out);
+}
+
+template <int MU>
+__device__ __forceinline__ void hop_terms(const C Xy[12], const C Yy[12], const C Xn[12], const C Yn[12],
+                                          double scale, M3& A, M3& B) {
+  C v[12];
+  spin_project_full<MU, -1>(Xn, v);  // (1 - g) X(y+mu)
+  outer_acc(v, Yy, scale, A);        // G += A^dag
+  spin_project_full<MU, +1>(Xy, v);  // (1 + g) X(y)
+  outer_acc(v, Yn, scale, B);        // G += B
+}
+
+// c0 s1 s2 s3 + s1 c1 s2 s3 + s1 s2 c2 s3 + s1 s2 s3 c3
+__device__ __forceinline__ M3 corner_staple(const M3& s1, const M3& s2, const M3& s3, const M3& c0, const M3& c1,
+                                           const M3& c2, const M3& c3) {
+  const M3 s23 = mul(s2, s3);
+  const M3 q3 = m3_add(mul(c2, s3), mul(s3, c3));
+  const M3 q2 = m3_add(mul(c1, s23), mul(s2, q3));
+  return m3_add(mul(c0, mul(s1, s23)), mul(s1, q2));
+}
+
+// 2. per link (y, lambda): hopping term + the clover leaves through the link
+__global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, int nrhs, const double2* g64,
+                                                        const double2* Xe, const double2* Xo, const double2* Ye,
+                                                        const double2* Yo, const double2* Cbuf, double2* out,
+                                                        int gradient) {
+  const int V = 2 * g.Vh;
+  const long long tid = (long long)blockIdx.x * FB + threadIdx.x;
+  if (tid >= 4LL * V) return;
+  const int lam = (int)(tid / V), i = (int)(tid - (long long)lam * V);
+  int c[4];
+  lex_coords(g, i, c);
+  const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
+  int cl[4] = {c[0], c[1], c[2], c[3]};
+  cl[lam] += 1;
+  const int j = lex_index(g, cl[0], cl[1], cl[2], cl[3]);
+  // hopping part
+  M3 Ah, Bh;
+#pragma unroll
+  for (int k = 0; k < 9; k++) Ah.e[k] = Bh.e[k] = cmk(0.0, 0.0);
+  double sgn = 1.0;
+  if (lam == 3 && c[3] == g.T - 1) sgn = g.t_bc;
+  const double scale = 2.0 * kappa * kappa * sgn;
+  for (int r = 0; r < nrhs; r++) {
+    C Xy[12], Yy[12], Xn[12], Yn[12];
+    load_spinor64(p == 0 ? Xe : Xo, g.Vh, r, i >> 1, Xy);
+    load_spinor64(p == 0 ? Ye : Yo, g.Vh, r, i >> 1, Yy);
+    load_spinor64(p == 0 ? Xo : Xe, g.Vh, r, j >> 1, Xn);
+    load_spinor64(p == 0 ? Yo : Ye, g.Vh, r, j >> 1, Yn);
+    switch (lam) {
+      case 0: hop_terms<0>(Xy, Yy, Xn, Yn, scale, Ah, Bh); break;
+      case 1: hop_terms<1>(Xy, Yy, Xn, Yn, scale, Ah, Bh); break;
+      case 2: hop_terms<2>(Xy, Yy, Xn, Yn, scale, Ah, Bh); break;
+      default: hop_terms<3>(Xy, Yy, Xn, Yn, scale, Ah, Bh); break;
+    }
+  }
+  M3 G = m3_add(m3_dag(Ah), Bh);
+  // clover part: the two plaquettes of each plane containing lambda
+  auto site_off = [&](int d1, int s1, int d2, int s2) {
+    int q[4] = {c[0], c[1], c[2], c[3]};
+    q[d1] += s1;
+    q[d2] += s2;
+    return lex_index(g, q[0], q[1], q[2], q[3]);
+  };
+  auto link_off = [&](int d1, int s1, int d2, int s2, int dir) {
+    int q[4] = {c[0], c[1], c[2], c[3]};
+    q[d1] += s1;
+    q[d2] += s2;
+    return link_at(g, g64, q[0], q[1], q[2], q[3], dir);
+  };
+  for (int pl = 0; pl < 6; pl++) {
+    int mu, nu;
+    plane_dirs(pl, mu, nu);
+    if (mu != lam && nu != lam) continue;
+    auto Cat = [&](int dm, int dn) { return load_m3(Cbuf, pl, V, site_off(mu, dm, nu, dn)); };
+    if (lam == mu) {
+      // plaquette at y: U_mu(y) U_nu(y+mu) U_mu(y+nu)^dag U_nu(y)^dag
+      M3 T = corner_staple(link_off(mu, 1, nu, 0, nu), m3_dag(link_off(mu, 0, nu, 1, mu)),
+                           m3_dag(link_off(mu, 0, nu, 0, nu)), Cat(1, 0), Cat(1, 1), Cat(0, 1), Cat(0, 0));
+      G = m3_add(G, m3_dag(T));
+      // plaquette at y-nu, where the link enters daggered: staple U_nu(y-nu)^dag U_mu(y-nu) U_nu(y+mu-nu)
+      T = corner_staple(m3_dag(link_off(mu, 0, nu, -1, nu)), link_off(mu, 0, nu, -1, mu), link_off(mu, 1, nu, -1, nu),
+                        Cat(0, 0), Cat(0, -1), Cat(1, -1), Cat(1, 0));
+      G = m3_add(G, T);
+    } else {
+      // plaquette at y-mu: staple U_mu(y-mu+nu)^dag U_nu(y-mu)^dag U_mu(y-mu)
+      M3 T = corner_staple(m3_dag(link_off(mu, -1, nu, 1, mu)), m3_dag(link_off(mu, -1, nu, 0, nu)),
+                           link_off(mu, -1, nu, 0, mu), Cat(0, 1), Cat(-1, 1), Cat(-1, 0), Cat(0, 0));
+      G = m3_add(G, m3_dag(T));
+      // plaquette at y, where the link enters daggered: staple U_mu(y) U_nu(y+mu) U_mu(y+nu)^dag
+      T = corner_staple(link_off(mu, 0, nu, 0, mu), link_off(mu, 1, nu, 0, nu), m3_dag(link_off(mu, 0, nu, 1, mu)),
+                        Cat(0, 0), Cat(1, 0), Cat(1, 1), Cat(0, 1));
+      G = m3_add(G, T);
+    }
+  }
+  M3 res;
+  if (gradient) {
+    res = G;
+  } else {
+    // F = -1/2 P_TA(U G^dag)
+    const M3 U = link_at(g, g64, c[0], c[1], c[2], c[3], lam);
+    const M3 M = mul_nd(U, G);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        const C d = M.e[3 * a + b] - conj(M.e[3 * b + a]);
+        res.e[3 * a + b] = cmk(-0.25 * d.re, -0.25 * d.im);
+      }
+    const double ti = (res.e[0].im + res.e[4].im + res.e[8].im) / 3.0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) res.e[4 * a].im -= ti;
+  }
+  double2* q = out + ((size_t)i * 4 + lam) * 9;
+#pragma unroll
+  for (int k = 0; k < 9; k++) q[k] = make_double2(res.e[k].re, res.e[k].im);
+}
+
+}  // namespace
+
+size_t force_clover_bytes(const Geom& g) { return (size_t)6 * 9 * 2 * g.Vh * sizeof(double2); }
+
+void launch_force(const Geom& g, double kappa, double csw, int nrhs, const void* g64, const double2* Xe,
+                  const double2* Xo, const double2* Ye, const double2* Yo, double2* Cbuf, double2* out,
+                  bool gradient, cudaStream_t st) {
+  g_kernel_launches += 2;
+  const int V = 2 * g.Vh;
+  const double2* G = static_cast<const double2*>(g64);
+  clover_coeff_kernel<<<(V + FB - 1) / FB, FB, 0, st>>>(g, kappa, csw, nrhs, Xe, Xo, Ye, Yo, Cbuf);
+  link_force_kernel<<<(int)((4LL * V + FB - 1) / FB), FB, 0, st>>>(g, kappa, nrhs, G, Xe, Xo, Ye, Yo, Cbuf, out,
+                                                                    gradient ? 1 : 0);
+}
+
+}  // namespace qcd

@@ -1,0 +1,22 @@
+// Fermion-force launchers (internal to libqcd).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+extern long long g_kernel_launches;
+
+// bytes of one per-site, per-plane 3x3 complex field over the full lattice (6 planes)
+size_t force_clover_bytes(const Geom& g);
+
+// G or F = -1/2 P_TA(U G^dag) for S = sum_r phi_r^dag (Mhat^dag Mhat)^-1 phi_r, given per RHS
+// the native FP64 fields X_e, X_o = A_oo^-1 D_oe X_e, Y_e = Mhat X_e, Y_o = A_oo^-1 D_eo^dag Y_e.
+// Cbuf: work field of force_clover_bytes; out: canonical [V][4][3][3] complex128.
+void launch_force(const Geom& g, double kappa, double csw, int nrhs, const void* g64, const double2* Xe,
+                  const double2* Xo, const double2* Ye, const double2* Yo, double2* Cbuf, double2* out,
+                  bool gradient, cudaStream_t st);
+
+}  // namespace qcd

@@ -1,0 +1,512 @@
+// Device-side building blocks shared by the CUDA translation units of libqcd:
+// lattice geometry, complex arithmetic, and loaders/storers for the
+// structure-of-arrays field layouts in every precision.
+//
+// Layout (all fields checkerboarded: parity p = (x+y+z+t) mod 2, half index
+// h = i >> 1 of the lexicographic index i = x + X (y + Y (z + Z t)); X even):
+//   spinor FP64 : [rhs][12][Vh] double2     component c = 3*spin + colour
+//   spinor FP32 : [rhs][6][Vh]  float4      two complex components per float4
+//   spinor FP16 : [rhs][3][Vh]  uint4 (8 halves = 4 complex) + [rhs][Vh] float norm
+//   gauge  FP64 : [p][mu][9][Vh] double2    element (i,j) at 3i+j
+//   gauge  FP32 : recon 18 [p][mu][9][Vh] float2, recon 12 [p][mu][3][Vh] float4
+//   gauge  FP16 : recon 18 [p][mu][9][Vh] half2,  recon 12 [p][mu][3][Vh] uint2
+//   clover FP64 : [p][36][Vh] double2, FP32 [p][18][Vh] float4: two chiral
+//                 6x6 Hermitian blocks, each 6 real diagonal + 15 complex
+//                 strictly-lower entries in row-major order.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qcd {
+
+struct Geom {
+  int X, Y, Z, T;
+  int Vh;          // sites of one parity
+  int XY, XYZ;     // lexicographic strides
+  double t_bc;     // factor on U_t(x) at t = T-1 in the hopping term
+};
+
+// ---------------------------------------------------------------- complex ----
+template <typename R>
+struct cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> cmk(R a, R b) { return cx<R>{a, b}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> times_i(cx<R> a) { return {-a.im, a.re}; }
+template <typename R>
+__device__ __forceinline__ cx<R> times_mi(cx<R> a) { return {a.im, -a.re}; }
+// acc + a*b
+template <typename R>
+__device__ __forceinline__ cx<R> cfma(cx<R> a, cx<R> b, cx<R> acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc + conj(a)*b
+template <typename R>
+__device__ __forceinline__ cx<R> cfmac(cx<R> a, cx<R> b, cx<R> acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+template <typename R>
+__device__ __forceinline__ R norm2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+
+// ------------------------------------------------------------- geometry ----
+struct Site {
+  int x, y, z, t;
+  int i;  // lexicographic index
+};
+
+__device__ __forceinline__ Site site_of(const Geom& g, int p, int h) {
+  Site s;
+  int i0 = 2 * h;
+  int rest = i0 / g.X;
+  int x0 = i0 - rest * g.X;
+  s.y = rest % g.Y;
+  rest /= g.Y;
+  s.z = rest % g.Z;
+  s.t = rest / g.Z;
+  s.x = x0 + ((p + s.y + s.z + s.t) & 1);
+  s.i = s.x + g.X * (s.y + g.Y * (s.z + g.Z * s.t));
+  return s;
+}
+
+// lexicographic index of the neighbour x + dir*mu_hat (dir = +1 or -1)
+__device__ __forceinline__ int neighbor_fwd(const Geom& g, const Site& s, int mu) {
+  switch (mu) {
+    case 0: return s.x == g.X - 1 ? s.i - (g.X - 1) : s.i + 1;
+    case 1: return s.y == g.Y - 1 ? s.i - (g.XY - g.X) : s.i + g.X;
+    case 2: return s.z == g.Z - 1 ? s.i - (g.XYZ - g.XY) : s.i + g.XY;
+    default: return s.t == g.T - 1 ? s.i - (g.T - 1) * g.XYZ : s.i + g.XYZ;
+  }
+}
+__device__ __forceinline__ int neighbor_bwd(const Geom& g, const Site& s, int mu) {
+  switch (mu) {
+    case 0: return s.x == 0 ? s.i + (g.X - 1) : s.i - 1;
+    case 1: return s.y == 0 ? s.i + (g.XY - g.X) : s.i - g.X;
+    case 2: return s.z == 0 ? s.i + (g.XYZ - g.XY) : s.i - g.XY;
+    default: return s.t == 0 ? s.i + (g.T - 1) * g.XYZ : s.i - g.XYZ;
+  }
+}
+
+// ------------------------------------------------------------ precision ----
+template <int P>
+struct Real;
+template <>
+struct Real<64> { using T = double; };
+template <>
+struct Real<32> { using T = float; };
+template <>
+struct Real<16> { using T = float; };
+
+// spinor accessors: 12 complex components, component c = 3*spin + colour
+template <int P>
+struct SpinorIO;
+
+template <>
+struct SpinorIO<64> {
+  static constexpr int NVEC = 12;  // double2 per site
+  __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<double> s[12]) {
+    const double2* p = static_cast<const double2*>(base) + (size_t)r * NVEC * Vh + h;
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      double2 v = __ldg(p + (size_t)c * Vh);
+      s[c] = cmk(v.x, v.y);
+    }
+  }
+  __device__ static void store(void* base, float*, int Vh, int r, int h, const cx<double> s[12]) {
+    double2* p = static_cast<double2*>(base) + (size_t)r * NVEC * Vh + h;
+#pragma unroll
+    for (int c = 0; c < 12; c++) p[(size_t)c * Vh] = make_double2(s[c].re, s[c].im);
+  }
+};
+
+template <>
+struct SpinorIO<32> {
+  static constexpr int NVEC = 6;  // float4 per site
+  __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<float> s[12]) {
+    const float4* p = static_cast<const float4*>(base) + (size_t)r * NVEC * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      float4 v = __ldg(p + (size_t)k * Vh);
+      s[2 * k] = cmk(v.x, v.y);
+      s[2 * k + 1] = cmk(v.z, v.w);
+    }
+  }
+  __device__ static void store(void* base, float*, int Vh, int r, int h, const cx<float> s[12]) {
+    float4* p = static_cast<float4*>(base) + (size_t)r * NVEC * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+      p[(size_t)k * Vh] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
+  }
+};
+
+__device__ __forceinline__ float2 h2f(uint32_t u) {
+  __half2 h = *reinterpret_cast<__half2*>(&u);
+  return __half22float2(h);
+}
+__device__ __forceinline__ uint32_t f2h(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// FP16 spinor: each real is stored as half(v / n) with n = max |v| over the site's 24 reals
+template <>
+struct SpinorIO<16> {
+  static constexpr int NVEC = 3;  // uint4 per site
+  __device__ static void load(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
+    const uint4* p = static_cast<const uint4*>(base) + (size_t)r * NVEC * Vh + h;
+    float n = __ldg(nrm + (size_t)r * Vh + h);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint4 v = __ldg(p + (size_t)k * Vh);
+      float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+      s[4 * k + 0] = cmk(a.x * n, a.y * n);
+      s[4 * k + 1] = cmk(b.x * n, b.y * n);
+      s[4 * k + 2] = cmk(c.x * n, c.y * n);
+      s[4 * k + 3] = cmk(d.x * n, d.y * n);
+    }
+  }
+  __device__ static void store(void* base, float* nrm, int Vh, int r, int h, const cx<float> s[12]) {
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < 12; c++) m = fmaxf(m, fmaxf(fabsf(s[c].re), fabsf(s[c].im)));
+    float inv = m > 0.f ? 1.0f / m : 0.f;
+    uint4* p = static_cast<uint4*>(base) + (size_t)r * NVEC * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint4 v;
+      v.x = f2h(s[4 * k + 0].re * inv, s[4 * k + 0].im * inv);
+      v.y = f2h(s[4 * k + 1].re * inv, s[4 * k + 1].im * inv);
+      v.z = f2h(s[4 * k + 2].re * inv, s[4 * k + 2].im * inv);
+      v.w = f2h(s[4 * k + 3].re * inv, s[4 * k + 3].im * inv);
+      p[(size_t)k * Vh] = v;
+    }
+    nrm[(size_t)r * Vh + h] = m;
+  }
+};
+
+// gauge accessors: u[3i+j] = U_ij of the link at (parity p, direction mu, half index h)
+template <typename R>
+__device__ __forceinline__ void reconstruct_row2(cx<R> u[9]) {
+  // row 2 = conj(row 0 x row 1) for a special unitary matrix
+  u[6] = conj(u[1] * u[5] - u[2] * u[4]);
+  u[7] = conj(u[2] * u[3] - u[0] * u[5]);
+  u[8] = conj(u[0] * u[4] - u[1] * u[3]);
+}
+
+template <int P, int RECON>
+struct GaugeIO;
+
+template <>
+struct GaugeIO<64, 18> {
+  static constexpr int NVEC = 9;
+  __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<double> u[9]) {
+    const double2* q = static_cast<const double2*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      double2 v = __ldg(q + (size_t)k * Vh);
+      u[k] = cmk(v.x, v.y);
+    }
+  }
+};
+
+template <>
+struct GaugeIO<32, 18> {
+  static constexpr int NVEC = 9;
+  __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+    const float2* q = static_cast<const float2*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      float2 v = __ldg(q + (size_t)k * Vh);
+      u[k] = cmk(v.x, v.y);
+    }
+  }
+};
+
+template <>
+struct GaugeIO<32, 12> {
+  static constexpr int NVEC = 3;
+  __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+    const float4* q = static_cast<const float4*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      float4 v = __ldg(q + (size_t)k * Vh);
+      u[2 * k] = cmk(v.x, v.y);
+      u[2 * k + 1] = cmk(v.z, v.w);
+    }
+    reconstruct_row2(u);
+  }
+};
+
+template <>
+struct GaugeIO<16, 18> {
+  static constexpr int NVEC = 9;
+  __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+    const uint32_t* q = static_cast<const uint32_t*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      float2 v = h2f(__ldg(q + (size_t)k * Vh));
+      u[k] = cmk(v.x, v.y);
+    }
+  }
+};
+
+template <>
+struct GaugeIO<16, 12> {
+  static constexpr int NVEC = 3;
+  __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+    const uint2* q = static_cast<const uint2*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint2 v = __ldg(q + (size_t)k * Vh);
+      float2 a = h2f(v.x), b = h2f(v.y);
+      u[2 * k] = cmk(a.x, a.y);
+      u[2 * k + 1] = cmk(b.x, b.y);
+    }
+    reconstruct_row2(u);
+  }
+};
+
+// clover accessors: y = A x for chiral block b (x, y: 6 complex, index 3*local_spin + colour)
+template <int CP>
+struct CloverIO;
+
+template <typename R>
+__device__ __forceinline__ void hermitian6_accumulate(const R d[6], const cx<R> L[15], const cx<R> x[6],
+                                                      cx<R> y[6]) {
+#pragma unroll
+  for (int i = 0; i < 6; i++) y[i] = d[i] * x[i];
+  int k = 0;
+#pragma unroll
+  for (int i = 1; i < 6; i++) {
+#pragma unroll
+    for (int j = 0; j < i; j++) {
+      y[i] = cfma(L[k], x[j], y[i]);
+      y[j] = cfmac(L[k], x[i], y[j]);
+      k++;
+    }
+  }
+}
+
+template <>
+struct CloverIO<64> {
+  static constexpr int NVEC = 36;  // double2 per site
+  __device__ static void apply(const void* c, int Vh, int h, int b, const cx<double> x[6], cx<double> y[6]) {
+    const double2* q = static_cast<const double2*>(c) + (size_t)(b * 18) * Vh + h;
+    double d[6];
+    cx<double> L[15];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      double2 v = __ldg(q + (size_t)k * Vh);
+      d[2 * k] = v.x;
+      d[2 * k + 1] = v.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 15; k++) {
+      double2 v = __ldg(q + (size_t)(3 + k) * Vh);
+      L[k] = cmk(v.x, v.y);
+    }
+    hermitian6_accumulate(d, L, x, y);
+  }
+};
+
+template <>
+struct CloverIO<32> {
+  static constexpr int NVEC = 18;  // float4 per site
+  __device__ static void apply(const void* c, int Vh, int h, int b, const cx<float> x[6], cx<float> y[6]) {
+    const float4* q = static_cast<const float4*>(c) + (size_t)(b * 9) * Vh + h;
+    float f[36];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      float4 v = __ldg(q + (size_t)k * Vh);
+      f[4 * k] = v.x;
+      f[4 * k + 1] = v.y;
+      f[4 * k + 2] = v.z;
+      f[4 * k + 3] = v.w;
+    }
+    float d[6];
+    cx<float> L[15];
+#pragma unroll
+    for (int k = 0; k < 6; k++) d[k] = f[k];
+#pragma unroll
+    for (int k = 0; k < 15; k++) L[k] = cmk(f[6 + 2 * k], f[7 + 2 * k]);
+    hermitian6_accumulate(d, L, x, y);
+  }
+};
+
+// ---------------------------------------------------------- CG control ----
+// Per right-hand side state of the CG iteration, resident in device memory so
+// that the iteration runs without host round trips.
+struct CGState {
+  double rr;            // |r|^2 of the iterated residual
+  double rr_prev;       // |r|^2 one iteration earlier
+  double rr_reliable;   // |r|^2 at the last reliable update
+  double pAp;           // <p, A p> = |Mhat p|^2
+  double alpha, beta;
+  double tol2;          // stop when |r|^2 <= tol2 (= tol^2 |b|^2)
+  double bnorm2;
+  double true_rr;       // last true residual |b - A x|^2 (FP64)
+  int active;           // 1 until converged
+  int iters;
+  int since_reliable;
+  int pending;          // reliable update requested
+  int reliable_updates;
+  int pad_;
+};
+
+struct CGControl {
+  int halt;             // set when any RHS wants a reliable update or on error
+  int nan;              // non-finite reduction or breakdown
+  int reliable_every;
+  int pad_;
+  double delta2;        // reliable update when |r|^2 < delta2 * rr_reliable
+};
+
+enum FinalizeMode {
+  FIN_STORE = 0,     // result[r] = total
+  FIN_CG_PAP = 1,    // alpha = rr / pAp
+  FIN_CG_RR = 2,     // new |r|^2, beta, reliable-update and convergence triggers
+  FIN_CG_TRUE = 3,   // true residual after a reliable update
+};
+
+struct ReduceArgs {
+  double* partials;        // [nrhs][gridDim.x]
+  unsigned int* counter;   // zero before the launch; the last block resets it
+  double* result;          // [nrhs], FIN_STORE
+  int mode;
+  CGState* cg;
+  CGControl* ctl;
+};
+
+// Per-RHS action of the last block once the grid-wide total is known.
+__device__ __forceinline__ void finalize_total(const ReduceArgs& ra, int r, double total) {
+  switch (ra.mode) {
+    case FIN_STORE:
+      ra.result[r] = total;
+      break;
+    case FIN_CG_PAP: {
+      CGState& s = ra.cg[r];
+      s.pAp = total;
+      if (s.active) {
+        if (!(total > 0.0) || !isfinite(total)) {
+          ra.ctl->nan = 1;
+          ra.ctl->halt = 1;
+          s.alpha = 0.0;
+        } else {
+          s.alpha = s.rr / total;
+        }
+      } else {
+        s.alpha = 0.0;
+      }
+      break;
+    }
+    case FIN_CG_RR: {
+      CGState& s = ra.cg[r];
+      if (!s.active) break;
+      if (!isfinite(total)) {
+        ra.ctl->nan = 1;
+        ra.ctl->halt = 1;
+        break;
+      }
+      s.rr_prev = s.rr;
+      s.beta = total / s.rr;
+      s.rr = total;
+      s.iters += 1;
+      s.since_reliable += 1;
+      bool want = total <= s.tol2 || s.since_reliable >= ra.ctl->reliable_every ||
+                  total < ra.ctl->delta2 * s.rr_reliable;
+      if (want) {
+        s.pending = 1;
+        ra.ctl->halt = 1;
+      }
+      break;
+    }
+    case FIN_CG_TRUE: {
+      CGState& s = ra.cg[r];
+      if (!isfinite(total)) {
+        ra.ctl->nan = 1;
+        break;
+      }
+      s.true_rr = total;
+      if (!s.active) break;
+      s.beta = s.rr_prev > 0.0 ? total / s.rr_prev : 0.0;
+      s.rr = total;
+      s.rr_reliable = total;
+      s.since_reliable = 0;
+      s.pending = 0;
+      s.reliable_updates += 1;
+      if (total <= s.tol2) s.active = 0;
+      break;
+    }
+  }
+}
+
+// Grid-wide deterministic sum of one double per thread, per right-hand side
+// (rhs = global thread index mod nrhs; nrhs divides 32, blockDim a multiple of
+// 32).  Warp shuffles, then shared memory, then per-block partials; the last
+// block to finish sums the partials in a fixed order and runs finalize_total.
+template <int BLOCK>
+__device__ __forceinline__ void grid_reduce(double v, int nrhs, const ReduceArgs& ra) {
+  __shared__ double sm[BLOCK / 32][8];
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int off = 16; off >= nrhs; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if (lane < nrhs) sm[warp][lane] = v;
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double s = 0.0;
+#pragma unroll 1
+    for (int w = 0; w < BLOCK / 32; w++) s += sm[w][threadIdx.x];
+    ra.partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int ticket = atomicAdd(ra.counter, 1u);
+    is_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int r = 0; r < nrhs; r++) {
+    double s = 0.0;
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += BLOCK) s += __ldcg(ra.partials + (size_t)r * gridDim.x + j);
+    for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    __syncthreads();
+    if (lane == 0) sm[warp][0] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < BLOCK / 32; w++) tot += sm[w][0];
+      finalize_total(ra, r, tot);
+    }
+  }
+  if (threadIdx.x == 0) *ra.counter = 0u;
+}
+
+}  // namespace qcd

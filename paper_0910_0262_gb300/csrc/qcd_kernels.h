@@ -1,0 +1,58 @@
+// Host-side launchers of the CUDA kernels (internal to libqcd; not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qcd_internal.cuh"
+
+namespace qcd {
+
+// kernels launched by the library since the last reset (profiling)
+extern long long g_kernel_launches;
+
+// ---- layout (qcd_layout.cu)
+void launch_pack_gauge(const Geom& g, const double2* canon, void* g64, void* g32, int recon32, void* g16,
+                       int recon16, cudaStream_t st);
+void launch_spinor_to_native(int prec, const Geom& g, const double2* canon, void* nat, float* norm, int nrhs,
+                             cudaStream_t st);
+void launch_spinor_to_canon(int prec, const Geom& g, const void* nat, const float* norm, double2* canon, int nrhs,
+                            cudaStream_t st);
+void launch_check_finite(const double* data, size_t n, int* flag, cudaStream_t st);
+
+// ---- clover (qcd_clover.cu)
+// A (both parities) and A^-1 (both parities) in FP64 and FP32; flag set if a block is not positive definite.
+void launch_clover_build(const Geom& g, const void* g64, double kappa, double csw, void* A64, void* Ainv64,
+                         void* A32, void* Ainv32, int* notposdef, cudaStream_t st);
+// out = C in for a site-local clover field C of parity-matched fields
+void launch_clover_apply(int prec, const Geom& g, const void* clover, const void* in, const float* in_norm,
+                         void* out, float* out_norm, int nrhs, cudaStream_t st);
+
+// ---- hopping term (qcd_dslash.cu)
+struct DslashArgs;
+void launch_dslash(int prec, int recon, int epi, const DslashArgs& a, cudaStream_t st);
+int dslash_block();
+
+// ---- BLAS-1 and CG steps (qcd_blas.cu)
+int blas_block();
+int blas_grid(const Geom& g, int nrhs);
+// x += alpha p ; r -= alpha Ap ; |r|^2 -> FIN_CG_RR
+void launch_cg_update(int prec_r, int prec_p, const Geom& g, int nrhs, void* x, float* xn, void* r, float* rn,
+                      const void* p, const float* pn, const void* Ap, const float* Apn, const ReduceArgs& red,
+                      const int* halt, cudaStream_t st);
+// p = r + beta p
+void launch_p_update(int prec_r, int prec_p, const Geom& g, int nrhs, const void* r, const float* rn, void* p,
+                     float* pn, const CGState* cg, const int* halt, cudaStream_t st);
+// x_hi += x_lo ; x_lo = 0
+void launch_accumulate_x(int prec_r, const Geom& g, int nrhs, double2* x_hi, void* x_lo, float* x_lon,
+                         cudaStream_t st);
+// r_lo = b - Ap_hi ; |b - Ap_hi|^2 -> reduction (FIN_CG_TRUE)
+void launch_true_residual(int prec_r, const Geom& g, int nrhs, const double2* b, const double2* Ap, void* r_lo,
+                          float* r_lon, const ReduceArgs& red, cudaStream_t st);
+// |v|^2 (FP64 native) -> reduction
+void launch_norm2(const Geom& g, int nrhs, const double2* v, const ReduceArgs& red, cudaStream_t st);
+// Re <a, b> (FP64 native) -> reduction
+void launch_redot(const Geom& g, int nrhs, const double2* a, const double2* b, const ReduceArgs& red,
+                  cudaStream_t st);
+void launch_zero(void* ptr, size_t bytes, cudaStream_t st);
+
+}  // namespace qcd

@@ -1,0 +1,287 @@
+"""Python binding of libqcd (include/qcd.h): argument marshalling only.
+
+Every step of the operator, the solver and the force runs in the CUDA library;
+this module passes torch tensors' device pointers and the context's stream
+through ctypes.  There is no fallback: if ``libqcd.so`` is missing or no GPU is
+present, the calls raise.
+
+``qcd_*`` functions mirror the C ABI one to one; ``CloverWilson`` is a thin
+owner of a ``qcd_ctx`` working on torch tensors; ``CloverPseudofermionAction``
+is the torch.autograd.Function S(U, phi) = phi^dag (Mhat^dag Mhat)^-1 phi whose
+backward is the fermion force.
+"""
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqcd.so")
+
+QCD_OK = 0
+STATUS = {0: "QCD_OK", 1: "QCD_ERR_ARG", 2: "QCD_ERR_CUDA", 3: "QCD_ERR_NOMEM", 4: "QCD_ERR_STATE",
+          5: "QCD_ERR_NOT_POSDEF", 6: "QCD_ERR_NOT_CONVERGED", 7: "QCD_ERR_NAN", 8: "QCD_ERR_TIMEOUT"}
+
+QCD_GAUGE_RECON12 = 1
+QCD_OP_DSLASH_EO, QCD_OP_DSLASH_OE, QCD_OP_MHAT, QCD_OP_MDAGM, QCD_OP_CLOVER, QCD_OP_CLOVER_INV = range(6)
+QCD_FORCE_INPUT_IS_SOLUTION = 1
+QCD_FORCE_GRADIENT = 2
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("inner_prec", ctypes.c_int),
+                ("reliable_every", ctypes.c_int), ("reliable_delta", ctypes.c_double), ("use_x0", ctypes.c_int)]
+
+
+class SolverStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int), ("true_rel_resid", ctypes.c_double),
+                ("b_dot_x", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+class QCDError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+        self.status = status
+        self.message = message
+
+
+_lib = None
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "qcd_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int), ctypes.c_double, _P]),
+    "qcd_destroy": (ctypes.c_int, [_P]),
+    "qcd_load_gauge": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int]),
+    "qcd_clover_build": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double]),
+    "qcd_dslash": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "qcd_cg_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(SolverParams),
+                                    ctypes.POINTER(SolverStats)]),
+    "qcd_fermion_force": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(SolverParams),
+                                         ctypes.POINTER(SolverStats)]),
+    "qcd_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "qcd_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "qcd_last_error": (ctypes.c_char_p, []),
+}
+
+
+def lib():
+    """Load libqcd.so (built in-tree by ``paper_0910_0262_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libqcd.so is not built; run `python -m paper_0910_0262_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != QCD_OK:
+        raise QCDError(status, lib().qcd_last_error().decode())
+    return status
+
+
+# ---- one-to-one wrappers of the C ABI ---------------------------------------------------------------------
+def qcd_create(dims, t_bc=-1.0, stream=None):
+    ctx = _P()
+    d = (ctypes.c_int * 4)(*dims)
+    _check(lib().qcd_create(ctypes.byref(ctx), d, float(t_bc), stream))
+    return ctx
+
+
+def qcd_destroy(ctx):
+    return _check(lib().qcd_destroy(ctx))
+
+
+def qcd_load_gauge(ctx, U_ptr, on_device, flags=0):
+    return _check(lib().qcd_load_gauge(ctx, U_ptr, int(on_device), int(flags)))
+
+
+def qcd_clover_build(ctx, kappa, csw):
+    return _check(lib().qcd_clover_build(ctx, float(kappa), float(csw)))
+
+
+def qcd_dslash(ctx, out_ptr, in_ptr, op, dagger, precision, nrhs):
+    return _check(lib().qcd_dslash(ctx, out_ptr, in_ptr, int(op), int(dagger), int(precision), int(nrhs)))
+
+
+def qcd_cg_solve(ctx, x_ptr, b_ptr, nrhs, params, stats):
+    """Returns the status (QCD_OK or QCD_ERR_NOT_CONVERGED); raises on other errors."""
+    s = lib().qcd_cg_solve(ctx, x_ptr, b_ptr, int(nrhs), ctypes.byref(params), stats)
+    if s not in (QCD_OK, 6):
+        _check(s)
+    return s
+
+
+def qcd_fermion_force(ctx, F_ptr, in_ptr, nrhs, flags, params, stats):
+    s = lib().qcd_fermion_force(ctx, F_ptr, in_ptr, int(nrhs), int(flags),
+                                ctypes.byref(params) if params is not None else None, stats)
+    if s not in (QCD_OK, 6):
+        _check(s)
+    return s
+
+
+def qcd_profile(ctx, enable):
+    return _check(lib().qcd_profile(ctx, int(enable)))
+
+
+def qcd_profile_read(ctx, max_entries=64):
+    arr = (KernelStat * max_entries)()
+    n = ctypes.c_int(0)
+    _check(lib().qcd_profile_read(ctx, arr, max_entries, ctypes.byref(n)))
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "total_ms": arr[i].total_ms,
+             "bytes": arr[i].bytes, "flops": arr[i].flops} for i in range(n.value)]
+
+
+def qcd_last_error():
+    return lib().qcd_last_error().decode()
+
+
+def solver_params(tol=1e-8, max_iter=20000, inner_prec=32, reliable_every=50, reliable_delta=0.1, use_x0=False):
+    return SolverParams(float(tol), int(max_iter), int(inner_prec), int(reliable_every), float(reliable_delta),
+                        int(bool(use_x0)))
+
+
+# ---- torch-facing owner of a context ----------------------------------------------------------------------
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class CloverWilson:
+    """Owns one qcd_ctx for a lattice dims = (X, Y, Z, T) on the current CUDA device and stream."""
+
+    def __init__(self, dims, t_bc=-1.0, stream=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqcd needs a CUDA device")
+        self.dims = tuple(int(d) for d in dims)
+        X, Y, Z, T = self.dims
+        self.V = X * Y * Z * T
+        self.Vh = self.V // 2
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.ctx = qcd_create(self.dims, t_bc, ctypes.c_void_p(self.stream.cuda_stream))
+        self.kappa = None
+        self.csw = None
+
+    def close(self):
+        if self.ctx is not None:
+            qcd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _spinor(self, t, nrhs=None):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("fields must be contiguous complex128 CUDA tensors")
+        if t.numel() % (self.Vh * 12):
+            raise ValueError("field size is not a multiple of V/2 * 12")
+        return t.numel() // (self.Vh * 12)
+
+    def load_gauge(self, U, recon12=False):
+        """U: complex128 [T, Z, Y, X, 4, 3, 3] on the GPU (device copy) or on the CPU (host copy)."""
+        if U.dtype != torch.complex128 or not U.is_contiguous() or U.numel() != self.V * 36:
+            raise ValueError("U must be a contiguous complex128 tensor of V*4*9 elements")
+        qcd_load_gauge(self.ctx, _ptr(U), U.is_cuda, QCD_GAUGE_RECON12 if recon12 else 0)
+
+    def clover_build(self, kappa, csw):
+        qcd_clover_build(self.ctx, kappa, csw)
+        self.kappa, self.csw = float(kappa), float(csw)
+
+    def dslash(self, x, op, dagger=False, precision=64):
+        n = self._spinor(x)
+        out = torch.empty_like(x)
+        qcd_dslash(self.ctx, _ptr(out), _ptr(x), op, dagger, precision, n)
+        return out
+
+    def cg_solve(self, b, x0=None, **kw):
+        """Solve Mhat^dag Mhat x = b; returns (x, [stats dict per RHS], converged)."""
+        n = self._spinor(b)
+        x = torch.zeros_like(b) if x0 is None else x0.clone()
+        prm = solver_params(use_x0=x0 is not None, **kw)
+        st = (SolverStats * n)()
+        s = qcd_cg_solve(self.ctx, _ptr(x), _ptr(b), n, prm, st)
+        return x, [st[i].as_dict() for i in range(n)], s == QCD_OK
+
+    def fermion_force(self, phi_or_x, input_is_solution=False, gradient=False, **kw):
+        """Force (or Wirtinger gradient) [T, Z, Y, X, 4, 3, 3] summed over the RHS of phi_or_x."""
+        n = self._spinor(phi_or_x)
+        X, Y, Z, T = self.dims
+        F = torch.empty((T, Z, Y, X, 4, 3, 3), dtype=torch.complex128, device=phi_or_x.device)
+        flags = (QCD_FORCE_INPUT_IS_SOLUTION if input_is_solution else 0) | (QCD_FORCE_GRADIENT if gradient else 0)
+        prm = None if input_is_solution else solver_params(**kw)
+        st = (SolverStats * n)()
+        qcd_fermion_force(self.ctx, _ptr(F), _ptr(phi_or_x), n, flags, prm, st)
+        return F, [st[i].as_dict() for i in range(n)]
+
+    def profile(self, enable=True):
+        qcd_profile(self.ctx, enable)
+
+    def profile_read(self):
+        return qcd_profile_read(self.ctx)
+
+
+class CloverPseudofermionAction(torch.autograd.Function):
+    """S(U, phi) = sum_i phi_i^dag (Mhat[U]^dag Mhat[U])^-1 phi_i and its gradients.
+
+    forward(U, phi, op, kappa, csw, solver_kw, recompute): loads U into the
+    CloverWilson context op, builds the clover term, solves (mixed or FP64
+    precision per solver_kw) and returns S as a 0-d float64 tensor computed from
+    the library's FP64 <phi, X>.  backward returns dS/dU as the Wirtinger
+    gradient G = dS/dRe U + i dS/dIm U (torch's convention for a real loss of a
+    complex input) from the library's force kernels, and dS/dphi = 2 X.  With
+    recompute=True the solution X is not kept between forward and backward; the
+    backward solves again.
+    """
+
+    @staticmethod
+    def forward(ctx, U, phi, op, kappa, csw, solver_kw=None, recompute=False):
+        solver_kw = dict(solver_kw or {})
+        op.load_gauge(U.detach().contiguous(), recon12=solver_kw.pop("recon12", False))
+        op.clover_build(kappa, csw)
+        x, stats, ok = op.cg_solve(phi.detach().contiguous(), **solver_kw)
+        if not ok:
+            raise QCDError(6, "CG did not converge in the action's forward solve")
+        S = sum(s["b_dot_x"] for s in stats)
+        ctx.op = op
+        ctx.solver_kw = solver_kw
+        ctx.recompute = recompute
+        ctx.kappa, ctx.csw = kappa, csw
+        if recompute:
+            ctx.save_for_backward(U, phi)
+        else:
+            ctx.save_for_backward(U, phi, x)
+        return torch.tensor(S, dtype=torch.float64, device=U.device)
+
+    @staticmethod
+    def backward(ctx, gS):
+        op = ctx.op
+        saved = ctx.saved_tensors
+        U, phi = saved[0], saved[1]
+        op.load_gauge(U.detach().contiguous())
+        op.clover_build(ctx.kappa, ctx.csw)
+        if ctx.recompute:
+            x, _, ok = op.cg_solve(phi.detach().contiguous(), **ctx.solver_kw)
+            if not ok:
+                raise QCDError(6, "CG did not converge in the recomputation")
+        else:
+            x = saved[2]
+        G, _ = op.fermion_force(x, input_is_solution=True, gradient=True)
+        gU = gS * G if ctx.needs_input_grad[0] else None
+        gphi = gS * 2.0 * x if ctx.needs_input_grad[1] else None
+        return gU, gphi, None, None, None, None, None

@@ -1,0 +1,65 @@
+"""The C ABI library builds for sm_103a, loads, and exports every symbol include/qcd.h declares.
+
+These run without a GPU: they make no compute call.  Argument checks that the
+library performs before touching the device are exercised too.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libqcd():
+    from paper_0910_0262_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "qcd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(qcd_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("qcd_create", "qcd_destroy", "qcd_load_gauge", "qcd_clover_build", "qcd_dslash",
+              "qcd_cg_solve", "qcd_fermion_force", "qcd_last_error"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(libqcd):
+    for n in declared_functions():
+        assert hasattr(libqcd, n), n
+
+
+def test_binding_names_match_the_abi():
+    from paper_0910_0262_gb300 import qcd
+    for n in declared_functions():
+        assert n in qcd._SIGNATURES, n
+        assert callable(getattr(qcd, n)), n
+
+
+def test_create_rejects_bad_extents_without_a_device(libqcd):
+    from paper_0910_0262_gb300 import qcd
+    for dims in [(3, 4, 4, 4), (4, 4, 4, 0), (4, 4, 5, 4)]:
+        with pytest.raises(qcd.QCDError) as e:
+            qcd.qcd_create(dims, -1.0, None)
+        assert e.value.status == 1
+        assert "even" in e.value.message
+    with pytest.raises(qcd.QCDError) as e:
+        qcd.qcd_create((4, 4, 4, 4), 0.5, None)
+    assert e.value.status == 1
+
+
+def test_null_context_is_an_argument_error(libqcd):
+    from paper_0910_0262_gb300 import qcd
+    L = qcd.lib()
+    assert L.qcd_clover_build(None, 0.12, 1.0) == 1
+    assert L.qcd_destroy(None) == 0
+    assert "null" in qcd.qcd_last_error()

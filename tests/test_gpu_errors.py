@@ -1,0 +1,111 @@
+"""Error paths of the C ABI on the GPU.  No test faults, traps or hangs the GPU: every
+failure is produced by arguments or inputs that the library checks itself."""
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_0910_0262_gb300 import synth
+from gpu_util import require_gpu, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    require_gpu()
+    from paper_0910_0262_gb300 import qcd
+    return qcd
+
+
+def test_state_errors(Q):
+    c = Q.CloverWilson((4, 4, 4, 4))
+    x = torch.zeros((1, 128, 4, 3), dtype=torch.complex128, device="cuda")
+    with pytest.raises(Q.QCDError) as e:
+        c.dslash(x, Q.QCD_OP_DSLASH_EO)
+    assert e.value.status == 4
+    with pytest.raises(Q.QCDError) as e:
+        c.clover_build(0.12, 1.0)
+    assert e.value.status == 4
+    U, _ = synth.make_problem((4, 4, 4, 4), 0.2, 1)
+    c.load_gauge(to_dev(U))
+    c.dslash(x, Q.QCD_OP_DSLASH_EO)  # hopping alone needs no clover
+    with pytest.raises(Q.QCDError) as e:
+        c.dslash(x, Q.QCD_OP_MHAT)
+    assert e.value.status == 4
+    with pytest.raises(Q.QCDError) as e:
+        c.cg_solve(x)
+    assert e.value.status == 4
+
+
+def test_argument_errors(Q):
+    c = Q.CloverWilson((4, 4, 4, 4))
+    U, _ = synth.make_problem((4, 4, 4, 4), 0.2, 1)
+    c.load_gauge(to_dev(U))
+    c.clover_build(0.12, 1.0)
+    x = torch.zeros((1, 128, 4, 3), dtype=torch.complex128, device="cuda")
+    L = Q.lib()
+    p = ctypes.c_void_p(x.data_ptr())
+    assert L.qcd_dslash(c.ctx, p, p, 2, 0, 64, 1) == 1          # in == out
+    assert L.qcd_dslash(c.ctx, None, p, 2, 0, 64, 1) == 1       # null
+    y = torch.zeros_like(x)
+    q = ctypes.c_void_p(y.data_ptr())
+    assert L.qcd_dslash(c.ctx, q, p, 99, 0, 64, 1) == 1         # op
+    assert L.qcd_dslash(c.ctx, q, p, 2, 0, 24, 1) == 1          # precision
+    assert L.qcd_dslash(c.ctx, q, p, 2, 0, 64, 0) == 1          # nrhs
+    prm = Q.solver_params(tol=-1.0)
+    assert L.qcd_cg_solve(c.ctx, q, p, 1, ctypes.byref(prm), None) == 1
+    assert L.qcd_load_gauge(c.ctx, p, 1, 0x10) == 1             # flags
+
+
+def test_not_positive_definite(Q):
+    c = Q.CloverWilson((4, 4, 4, 4))
+    U, _ = synth.make_problem((4, 4, 4, 4), 1.5, 3)
+    c.load_gauge(to_dev(U))
+    with pytest.raises(Q.QCDError) as e:
+        c.clover_build(1.0, 40.0)
+    assert e.value.status == 5
+
+
+def test_not_converged_writes_best_x(Q):
+    c = Q.CloverWilson((4, 4, 4, 4))
+    U, b = synth.make_problem((4, 4, 4, 4), 0.2, 3)
+    c.load_gauge(to_dev(U))
+    c.clover_build(0.12, 1.0)
+    x, stats, ok = c.cg_solve(to_dev(b), max_iter=3, inner_prec=32)
+    assert not ok
+    assert 0 < stats[0]["true_rel_resid"] < 1.0
+    assert torch.count_nonzero(x) > 0
+
+
+def test_nan_inputs(Q):
+    c = Q.CloverWilson((4, 4, 4, 4))
+    U, b = synth.make_problem((4, 4, 4, 4), 0.2, 3)
+    Ubad = U.copy()
+    Ubad[1, 2, 3, 0, 2, 1, 1] = np.nan
+    with pytest.raises(Q.QCDError) as e:
+        c.load_gauge(to_dev(Ubad))
+    assert e.value.status == 7
+    c.load_gauge(to_dev(U))
+    c.clover_build(0.12, 1.0)
+    bb = b.copy()
+    bb[0, 5, 1, 2] = np.inf
+    with pytest.raises(Q.QCDError) as e:
+        c.cg_solve(to_dev(bb))
+    assert e.value.status == 7
+    # the context stays usable
+    x, stats, ok = c.cg_solve(to_dev(b))
+    assert ok
+
+
+def test_host_gauge_pointer_matches_device(Q):
+    dims = (4, 2, 2, 4)
+    U, b = synth.make_problem(dims, 0.2, 4)
+    c1 = Q.CloverWilson(dims)
+    c1.load_gauge(to_dev(U))
+    c2 = Q.CloverWilson(dims)
+    c2.load_gauge(torch.from_numpy(U.copy()))
+    xb = to_dev(b)
+    assert torch.equal(c1.dslash(xb, Q.QCD_OP_DSLASH_OE), c2.dslash(xb, Q.QCD_OP_DSLASH_OE))

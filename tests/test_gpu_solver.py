@@ -1,0 +1,67 @@
+"""CG on Mhat^dag Mhat x = b on the GPU: FP64, mixed FP32 and mixed FP16 (with FP64
+reliable updates), several right-hand sides.  Every solution must have a true
+relative residual <= 1e-8 recomputed by the FP64 oracle's operator."""
+
+import numpy as np
+import pytest
+
+from oracle import evenodd, cg as ocg
+from paper_0910_0262_gb300 import synth
+from gpu_util import require_gpu, to_dev, to_np, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+KAPPA, CSW = 0.12, 1.0
+
+
+@pytest.fixture(scope="module")
+def problem():
+    require_gpu()
+    from paper_0910_0262_gb300.qcd import CloverWilson
+    dims = (6, 6, 4, 8)
+    U, b = synth.make_problem(dims, 0.2, 11, nrhs=3)
+    ref = evenodd.SchurOperator(U, KAPPA, CSW, -1.0)
+    c = CloverWilson(dims, -1.0)
+    c.load_gauge(to_dev(U), recon12=True)
+    c.clover_build(KAPPA, CSW)
+    return dims, U, b, ref, c
+
+
+def true_residual(ref, x, b):
+    return np.linalg.norm((b - ref.MdagM(x)).reshape(-1)) / np.linalg.norm(b.reshape(-1))
+
+
+@pytest.mark.parametrize("inner", [64, 32, 16])
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_cg_true_residual(problem, inner, nrhs):
+    dims, U, b, ref, c = problem
+    bb = b[:nrhs]
+    x, stats, ok = c.cg_solve(to_dev(bb), tol=1e-8, inner_prec=inner, max_iter=5000)
+    assert ok
+    x = to_np(x)
+    xo, it, res = ocg.cg(ref.MdagM, bb[0], tol=1e-10)
+    for r in range(nrhs):
+        tr = true_residual(ref, x[r], bb[r])
+        assert tr <= 1e-8 * (1 + 1e-6), (inner, r, tr)
+        assert stats[r]["true_rel_resid"] <= 1e-8
+        assert abs(stats[r]["true_rel_resid"] - tr) <= 1e-12
+        assert stats[r]["iters"] > 0
+        S = float(np.vdot(bb[r], x[r]).real)
+        assert abs(stats[r]["b_dot_x"] - S) <= 1e-12 * abs(S)
+    assert rel_l2(x[0], xo) < 1e-5
+
+
+def test_cg_from_initial_guess(problem):
+    dims, U, b, ref, c = problem
+    x0, _, ok = c.cg_solve(to_dev(b[:1]), tol=1e-10, inner_prec=64)
+    assert ok
+    x, stats, ok = c.cg_solve(to_dev(b[:1]), x0=x0, tol=1e-8, inner_prec=32)
+    assert ok and stats[0]["iters"] == 0
+    assert true_residual(ref, to_np(x)[0], b[0]) <= 1e-8
+
+
+def test_cg_zero_source(problem):
+    dims, U, b, ref, c = problem
+    z = np.zeros_like(b[:1])
+    x, stats, ok = c.cg_solve(to_dev(z), inner_prec=32)
+    assert ok and np.all(to_np(x) == 0) and stats[0]["iters"] == 0
