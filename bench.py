@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--only", default=None, choices=[None, "dslash"],
+                    help="dslash: only apply Mhat^dag Mhat (FP32 and FP64) a few times, for profiler captures")
     return ap.parse_args()
 
 
@@ -373,9 +375,33 @@ def run_reference(args, world, rank):
 WORKLOAD_ITERS = 300
 
 
+def run_dslash_only(args):
+    """Load the workload's links, build the clover term, apply Mhat^dag Mhat in FP32 (12-real links)
+    and FP64 `steps` times each; prints a one-line JSON summary (for profiler captures)."""
+    import torch
+    from paper_0910_0262_gb300 import synth, build
+    from paper_0910_0262_gb300 import qcd as Q
+    build.build()
+    w = workload_params(args.workload)
+    U_np, b_np = synth.make_problem(w["dims"], w["eps"], w["seed"], w["nrhs"])
+    op = Q.CloverWilson(w["dims"], w["t_bc"])
+    op.load_gauge(torch.from_numpy(U_np).cuda(), recon12=True)
+    op.clover_build(w["kappa"], w["csw"])
+    b = torch.from_numpy(b_np).cuda()
+    for prec in (32, 64):
+        for _ in range(args.steps):
+            y = op.dslash(b, Q.QCD_OP_MDAGM, precision=prec)
+    torch.cuda.synchronize()
+    print(json.dumps({"only": "dslash", "workload": args.workload, "applications": args.steps,
+                      "norm": float(torch.linalg.vector_norm(y).item())}))
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
+    if args.only == "dslash":
+        run_dslash_only(args)
+        return
     if args.impl == "reference":
         if rank == 0:
             print(json.dumps(run_reference(args, world, rank)))
