@@ -181,6 +181,29 @@ typedef struct {
 /* Copy up to max_entries kernel classes into out (synchronises the stream). */
 qcd_status qcd_profile_read(qcd_ctx* ctx, qcd_kernel_stat* out, int max_entries, int* n_entries);
 
+/*
+ * qcd_mhat_static -- out = Mhat in (dagger = 1: Mhat^dag in) in FP64 for one
+ * even-site field, allocating no device memory.  The paper has no counterpart:
+ * this entry exists for callers that cannot call cudaMalloc, such as a host
+ * application whose memory pool already holds the GPU's free memory, or a
+ * latency-sensitive loop that cannot take the device-wide synchronisation that
+ * cudaMalloc / cudaFree may cause.  (qcd_dslash, by contrast, allocates its work
+ * buffers on first use.)
+ *
+ * in, out: device complex128 [V/2][4][3] (canonical layout), not overlapping.
+ * Work space is one file-scope device array of QCD_STATIC_SCRATCH_BYTES that every
+ * GPU loading the library holds until exit; lattices needing more than
+ * 3 * 192 * V/2 bytes of it are rejected with QCD_ERR_ARG before any launch.  The
+ * first call on a device looks up the array's device address for that device
+ * (make it before any stream capture).  All calls share the array, which keeps
+ * the last call's contents (each call writes everything it reads); calls whose
+ * work overlaps on the GPU race on it.  Needs qcd_load_gauge and
+ * qcd_clover_build (QCD_ERR_STATE otherwise).  Enqueued on the context's stream;
+ * returns without synchronising.
+ */
+#define QCD_STATIC_SCRATCH_BYTES (24u << 20)
+qcd_status qcd_mhat_static(qcd_ctx* ctx, double* out, const double* in, int dagger);
+
 /* Message describing the last failed call on this thread ("" if none). */
 const char* qcd_last_error(void);
 

@@ -316,6 +316,37 @@ int batch_of(int n) {
 
 }  // namespace
 
+// Read-only view of a context and the thread's error message, for entry points defined in other
+// translation units of the library.
+namespace qcd {
+struct CtxView {
+  Geom g;
+  cudaStream_t st;
+  int device;
+  const void* g64;
+  const void* A_even64;
+  const void* Ainv_odd64;
+  double kappa;
+  bool have_gauge, have_clover;
+};
+
+bool ctx_view(const qcd_ctx* c, CtxView* v) {
+  if (!c) return false;
+  v->g = c->g;
+  v->st = c->st;
+  v->device = c->device;
+  v->g64 = c->g64;
+  v->A_even64 = c->A64 ? clover_ptr(c, 64, false, 0) : nullptr;
+  v->Ainv_odd64 = c->Ainv64 ? clover_ptr(c, 64, true, 1) : nullptr;
+  v->kappa = c->kappa;
+  v->have_gauge = c->have_gauge;
+  v->have_clover = c->have_clover;
+  return true;
+}
+
+qcd_status set_error(qcd_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace qcd
+
 // ===================================================================== ABI ==
 extern "C" {
 

@@ -68,6 +68,7 @@ _SIGNATURES = {
                                          ctypes.POINTER(SolverStats)]),
     "qcd_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "qcd_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "qcd_mhat_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -143,6 +144,11 @@ def qcd_profile_read(ctx, max_entries=64):
     _check(lib().qcd_profile_read(ctx, arr, max_entries, ctypes.byref(n)))
     return [{"name": arr[i].name.decode(), "launches": arr[i].launches, "total_ms": arr[i].total_ms,
              "bytes": arr[i].bytes, "flops": arr[i].flops} for i in range(n.value)]
+
+
+def qcd_mhat_static(ctx, out_ptr, in_ptr, dagger=0):
+    """Mhat (or Mhat^dag) in FP64 on one field with no device allocation (see include/qcd.h)."""
+    return _check(lib().qcd_mhat_static(ctx, out_ptr, in_ptr, int(dagger)))
 
 
 def qcd_last_error():
