@@ -7,6 +7,7 @@
 // scalars in device memory (alpha, beta, |r|^2 are produced by the reducing
 // kernels themselves), so the host only looks at the solver state once per
 // chunk of iterations and when a reliable update is due.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -68,6 +69,40 @@ struct ProfPending {
   double bytes, flops;
 };
 
+
+struct SolverFields {
+  int pr, pp;  // precision of x_lo/r_lo and of p/Ap/temporaries
+  double2 *b_hi, *x_hi, *ap_hi, *t_hi, *y_hi;
+  void *x_lo, *r_lo, *p, *ap, *t, *y;
+  float *x_lo_n, *r_lo_n, *p_n, *ap_n, *t_n, *y_n;
+};
+
+// one profiled launch inside a captured graph: an event pair recorded by the graph itself
+struct ProfSlot {
+  int cls;
+  cudaEvent_t a, b;
+  double bytes, flops;
+  int iter;  // CG iteration inside the graph (-1: always runs)
+};
+
+// an instantiated CUDA graph of CG work for one set of solver fields
+struct ItGraph {
+  int kind = 0;  // 0: `len` CG iterations; 1: one reliable update
+  int len = 0, nrhs = 0;
+  bool prof = false;
+  SolverFields f;
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+  std::vector<cudaEvent_t> events;
+  std::vector<ProfSlot> slots;
+};
+
+struct CaptureSink {
+  ItGraph* g;
+  int iter;
+  size_t next;
+};
+
 }  // namespace
 
 struct qcd_ctx {
@@ -106,6 +141,13 @@ struct qcd_ctx {
   std::vector<ProfClass> prof;
   std::vector<ProfPending> pending;
   std::vector<cudaEvent_t> ev_free;
+  // launch stream of the moment (the caller's stream, or the capture stream while a graph is recorded)
+  cudaStream_t cur = nullptr;
+  cudaStream_t cap = nullptr;
+  CaptureSink* sink = nullptr;
+  std::vector<ItGraph*> graphs;
+  std::vector<std::pair<ItGraph*, int>> launched;  // graphs launched since the last collection, with iteration offset
+  double last_rho = 0.0;                            // per-iteration |r|^2 ratio seen by the last solve
 };
 
 namespace {
@@ -165,15 +207,29 @@ struct ProfScope {
   int cls = -1;
   double bytes, flops;
   ProfScope(qcd_ctx* c_, const char* name, double bytes_, double flops_) : c(c_), bytes(bytes_), flops(flops_) {
+    if (c->sink) {
+      // recording a graph: the event pair becomes two event-record nodes of the graph
+      if (!c->sink->g->prof) return;
+      cls = prof_class(c, name);
+      a = c->sink->g->events[c->sink->next++];
+      cudaEventRecordWithFlags(a, c->cur, cudaEventRecordExternal);
+      return;
+    }
     if (!c->prof_on) return;
     cls = prof_class(c, name);
     a = prof_event(c);
-    cudaEventRecord(a, c->st);
+    cudaEventRecord(a, c->cur);
   }
   ~ProfScope() {
-    if (!c->prof_on || cls < 0) return;
+    if (cls < 0) return;
+    if (c->sink) {
+      cudaEvent_t b = c->sink->g->events[c->sink->next++];
+      cudaEventRecordWithFlags(b, c->cur, cudaEventRecordExternal);
+      c->sink->g->slots.push_back(ProfSlot{cls, a, b, bytes, flops, c->sink->iter});
+      return;
+    }
     cudaEvent_t b = prof_event(c);
-    cudaEventRecord(b, c->st);
+    cudaEventRecord(b, c->cur);
     c->pending.push_back(ProfPending{a, b, cls, bytes, flops});
   }
 };
@@ -237,7 +293,7 @@ void run_dslash(qcd_ctx* c, int prec, int epi, const DslashArgs& a) {
   snprintf(name, sizeof name, "dslash_p%d_r%d_%s", prec, prec == 64 ? 18 : c->recon,
            epi == EPI_NONE ? "plain" : (epi == EPI_CLOVER_INV ? "cloverinv" : "xpay"));
   ProfScope ps(c, name, bytes, flops);
-  launch_dslash(prec, prec == 64 ? 18 : c->recon, epi, a, c->st);
+  launch_dslash(prec, prec == 64 ? 18 : c->recon, epi, a, c->cur);
 }
 
 ReduceArgs reduce_args(qcd_ctx* c, int mode) {
@@ -366,6 +422,7 @@ qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* strea
   qcd_ctx* c = new qcd_ctx();
   c->device = dev;
   c->st = static_cast<cudaStream_t>(stream);
+  c->cur = c->st;
   c->g.X = dims[0];
   c->g.Y = dims[1];
   c->g.Z = dims[2];
@@ -392,6 +449,11 @@ qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* strea
   }
   cudaMemset(c->counter, 0, sizeof(unsigned));
   cudaMemset(c->flags, 0, 4 * sizeof(int));
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    qcd_destroy(c);
+    return fail(QCD_ERR_CUDA, "capture stream creation failed");
+  }
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     qcd_destroy(c);
@@ -420,6 +482,12 @@ qcd_status qcd_destroy(qcd_ctx* c) {
     cudaEventDestroy(p.b);
   }
   for (auto e : c->ev_free) cudaEventDestroy(e);
+  for (ItGraph* gph : c->graphs) {
+    if (gph->exec) cudaGraphExecDestroy(gph->exec);
+    for (auto e : gph->events) cudaEventDestroy(e);
+    delete gph;
+  }
+  if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
   return QCD_OK;
 }
@@ -557,12 +625,7 @@ qcd_status qcd_dslash(qcd_ctx* c, double* out, const double* in, int op, int dag
 // ============================================================ CG driver ==
 namespace {
 
-struct SolverFields {
-  int pr, pp;  // precision of x_lo/r_lo and of p/Ap/temporaries
-  double2 *b_hi, *x_hi, *ap_hi, *t_hi, *y_hi;
-  void *x_lo, *r_lo, *p, *ap, *t, *y;
-  float *x_lo_n, *r_lo_n, *p_n, *ap_n, *t_n, *y_n;
-};
+
 
 qcd_status solver_fields(qcd_ctx* c, int inner, int nrhs, SolverFields* f) {
   const Geom& g = c->g;
@@ -602,21 +665,196 @@ void update_cost(const Geom& g, int pr, int pp, int nrhs, double* bytes) {
   *bytes = (double)g.Vh * nrhs * (4 * sr + 2 * sp);
 }
 
-// one reliable update: x_hi += x_lo, r = b - A x_hi in FP64, p = r + beta p
-void reliable_update(qcd_ctx* c, const SolverFields& f, int nrhs) {
+// --- work of one CG iteration and of one reliable update, enqueued on c->cur ---------------------
+
+// Mhat^dag Mhat p (|Mhat p|^2 -> alpha), x += alpha p, r -= alpha Ap (|r|^2 -> beta and the
+// reliable-update / convergence triggers), p = r + beta p.  Every kernel returns at once while
+// ctl->halt is set, so iterations enqueued past a trigger cost only their launch.
+void enqueue_iteration(qcd_ctx* c, const SolverFields& f, int nrhs) {
   const Geom& g = c->g;
-  launch_accumulate_x(f.pr, g, nrhs, f.x_hi, f.x_lo, f.x_lo_n, c->st);
+  const int* halt = &c->ctl->halt;
+  ReduceArgs red_pap = reduce_args(c, FIN_CG_PAP);
+  ReduceArgs red_rr = reduce_args(c, FIN_CG_RR);
+  apply_mdagm(c, f.pp, nrhs, f.p, f.p_n, f.ap, f.ap_n, f.t, f.t_n, f.y, f.y_n, &red_pap, halt);
+  double ub;
+  update_cost(g, f.pr, f.pp, nrhs, &ub);
+  {
+    ProfScope ps(c, "cg_update", ub, 0);
+    launch_cg_update(f.pr, f.pp, g, nrhs, f.x_lo, f.x_lo_n, f.r_lo, f.r_lo_n, f.p, f.p_n, f.ap, f.ap_n, red_rr, halt,
+                     c->cur);
+  }
+  {
+    const double pb = (double)g.Vh * nrhs * (24.0 * real_bytes(f.pr) + 2 * (24.0 * real_bytes(f.pp) + (f.pp == 16 ? 4 : 0)));
+    ProfScope ps(c, "p_update", pb, 0);
+    launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, halt, c->cur);
+  }
+}
+
+// x_hi += x_lo, r = b - Mhat^dag Mhat x_hi in FP64 (true residual, convergence test, halt cleared
+// unless every RHS is done), p = r + beta p.
+void enqueue_reliable(qcd_ctx* c, const SolverFields& f, int nrhs) {
+  const Geom& g = c->g;
+  launch_accumulate_x(f.pr, g, nrhs, f.x_hi, f.x_lo, f.x_lo_n, c->cur);
   apply_mdagm(c, 64, nrhs, f.x_hi, nullptr, f.ap_hi, nullptr, f.t_hi, nullptr, f.y_hi, nullptr, nullptr, nullptr);
-  ReduceArgs red = reduce_args(c, FIN_CG_TRUE);
-  launch_true_residual(f.pr, g, nrhs, f.b_hi, f.ap_hi, f.r_lo, f.r_lo_n, red, c->st);
-  launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->st);
-  cudaMemsetAsync(&c->ctl->halt, 0, sizeof(int), c->st);
+  launch_true_residual(f.pr, g, nrhs, f.b_hi, f.ap_hi, f.r_lo, f.r_lo_n, reduce_args(c, FIN_CG_TRUE), c->cur);
+  launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->cur);
+}
+
+// --- CUDA graphs of that work ----------------------------------------------------------------------
+
+const int MAX_GRAPH_LEN = 64;
+
+qcd_status capture_graph(qcd_ctx* c, ItGraph* gph) {
+  if (gph->prof) {
+    const size_t need = gph->kind == 0 ? (size_t)12 * gph->len : 14;
+    while (gph->events.size() < need) {
+      cudaEvent_t e;
+      CUDA_TRY(cudaEventCreate(&e));
+      gph->events.push_back(e);
+    }
+  }
+  gph->slots.clear();
+  CaptureSink sink{gph, -1, 0};
+  const long long k0 = g_kernel_launches;
+  c->cur = c->cap;
+  c->sink = &sink;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (gph->kind == 0) {
+      for (int j = 0; j < gph->len; j++) {
+        sink.iter = j;
+        enqueue_iteration(c, gph->f, gph->nrhs);
+      }
+    } else {
+      enqueue_reliable(c, gph->f, gph->nrhs);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(c->cap, &graph);
+    if (e == cudaSuccess) {
+      e = cudaGraphInstantiate(&gph->exec, graph, 0);
+      cudaGraphDestroy(graph);
+    }
+  }
+  c->sink = nullptr;
+  c->cur = c->st;
+  gph->kernels = g_kernel_launches - k0;
+  g_kernel_launches = k0;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    gph->exec = nullptr;
+    return fail(QCD_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  return QCD_OK;
+}
+
+// cached graph for (kind, len) on these fields, recorded on first use
+qcd_status get_graph(qcd_ctx* c, int kind, int len, const SolverFields& f, int nrhs, ItGraph** out) {
+  for (ItGraph* gph : c->graphs) {
+    if (gph->kind == kind && gph->len == len && gph->nrhs == nrhs && gph->prof == c->prof_on &&
+        memcmp(&gph->f, &f, sizeof f) == 0) {
+      *out = gph;
+      return QCD_OK;
+    }
+  }
+  ItGraph* gph = new ItGraph();
+  gph->kind = kind;
+  gph->len = len;
+  gph->nrhs = nrhs;
+  gph->prof = c->prof_on;
+  gph->f = f;
+  qcd_status s = capture_graph(c, gph);
+  if (s) {
+    delete gph;
+    return s;
+  }
+  c->graphs.push_back(gph);
+  *out = gph;
+  return QCD_OK;
+}
+
+qcd_status launch_graph(qcd_ctx* c, ItGraph* gph, int iter_offset) {
+  CUDA_TRY(cudaGraphLaunch(gph->exec, c->st));
+  g_kernel_launches += gph->kernels;
+  if (gph->prof) c->launched.push_back({gph, iter_offset});
+  return QCD_OK;
+}
+
+// after a synchronisation: fold the event pairs of the graphs launched since the last call into the
+// kernel classes, counting only CG iterations that ran (the first `real_iters` of the segment)
+void collect_graphs(qcd_ctx* c, int real_iters) {
+  for (auto& lg : c->launched) {
+    for (const ProfSlot& sl : lg.first->slots) {
+      if (sl.iter >= 0 && lg.second + sl.iter >= real_iters) continue;
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, sl.a, sl.b) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      ProfClass& pc = c->prof[sl.cls];
+      pc.launches += 1;
+      pc.ms += ms;
+      pc.bytes += sl.bytes;
+      pc.flops += sl.flops;
+    }
+  }
+  c->launched.clear();
+}
+
+// n CG iterations as graphs of power-of-two lengths (each length at most once, so that a profiled
+// graph's events are read before they are recorded again)
+qcd_status launch_iterations(qcd_ctx* c, const SolverFields& f, int nrhs, int n) {
+  int offset = 0;
+  for (int len = MAX_GRAPH_LEN; len >= 1; len >>= 1) {
+    if (n & len) {
+      ItGraph* gph;
+      qcd_status s = get_graph(c, 0, len, f, nrhs, &gph);
+      if (s) return s;
+      if ((s = launch_graph(c, gph, offset))) return s;
+      offset += len;
+    }
+  }
+  return QCD_OK;
 }
 
 qcd_status read_state(qcd_ctx* c, int nrhs) {
   cudaMemcpyAsync(c->h_cg, c->cg, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, c->st);
   cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(CGControl), cudaMemcpyDeviceToHost, c->st);
   return sync_and_check(c, "cg state");
+}
+
+// Iterations to enqueue before the next look at the solver state: the fewest, over the active
+// right-hand sides, until a reliable-update trigger (|r| down by reliable_delta since the last
+// update, reliable_every iterations, or the target residual), predicted from the per-iteration
+// ratio rho of |r|^2 seen so far.  One extra iteration is added: overshooting costs a few
+// empty launches, undershooting a host round trip.
+int predict_iterations(const qcd_ctx* c, int nrhs, const std::vector<double>& rho, bool after_reliable) {
+  const CGControl& ctl = *c->h_ctl;
+  long long best = 1LL << 30;
+  for (int r = 0; r < nrhs; r++) {
+    const CGState& st = c->h_cg[r];
+    if (!st.active) continue;
+    const int since = after_reliable ? 0 : st.since_reliable;
+    long long n = (long long)ctl.reliable_every - since;
+    const double rh = rho[r];
+    if (rh > 0.0 && rh < 1.0) {
+      const double lr = log(rh);
+      if (ctl.delta2 > 0.0) {
+        const long long k = (long long)ceil(log(ctl.delta2) / lr) - since;
+        if (k < n) n = k;
+      }
+      if (st.rr > 0.0 && st.tol2 > 0.0) {
+        const long long k = (long long)ceil(log(st.tol2 / st.rr) / lr) - (after_reliable ? 0 : 0);
+        if (k < n) n = k;
+      }
+    } else if (n > 8) {
+      n = 8;
+    }
+    if (n < best) best = n;
+  }
+  if (best < 1) best = 1;
+  best += 1;
+  if (best > 2 * MAX_GRAPH_LEN - 1) best = 2 * MAX_GRAPH_LEN - 1;
+  return (int)best;
 }
 
 // Solve for one batch of nrhs (1, 2, 4 or 8) canonical fields.
@@ -626,32 +864,25 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
   SolverFields f;
   qcd_status s = solver_fields(c, prm->inner_prec, nrhs, &f);
   if (s) return s;
-  // b_hi and |b|^2
-  launch_spinor_to_native(64, g, b, f.b_hi, nullptr, nrhs, c->st);
-  launch_norm2(g, nrhs, f.b_hi, reduce_args(c, FIN_STORE), c->st);
-  CUDA_TRY(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
-  if ((s = sync_and_check(c, "cg init"))) return s;
-  bool any = false;
+  const bool mixed = prm->inner_prec != 64;
   for (int r = 0; r < nrhs; r++) {
-    if (!std::isfinite(c->h_results[r])) return fail(QCD_ERR_NAN, "source %d holds a non-finite value", r);
     CGState st;
     memset(&st, 0, sizeof st);
-    st.bnorm2 = c->h_results[r];
-    st.tol2 = prm->tol * prm->tol * st.bnorm2;
-    st.active = st.bnorm2 > 0.0 ? 1 : 0;
+    st.tol2 = prm->tol * prm->tol;  // scaled by |b|^2 on the device
+    st.active = 1;
     st.reliable_updates = -1;
-    any |= st.active != 0;
     c->h_cg[r] = st;
   }
   CGControl ctl;
   memset(&ctl, 0, sizeof ctl);
-  const bool mixed = prm->inner_prec != 64;
   ctl.reliable_every = mixed ? (prm->reliable_every > 0 ? prm->reliable_every : 50) : (1 << 30);
   ctl.delta2 = mixed ? prm->reliable_delta * prm->reliable_delta : 0.0;
   *c->h_ctl = ctl;
   CUDA_TRY(cudaMemcpyAsync(c->cg, c->h_cg, sizeof(CGState) * nrhs, cudaMemcpyHostToDevice, c->st));
   CUDA_TRY(cudaMemcpyAsync(c->ctl, c->h_ctl, sizeof(CGControl), cudaMemcpyHostToDevice, c->st));
-  // x_hi, x_lo = 0, p = 0, Ap_hi = A x0
+  // b_hi, |b|^2 (tolerance, zero sources), x_hi = x0 or 0, x_lo = 0, p = 0, r = b - A x_hi, p = r
+  launch_spinor_to_native(64, g, b, f.b_hi, nullptr, nrhs, c->st);
+  launch_norm2(g, nrhs, f.b_hi, reduce_args(c, FIN_CG_BNORM), c->st);
   if (prm->use_x0) launch_spinor_to_native(64, g, x, f.x_hi, nullptr, nrhs, c->st);
   else launch_zero(f.x_hi, spinor_bytes(g, 64, nrhs), c->st);
   launch_zero(f.x_lo, spinor_bytes(g, f.pr, nrhs), c->st);
@@ -663,22 +894,30 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
     launch_zero(f.ap_hi, spinor_bytes(g, 64, nrhs), c->st);
   launch_true_residual(f.pr, g, nrhs, f.b_hi, f.ap_hi, f.r_lo, f.r_lo_n, reduce_args(c, FIN_CG_TRUE), c->st);
   launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->st);
-  if ((s = read_state(c, nrhs))) return s;
 
-  const int* halt = &c->ctl->halt;
-  ReduceArgs red_pap = reduce_args(c, FIN_CG_PAP);
-  ReduceArgs red_rr = reduce_args(c, FIN_CG_RR);
-  double ub;
-  update_cost(g, f.pr, f.pp, nrhs, &ub);
-  int chunk = 8;
+  std::vector<double> rho(nrhs, c->last_rho);
   qcd_status result = QCD_OK;
+  bool after_reliable = true;
+  int done_iters = 0;
+  ItGraph* rel = nullptr;
   while (true) {
-    bool active = false;
+    // the state is only known after a synchronisation; right after the set-up or a reliable
+    // update the host copy is stale, which predict_iterations accounts for
+    const int n = std::min(predict_iterations(c, nrhs, rho, after_reliable), std::max(1, prm->max_iter - done_iters));
+    if ((s = launch_iterations(c, f, nrhs, n))) return s;
+    if ((s = read_state(c, nrhs))) return s;
     int max_it = 0;
+    bool active = false, candidate = false;
     for (int r = 0; r < nrhs; r++) {
-      active |= c->h_cg[r].active != 0;
-      if (c->h_cg[r].iters > max_it) max_it = c->h_cg[r].iters;
+      const CGState& st = c->h_cg[r];
+      max_it = std::max(max_it, st.iters);
+      active |= st.active != 0;
+      candidate |= st.active && st.pending && st.rr <= st.tol2;
+      if (st.active && st.since_reliable > 0 && st.rr_reliable > 0.0 && st.rr > 0.0)
+        rho[r] = pow(st.rr / st.rr_reliable, 1.0 / st.since_reliable);
     }
+    if (c->prof_on) collect_graphs(c, max_it - done_iters);
+    done_iters = max_it;
     if (c->h_ctl->nan) {
       result = fail(QCD_ERR_NAN, "non-finite value or breakdown in CG");
       break;
@@ -688,32 +927,36 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
       result = fail(QCD_ERR_NOT_CONVERGED, "CG did not converge in %d iterations", prm->max_iter);
       break;
     }
+    after_reliable = false;
     if (c->h_ctl->halt) {
-      reliable_update(c, f, nrhs);
-      if ((s = read_state(c, nrhs))) return s;
-      continue;
-    }
-    const int n = chunk < prm->max_iter - max_it ? chunk : prm->max_iter - max_it;
-    for (int k = 0; k < n; k++) {
-      apply_mdagm(c, f.pp, nrhs, f.p, f.p_n, f.ap, f.ap_n, f.t, f.t_n, f.y, f.y_n, &red_pap, halt);
-      {
-        ProfScope ps(c, "cg_update", ub, 0);
-        launch_cg_update(f.pr, f.pp, g, nrhs, f.x_lo, f.x_lo_n, f.r_lo, f.r_lo_n, f.p, f.p_n, f.ap, f.ap_n, red_rr,
-                         halt, c->st);
+      if (!rel && (s = get_graph(c, 1, 0, f, nrhs, &rel))) return s;
+      if ((s = launch_graph(c, rel, 0))) return s;
+      after_reliable = true;
+      if (candidate) {
+        // the update may have finished the solve: look before enqueuing more iterations
+        if ((s = read_state(c, nrhs))) return s;
+        if (c->prof_on) collect_graphs(c, 0);
+        bool any = false;
+        for (int r = 0; r < nrhs; r++) any |= c->h_cg[r].active != 0;
+        if (c->h_ctl->nan) {
+          result = fail(QCD_ERR_NAN, "non-finite value in the reliable update");
+          break;
+        }
+        if (!any) break;
       }
-      launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, halt, c->st);
     }
-    if ((s = read_state(c, nrhs))) return s;
-    if (chunk < 32) chunk *= 2;
   }
+  for (int r = 0; r < nrhs; r++)
+    if (rho[r] > 0.0 && rho[r] < 1.0) c->last_rho = rho[r];
   // not converged: fold the progress into x and recompute the true residual for the stats
-  if (result == QCD_ERR_NOT_CONVERGED) reliable_update(c, f, nrhs);
+  if (result == QCD_ERR_NOT_CONVERGED) enqueue_reliable(c, f, nrhs);
   // fold the last low-precision increment into x and write out
   launch_accumulate_x(f.pr, g, nrhs, f.x_hi, f.x_lo, f.x_lo_n, c->st);
   launch_spinor_to_canon(64, g, f.x_hi, nullptr, x, nrhs, c->st);
   launch_redot(g, nrhs, f.b_hi, f.x_hi, reduce_args(c, FIN_STORE), c->st);
   CUDA_TRY(cudaMemcpyAsync(c->h_results, c->results, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->st));
   if ((s = read_state(c, nrhs))) return s;
+  if (c->prof_on) collect_graphs(c, 0);
   if (stats) {
     for (int r = 0; r < nrhs; r++) {
       const CGState& st = c->h_cg[r];

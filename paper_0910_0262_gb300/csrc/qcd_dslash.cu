@@ -2,13 +2,34 @@
 #include "qcd_dslash.cuh"
 #include "qcd_kernels.h"
 
+#include <cstdlib>
+
 namespace qcd {
 
 namespace {
 constexpr int DB = 128;  // threads per block of the hopping kernels
 
+// 1: direction-split kernel (default); 0: one site per thread (QCD_DSLASH_SPLIT=0)
+int split_mode() {
+  static int mode = -1;
+  if (mode < 0) {
+    const char* e = getenv("QCD_DSLASH_SPLIT");
+    mode = (e && e[0] == '0') ? 0 : 1;
+  }
+  return mode;
+}
+
 template <int P, int RECON>
 void launch_epi(int epi, const DslashArgs& a, cudaStream_t st) {
+  if (split_mode()) {
+    const int nb = (a.g.Vh * a.nrhs + 31) / 32;
+    switch (epi) {
+      case EPI_NONE: dslash_split_kernel<P, RECON, EPI_NONE><<<nb, 128, 0, st>>>(a); break;
+      case EPI_CLOVER_INV: dslash_split_kernel<P, RECON, EPI_CLOVER_INV><<<nb, 128, 0, st>>>(a); break;
+      default: dslash_split_kernel<P, RECON, EPI_XPAY><<<nb, 128, 0, st>>>(a); break;
+    }
+    return;
+  }
   const int nb = (a.g.Vh * a.nrhs + DB - 1) / DB;
   switch (epi) {
     case EPI_NONE: dslash_kernel<P, RECON, EPI_NONE, DB><<<nb, DB, 0, st>>>(a); break;

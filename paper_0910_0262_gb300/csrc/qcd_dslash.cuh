@@ -224,4 +224,105 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs A) {
   if (A.do_norm) grid_reduce<BLOCK>(nrm, A.nrhs, A.red);
 }
 
+// Direction-split variant: a block of 128 threads handles 32 (site, RHS) pairs; warp w
+// computes the two hops along mu = w for its lane's pair (uniform per warp, no divergence), the
+// four partial sums meet in shared memory, warps 0 and 1 finish chiral block 0 and 1 (sum,
+// clover epilogue, gamma_5, norm), and the warps share the stores.  Four times the threads of
+// the one-site-per-thread kernel, so small lattices fill the GPU and each thread keeps fewer
+// live registers.
+template <int P, int RECON, int EPI>
+__global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
+  using R = typename Real<P>::T;
+  __shared__ cx<R> part[4][12][32];
+  if (A.halt && *A.halt) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int pair = blockIdx.x * 32 + lane;
+  const int r = pair % A.nrhs;
+  const int hh = pair / A.nrhs;
+  const bool valid = hh < A.g.Vh;
+  {
+    cx<R> acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
+    if (valid) {
+      const Site s = site_of(A.g, A.p, hh);
+      switch (w) {
+        case 0: hop_direction<P, RECON, 0>(A, s, r, acc); break;
+        case 1: hop_direction<P, RECON, 1>(A, s, r, acc); break;
+        case 2: hop_direction<P, RECON, 2>(A, s, r, acc); break;
+        default: hop_direction<P, RECON, 3>(A, s, r, acc); break;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 12; c++) part[w][c][lane] = acc[c];
+  }
+  __syncthreads();
+  double nrm = 0.0;
+  if (w < 2 && valid) {
+    const int b = w;
+    cx<R> v[6], res[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const int c = 6 * b + k;
+      v[k] = (part[0][c][lane] + part[1][c][lane]) + (part[2][c][lane] + part[3][c][lane]);
+    }
+    if (EPI == EPI_NONE) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = v[k];
+    } else if (EPI == EPI_CLOVER_INV) {
+      CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, v, res);
+    } else {
+      cx<R> xs[6], cxs[6];
+      SpinorIO<P>::load_block(A.x, A.x_norm, A.g.Vh, r, hh, b, xs);
+      if (A.x_g5 && b == 1) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) xs[k] = -xs[k];
+      }
+      CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, xs, cxs);
+      const R a = R(A.a);
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        res[k].re = fma(a, v[k].re, cxs[k].re);
+        res[k].im = fma(a, v[k].im, cxs[k].im);
+      }
+    }
+    if (A.out_g5 && b == 1) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = -res[k];
+    }
+    if (A.do_norm) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) nrm += double(res[k].re) * res[k].re + double(res[k].im) * res[k].im;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; k++) part[0][6 * b + k][lane] = res[k];
+  }
+  __syncthreads();
+  if (valid) {
+    if (P == 64) {
+      double2* q = static_cast<double2*>(A.out) + (size_t)r * 12 * A.g.Vh + hh;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const cx<R> v = part[0][3 * w + k][lane];
+        q[(size_t)(3 * w + k) * A.g.Vh] = make_double2(double(v.re), double(v.im));
+      }
+    } else if (P == 32) {
+      if (w < 3) {
+        float4* q = static_cast<float4*>(A.out) + (size_t)r * 6 * A.g.Vh + hh;
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+          const cx<R> v0 = part[0][4 * w + 2 * k][lane], v1 = part[0][4 * w + 2 * k + 1][lane];
+          q[(size_t)(2 * w + k) * A.g.Vh] = make_float4(float(v0.re), float(v0.im), float(v1.re), float(v1.im));
+        }
+      }
+    } else if (w == 0) {
+      cx<float> o[12];
+#pragma unroll
+      for (int c = 0; c < 12; c++) o[c] = cmk(float(part[0][c][lane].re), float(part[0][c][lane].im));
+      SpinorIO<16>::store(A.out, A.out_norm, A.g.Vh, r, hh, o);
+    }
+  }
+  if (A.do_norm) grid_reduce<128>(nrm, A.nrhs, A.red);
+}
+
 }  // namespace qcd

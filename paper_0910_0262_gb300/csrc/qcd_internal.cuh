@@ -143,6 +143,15 @@ struct SpinorIO<64> {
 #pragma unroll
     for (int c = 0; c < 12; c++) p[(size_t)c * Vh] = make_double2(s[c].re, s[c].im);
   }
+  // components 6b..6b+5 (chiral block b: spins 2b, 2b+1)
+  __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b, cx<double> s[6]) {
+    const double2* p = static_cast<const double2*>(base) + (size_t)r * NVEC * Vh + (size_t)(6 * b) * Vh + h;
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+      double2 v = __ldg(p + (size_t)c * Vh);
+      s[c] = cmk(v.x, v.y);
+    }
+  }
 };
 
 template <>
@@ -162,6 +171,15 @@ struct SpinorIO<32> {
 #pragma unroll
     for (int k = 0; k < 6; k++)
       p[(size_t)k * Vh] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
+  }
+  __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b, cx<float> s[6]) {
+    const float4* p = static_cast<const float4*>(base) + (size_t)r * NVEC * Vh + (size_t)(3 * b) * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      float4 v = __ldg(p + (size_t)k * Vh);
+      s[2 * k] = cmk(v.x, v.y);
+      s[2 * k + 1] = cmk(v.z, v.w);
+    }
   }
 };
 
@@ -207,6 +225,31 @@ struct SpinorIO<16> {
       p[(size_t)k * Vh] = v;
     }
     nrm[(size_t)r * Vh + h] = m;
+  }
+  // block 0 = chunk 0 and the first half of chunk 1; block 1 = the second half of chunk 1 and chunk 2
+  __device__ static void load_block(const void* base, const float* nrm, int Vh, int r, int h, int b, cx<float> s[6]) {
+    const uint4* p = static_cast<const uint4*>(base) + (size_t)r * NVEC * Vh + h;
+    const float n = __ldg(nrm + (size_t)r * Vh + h);
+    const uint4 mid = __ldg(p + (size_t)Vh);
+    const uint4 end = __ldg(p + (size_t)(b == 0 ? 0 : 2) * Vh);
+    float2 e0 = h2f(end.x), e1 = h2f(end.y), e2 = h2f(end.z), e3 = h2f(end.w);
+    if (b == 0) {
+      float2 m0 = h2f(mid.x), m1 = h2f(mid.y);
+      s[0] = cmk(e0.x * n, e0.y * n);
+      s[1] = cmk(e1.x * n, e1.y * n);
+      s[2] = cmk(e2.x * n, e2.y * n);
+      s[3] = cmk(e3.x * n, e3.y * n);
+      s[4] = cmk(m0.x * n, m0.y * n);
+      s[5] = cmk(m1.x * n, m1.y * n);
+    } else {
+      float2 m2 = h2f(mid.z), m3 = h2f(mid.w);
+      s[0] = cmk(m2.x * n, m2.y * n);
+      s[1] = cmk(m3.x * n, m3.y * n);
+      s[2] = cmk(e0.x * n, e0.y * n);
+      s[3] = cmk(e1.x * n, e1.y * n);
+      s[4] = cmk(e2.x * n, e2.y * n);
+      s[5] = cmk(e3.x * n, e3.y * n);
+    }
   }
 };
 
@@ -392,6 +435,7 @@ enum FinalizeMode {
   FIN_CG_PAP = 1,    // alpha = rr / pAp
   FIN_CG_RR = 2,     // new |r|^2, beta, reliable-update and convergence triggers
   FIN_CG_TRUE = 3,   // true residual after a reliable update
+  FIN_CG_BNORM = 4,  // |b|^2: tol2 *= |b|^2, a zero source is inactive from the start
 };
 
 struct ReduceArgs {
@@ -444,6 +488,19 @@ __device__ __forceinline__ void finalize_total(const ReduceArgs& ra, int r, doub
         s.pending = 1;
         ra.ctl->halt = 1;
       }
+      break;
+    }
+    case FIN_CG_BNORM: {
+      CGState& s = ra.cg[r];
+      if (!isfinite(total)) {
+        ra.ctl->nan = 1;
+        ra.ctl->halt = 1;
+        s.active = 0;
+        break;
+      }
+      s.bnorm2 = total;
+      s.tol2 *= total;
+      s.active = total > 0.0 ? 1 : 0;
       break;
     }
     case FIN_CG_TRUE: {
@@ -506,7 +563,16 @@ __device__ __forceinline__ void grid_reduce(double v, int nrhs, const ReduceArgs
       finalize_total(ra, r, tot);
     }
   }
-  if (threadIdx.x == 0) *ra.counter = 0u;
+  if (threadIdx.x == 0) {
+    if (ra.mode == FIN_CG_TRUE) {
+      // after a residual replacement the inner iteration may run again unless
+      // every right-hand side has converged or a non-finite value was seen
+      int any = 0;
+      for (int r = 0; r < nrhs; r++) any |= ra.cg[r].active;
+      ra.ctl->halt = (any && !ra.ctl->nan) ? 0 : 1;
+    }
+    *ra.counter = 0u;
+  }
 }
 
 }  // namespace qcd
