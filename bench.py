@@ -34,6 +34,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Dslash GFLOPS & HBM GB/s; time to 1e-8 CG solve, mixed vs FP64, 1 GB300"
+# FP64 peak of GB300 derived from its unit counts and clock: 2 FP64 FMA / clock / SM x 152 SMs x 2.07 GHz
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 WORKLOAD = "c1_16^4"
 
 
@@ -46,8 +48,12 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
+    ap.add_argument("--no-hbm", action="store_true", help="skip the large-volume Dslash bandwidth measurement")
     ap.add_argument("--only", default=None, choices=[None, "dslash"],
                     help="dslash: only apply Mhat^dag Mhat (FP32 and FP64) a few times, for profiler captures")
+    ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides for --only dslash")
+    ap.add_argument("--precs", default="32,64", help="precisions for --only dslash")
     return ap.parse_args()
 
 
@@ -214,22 +220,24 @@ def run_ours(args, world, rank, local):
     # plain FP64 GPU solve on the same lattice, for the mixed-vs-FP64 comparison
     fp64 = Q.solver_params(tol=1e-8, inner_prec=64, max_iter=20000)
     st64 = (Q.SolverStats * nrhs)()
-    Q.qcd_profile(op.ctx, 1)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    times64 = []
-    for _ in range(max(2, min(args.steps, 3))):
-        flush.zero_()
-        e0.record(stream)
-        Q.qcd_cg_solve(op.ctx, Q._ptr(x), Q._ptr(b), nrhs, fp64, st64)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        times64.append(e0.elapsed_time(e1))
-    prof64 = Q.qcd_profile_read(op.ctx)
-    Q.qcd_profile(op.ctx, 0)
+    times64, prof64 = [float("nan")], []
+    if not args.no_fp64:
+        Q.qcd_profile(op.ctx, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        times64 = []
+        for _ in range(max(2, min(args.steps, 3))):
+            flush.zero_()
+            e0.record(stream)
+            Q.qcd_cg_solve(op.ctx, Q._ptr(x), Q._ptr(b), nrhs, fp64, st64)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            times64.append(e0.elapsed_time(e1))
+        prof64 = Q.qcd_profile_read(op.ctx)
+        Q.qcd_profile(op.ctx, 0)
 
     result = dict(metric=METRIC, value=ms_per_step * 1.0, unit="ms per hot-path step (16^4, solve to 1e-8)")
     solve_mixed = float(np.mean(parts[:, 2]))
-    solve64 = float(np.mean(times64))
+    solve64 = None if args.no_fp64 else float(np.mean(times64))
 
     def kstats(prof_list, prefix):
         rows = [p for p in prof_list if p["name"].startswith(prefix)]
@@ -241,7 +249,7 @@ def run_ours(args, world, rank, local):
                     gflops=fl / (ms * 1e-3) / 1e9 if ms else 0.0, bytes_per_launch=by / max(n, 1))
 
     d32 = kstats(prof, "dslash_p32")
-    d64 = kstats(prof64, "dslash_p64")
+    d64 = kstats(prof, "dslash_p64")
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -250,6 +258,16 @@ def run_ours(args, world, rank, local):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     total_launches = next((p["launches"] for p in prof if p["name"] == "launches_total"), None)
+    # per-step device time of each kernel class: sampled average duration x launches per step
+    per_step_launches = {"dslash_p32": 4 * iters, "dslash_p64": 4 * max(stats[0].reliable_updates, 0),
+                         "force_links": 1, "force_clover_coeff": 1, "clover_build": 1, "cg_update": iters,
+                         "p_update": iters}
+    classes = {}
+    for key, n in per_step_launches.items():
+        ks = kstats(prof, key)
+        if ks["launches"]:
+            classes[key] = dict(ks, launches_per_step=n, est_ms_per_step=ks["avg_us"] * n / 1e3)
+    dominant = max(classes, key=lambda k: classes[k]["est_ms_per_step"])
     result.update({
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 reliable",
@@ -261,25 +279,74 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"replicas x{world}"},
         "parts_ms": {"load_gauge": float(np.mean(parts[:, 0])), "clover_build": float(np.mean(parts[:, 1])),
                      "cg_solve_mixed": solve_mixed, "fermion_force": float(np.mean(parts[:, 3]))},
-        "solve": {"mixed_ms": solve_mixed, "fp64_ms": solve64, "speedup_mixed_vs_fp64": solve64 / solve_mixed,
+        "solve": {"mixed_ms": solve_mixed, "fp64_ms": solve64, "speedup_mixed_vs_fp64": None if solve64 is None else solve64 / solve_mixed,
                   "mixed_iters": iters, "fp64_iters": st64[0].iters, "reliable_updates": stats[0].reliable_updates,
                   "true_rel_resid_mixed": resid, "true_rel_resid_fp64": st64[0].true_rel_resid},
         "dslash": {"fp32_in_solve": d32, "fp64_in_solve": d64},
+        "kernels_per_step": classes,
         "gpu_launches": total_launches,
         "clocks": clocks,
         "wall_s_timed_region": wall,
     })
-    # roofline of the dominant kernel: the FP32 hopping kernels inside the solve
-    result["roofline"] = {"kernel": "dslash_kernel<32,12,*> (FP32 hopping + fused clover epilogue)",
-                          "bound": "hbm", "achieved": d32["gbs"], "peak": hbm_peak, "unit": "GB/s",
-                          "frac": d32["gbs"] / hbm_peak, "traffic": None,
-                          "note": "16^4 working set is L2-resident inside a solve; see profiles/"}
+    # roofline of the kernel with the largest device time per step
+    dk = classes[dominant]
+    if dominant in ("dslash_p32",):
+        result["roofline"] = {"kernel": dominant, "bound": "hbm", "achieved": dk["gbs"], "peak": hbm_peak,
+                              "unit": "GB/s", "frac": dk["gbs"] / hbm_peak, "traffic": None,
+                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    else:
+        fp64_peak = FP64_PEAK_TFLOPS * 1e3
+        result["roofline"] = {"kernel": dominant, "bound": "alu", "achieved": dk["gflops"] / 1e3,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": dk["gflops"] / fp64_peak,
+                              "traffic": None,
+                              "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived; probe measured 1.19)"}
+    result["roofline_dslash_fp32_in_solve"] = {"bound": "hbm", "achieved": d32["gbs"], "peak": hbm_peak,
+                                               "unit": "GB/s", "frac": d32["gbs"] / hbm_peak,
+                                               "note": "16^4 working set is L2-resident inside a solve"}
+    if not args.no_hbm:
+        result["dslash_large_volume"] = dslash_large_volume(dev, hbm_peak)
     if not args.no_e2e:
         result["e2e"] = run_e2e(op, U_np, b_np, w, stream, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(w, iters)
     op.close()
     return result
+
+
+def dslash_large_volume(dev, hbm_peak, dims=(32, 32, 32, 64), reps=5):
+    """The hopping kernels on a 32^3 x 64 lattice (working set far above the 129 MB L2): Mhat^dag Mhat
+    in FP32 and FP16 (12-real links) with 1 and 8 right-hand sides, per-launch CUDA-event times on the
+    library's stream, algorithmic bytes per launch / duration against the measured HBM bandwidth."""
+    import torch
+    from paper_0910_0262_gb300 import synth
+    from paper_0910_0262_gb300 import qcd as Q
+    U_np, b_np = synth.make_problem(dims, 0.15, 4, 8)
+    op = Q.CloverWilson(dims, -1.0, stream=torch.cuda.current_stream(dev))
+    op.load_gauge(torch.from_numpy(U_np).to(dev), recon12=True)
+    op.clover_build(0.12, 1.0)
+    b = torch.from_numpy(b_np).to(dev)
+    out = {}
+    for prec in (32, 16):
+        for nrhs in (1, 8):
+            v = b[:nrhs].contiguous()
+            op.dslash(v, Q.QCD_OP_MDAGM, precision=prec)
+            torch.cuda.synchronize(dev)
+            op.profile(True)
+            for _ in range(reps):
+                op.dslash(v, Q.QCD_OP_MDAGM, precision=prec)
+            prof = op.profile_read()
+            op.profile(False)
+            rows = [p for p in prof if p["name"].startswith(f"dslash_p{prec}")]
+            ms = sum(p["total_ms"] for p in rows)
+            by = sum(p["bytes"] for p in rows)
+            fl = sum(p["flops"] for p in rows)
+            n = sum(p["launches"] for p in rows)
+            gbs = by / (ms * 1e-3) / 1e9
+            out[f"fp{prec}_rhs{nrhs}"] = {"launches": n, "avg_us": 1e3 * ms / n, "gbs": gbs, "frac_hbm": gbs / hbm_peak,
+                                          "gflops": fl / (ms * 1e-3) / 1e9, "bytes_per_launch": by / n}
+    op.close()
+    return {"dims": list(dims), "op": "Mhat^dag Mhat (4 hopping launches with fused clover epilogues)",
+            "peak_gbs": hbm_peak, "results": out}
 
 
 def run_e2e(op, U_np, b_np, w, stream, dev):
@@ -383,12 +450,13 @@ def run_dslash_only(args):
     from paper_0910_0262_gb300 import qcd as Q
     build.build()
     w = workload_params(args.workload)
-    U_np, b_np = synth.make_problem(w["dims"], w["eps"], w["seed"], w["nrhs"])
+    nrhs = args.nrhs or w["nrhs"]
+    U_np, b_np = synth.make_problem(w["dims"], w["eps"], w["seed"], nrhs)
     op = Q.CloverWilson(w["dims"], w["t_bc"])
     op.load_gauge(torch.from_numpy(U_np).cuda(), recon12=True)
     op.clover_build(w["kappa"], w["csw"])
     b = torch.from_numpy(b_np).cuda()
-    for prec in (32, 64):
+    for prec in [int(p) for p in args.precs.split(",")]:
         for _ in range(args.steps):
             y = op.dslash(b, Q.QCD_OP_MDAGM, precision=prec)
     torch.cuda.synchronize()

@@ -32,4 +32,4 @@ own sign and normalisation conventions is unpinned (no MILC code or output is
 available); the conventions are stated where they are defined.
 """
 
-from . import lattice, dirac, evenodd, cg, force  # noqa: F401
+from . import lattice, dirac, evenodd, cg, force, local  # noqa: F401

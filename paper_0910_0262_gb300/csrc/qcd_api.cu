@@ -120,6 +120,8 @@ struct qcd_ctx {
   void* Ainv64 = nullptr;
   void* A32 = nullptr;
   void* Ainv32 = nullptr;
+  void* A16 = nullptr;
+  void* Ainv16 = nullptr;
   bool have_clover = false;
   double kappa = 0, csw = 0;
   // device status words: [0] clover not positive definite, [1] non-finite input
@@ -134,7 +136,7 @@ struct qcd_ctx {
   CGState* h_cg = nullptr;
   CGControl* h_ctl = nullptr;
   double* h_results = nullptr;
-  int max_partials = 0;
+  long long max_partials = 0;
   Buf ws[S_COUNT];
   // profiling
   bool prof_on = false;
@@ -208,8 +210,10 @@ struct ProfScope {
   double bytes, flops;
   ProfScope(qcd_ctx* c_, const char* name, double bytes_, double flops_) : c(c_), bytes(bytes_), flops(flops_) {
     if (c->sink) {
-      // recording a graph: the event pair becomes two event-record nodes of the graph
-      if (!c->sink->g->prof) return;
+      // recording a graph: the event pair becomes two event-record nodes of the graph.  Only the
+      // first CG iteration of each graph is bracketed (a sample), since every event-record node
+      // also serialises the graph at that point.
+      if (!c->sink->g->prof || c->sink->iter > 0) return;
       cls = prof_class(c, name);
       a = c->sink->g->events[c->sink->next++];
       cudaEventRecordWithFlags(a, c->cur, cudaEventRecordExternal);
@@ -257,12 +261,18 @@ void dslash_cost(const qcd_ctx* c, int prec, int epi, int nrhs, double* bytes, d
   const double Vh = c->g.Vh;
   const int R = prec == 64 ? 18 : c->recon;
   const double bl = real_bytes(prec);
-  const double bc = prec == 64 ? 8 : 4;
+  const double bc = prec == 64 ? 8 : (prec == 32 ? 4 : 2);
   const double bs = 24.0 * real_bytes(prec) + (prec == 16 ? 4 : 0);
   double site = 8.0 * R * bl + (epi != EPI_NONE ? 72.0 * bc : 0.0);
   double rhs = bs * (epi == EPI_XPAY ? 3.0 : 2.0);
+  if (epi == EPI_XPAY_CG) {
+    // reads in, x, p; reads and writes x_lo, r_lo; writes nothing else
+    const double sr = 24.0 * (prec == 64 ? 8 : 4);
+    rhs = 3.0 * bs + 4.0 * sr;
+  }
   *bytes = Vh * site + Vh * nrhs * rhs;
-  *flops = Vh * nrhs * (1320.0 + (epi != EPI_NONE ? 504.0 : 0.0) + (epi == EPI_XPAY ? 48.0 : 0.0));
+  *flops = Vh * nrhs * (1320.0 + (epi != EPI_NONE ? 504.0 : 0.0) + (epi >= EPI_XPAY ? 48.0 : 0.0) +
+                        (epi == EPI_XPAY_CG ? 96.0 : 0.0));
 }
 
 const void* gauge_ptr(const qcd_ctx* c, int prec) { return prec == 64 ? c->g64 : (prec == 32 ? c->g32 : c->g16); }
@@ -271,6 +281,10 @@ const void* clover_ptr(const qcd_ctx* c, int prec, bool inverse, int parity) {
   if (prec == 64) {
     const double2* base = static_cast<const double2*>(inverse ? c->Ainv64 : c->A64);
     return base + (size_t)parity * 36 * c->g.Vh;
+  }
+  if (prec == 16) {
+    const uint4* base = static_cast<const uint4*>(inverse ? c->Ainv16 : c->A16);
+    return base + (size_t)parity * 9 * c->g.Vh;
   }
   const float4* base = static_cast<const float4*>(inverse ? c->Ainv32 : c->A32);
   return base + (size_t)parity * 18 * c->g.Vh;
@@ -291,7 +305,7 @@ void run_dslash(qcd_ctx* c, int prec, int epi, const DslashArgs& a) {
   dslash_cost(c, prec, epi, a.nrhs, &bytes, &flops);
   char name[40];
   snprintf(name, sizeof name, "dslash_p%d_r%d_%s", prec, prec == 64 ? 18 : c->recon,
-           epi == EPI_NONE ? "plain" : (epi == EPI_CLOVER_INV ? "cloverinv" : "xpay"));
+           epi == EPI_NONE ? "plain" : (epi == EPI_CLOVER_INV ? "cloverinv" : (epi == EPI_XPAY ? "xpay" : "xpaycg")));
   ProfScope ps(c, name, bytes, flops);
   launch_dslash(prec, prec == 64 ? 18 : c->recon, epi, a, c->cur);
 }
@@ -299,6 +313,7 @@ void run_dslash(qcd_ctx* c, int prec, int epi, const DslashArgs& a) {
 ReduceArgs reduce_args(qcd_ctx* c, int mode) {
   ReduceArgs r;
   r.partials = c->partials;
+  r.capacity = c->max_partials;
   r.counter = c->counter;
   r.result = c->results;
   r.mode = mode;
@@ -431,9 +446,12 @@ qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* strea
   c->g.XY = dims[0] * dims[1];
   c->g.XYZ = dims[0] * dims[1] * dims[2];
   c->g.t_bc = t_bc;
-  c->max_partials = (c->g.Vh * MAX_RHS + 63) / 64 + 64;
+  // partial sums of one reduction: nrhs x (blocks of the launch); the hopping kernel covers 32
+  // (site, RHS) pairs per block, the fewest of all reducing kernels, so nrhs <= MAX_RHS needs
+  // at most MAX_RHS * ceil(Vh * MAX_RHS / 32) slots
+  c->max_partials = (long long)MAX_RHS * ((c->g.Vh * (long long)MAX_RHS + 31) / 32) + 64;
   bool ok = cudaMalloc(&c->flags, 4 * sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&c->partials, sizeof(double) * (size_t)c->max_partials * MAX_RHS) == cudaSuccess &&
+            cudaMalloc(&c->partials, sizeof(double) * (size_t)c->max_partials) == cudaSuccess &&
             cudaMalloc(&c->counter, sizeof(unsigned)) == cudaSuccess &&
             cudaMalloc(&c->results, sizeof(double) * MAX_RHS) == cudaSuccess &&
             cudaMalloc(&c->cg, sizeof(CGState) * MAX_RHS) == cudaSuccess &&
@@ -449,6 +467,7 @@ qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* strea
   }
   cudaMemset(c->counter, 0, sizeof(unsigned));
   cudaMemset(c->flags, 0, 4 * sizeof(int));
+  cudaMemset(c->ctl, 0, sizeof(CGControl));
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     qcd_destroy(c);
@@ -468,7 +487,7 @@ qcd_status qcd_destroy(qcd_ctx* c) {
   cudaSetDevice(c->device);
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
-  void* dev[] = {c->g64, c->g32, c->g16, c->A64, c->Ainv64, c->A32, c->Ainv32, c->flags,
+  void* dev[] = {c->g64, c->g32, c->g16, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, c->flags,
                  c->partials, c->counter, c->results, c->cg, c->ctl};
   for (void* p : dev)
     if (p) cudaFree(p);
@@ -538,11 +557,14 @@ qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
     CUDA_TRY(cudaMalloc(&c->Ainv64, (size_t)2 * 36 * g.Vh * sizeof(double2)));
     CUDA_TRY(cudaMalloc(&c->A32, (size_t)2 * 18 * g.Vh * sizeof(float4)));
     CUDA_TRY(cudaMalloc(&c->Ainv32, (size_t)2 * 18 * g.Vh * sizeof(float4)));
+    CUDA_TRY(cudaMalloc(&c->A16, (size_t)2 * 9 * g.Vh * sizeof(uint4)));
+    CUDA_TRY(cudaMalloc(&c->Ainv16, (size_t)2 * 9 * g.Vh * sizeof(uint4)));
   }
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->st));
   {
     ProfScope ps(c, "clover_build", 0, 0);
-    launch_clover_build(g, c->g64, kappa, csw, c->A64, c->Ainv64, c->A32, c->Ainv32, c->flags, c->st);
+    launch_clover_build(g, c->g64, kappa, csw, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, c->flags,
+                        c->st);
   }
   CUDA_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   if ((s = sync_and_check(c, "clover_build"))) return s;
@@ -675,14 +697,36 @@ void enqueue_iteration(qcd_ctx* c, const SolverFields& f, int nrhs) {
   const int* halt = &c->ctl->halt;
   ReduceArgs red_pap = reduce_args(c, FIN_CG_PAP);
   ReduceArgs red_rr = reduce_args(c, FIN_CG_RR);
-  apply_mdagm(c, f.pp, nrhs, f.p, f.p_n, f.ap, f.ap_n, f.t, f.t_n, f.y, f.y_n, &red_pap, halt);
-  double ub;
-  update_cost(g, f.pr, f.pp, nrhs, &ub);
-  {
-    ProfScope ps(c, "cg_update", ub, 0);
-    launch_cg_update(f.pr, f.pp, g, nrhs, f.x_lo, f.x_lo_n, f.r_lo, f.r_lo_n, f.p, f.p_n, f.ap, f.ap_n, red_rr, halt,
-                     c->cur);
-  }
+  // y = Mhat p with |y|^2 = <p, Mhat^dag Mhat p> -> alpha
+  apply_mhat(c, f.pp, nrhs, false, f.p, f.p_n, f.y, f.y_n, f.t, f.t_n, &red_pap, halt);
+  // t = A_oo^-1 D_oe g5 y
+  DslashArgs a = base_args(c, f.pp, 1, nrhs);
+  a.in = f.y;
+  a.in_norm = f.y_n;
+  a.out = f.t;
+  a.out_norm = f.t_n;
+  a.clover = clover_ptr(c, f.pp, true, 1);
+  a.in_g5 = 1;
+  a.halt = halt;
+  run_dslash(c, f.pp, EPI_CLOVER_INV, a);
+  // Ap = g5 (A_ee g5 y - kappa^2 D_eo t), kept in registers: x += alpha p, r -= alpha Ap,
+  // |r|^2 -> beta and the reliable-update / convergence triggers
+  DslashArgs b = base_args(c, f.pp, 0, nrhs);
+  b.in = f.t;
+  b.in_norm = f.t_n;
+  b.x = f.y;
+  b.x_norm = f.y_n;
+  b.clover = clover_ptr(c, f.pp, false, 0);
+  b.a = -c->kappa * c->kappa;
+  b.x_g5 = 1;
+  b.out_g5 = 1;
+  b.halt = halt;
+  b.red = red_rr;
+  b.cg_x = f.x_lo;
+  b.cg_r = f.r_lo;
+  b.cg_p = f.p;
+  b.cg_p_norm = f.p_n;
+  run_dslash(c, f.pp, EPI_XPAY_CG, b);
   {
     const double pb = (double)g.Vh * nrhs * (24.0 * real_bytes(f.pr) + 2 * (24.0 * real_bytes(f.pp) + (f.pp == 16 ? 4 : 0)));
     ProfScope ps(c, "p_update", pb, 0);
@@ -706,7 +750,7 @@ const int MAX_GRAPH_LEN = 64;
 
 qcd_status capture_graph(qcd_ctx* c, ItGraph* gph) {
   if (gph->prof) {
-    const size_t need = gph->kind == 0 ? (size_t)12 * gph->len : 14;
+    const size_t need = 14;
     while (gph->events.size() < need) {
       cudaEvent_t e;
       CUDA_TRY(cudaEventCreate(&e));
@@ -918,6 +962,7 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
     }
     if (c->prof_on) collect_graphs(c, max_it - done_iters);
     done_iters = max_it;
+    if (c->h_ctl->overflow) return fail(QCD_ERR_CUDA, "reduction buffer too small (internal sizing error)");
     if (c->h_ctl->nan) {
       result = fail(QCD_ERR_NAN, "non-finite value or breakdown in CG");
       break;
@@ -1058,10 +1103,15 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
     run_dslash(c, 64, EPI_CLOVER_INV, a);
     done += nb;
   }
+  const double V = 2.0 * g.Vh;
   {
-    ProfScope ps(c, "force", 0, 0);
-    launch_force(g, c->kappa, c->csw, nrhs, c->g64, Xe, Xo, Ye, Yo, static_cast<double2*>(clf),
-                 reinterpret_cast<double2*>(F), (flags & QCD_FORCE_GRADIENT) != 0, c->st);
+    ProfScope ps(c, "force_clover_coeff", V * (nrhs * 2 * 192.0 + 6 * 144.0), V * force_coeff_flops(nrhs));
+    launch_force_coeff(g, c->kappa, c->csw, nrhs, Xe, Xo, Ye, Yo, static_cast<double2*>(clf), c->st);
+  }
+  {
+    ProfScope ps(c, "force_links", 4 * V * (504.0 + 96.0 * nrhs), 4 * V * force_link_flops(nrhs));
+    launch_force_links(g, c->kappa, nrhs, c->g64, Xe, Xo, Ye, Yo, static_cast<const double2*>(clf),
+                       reinterpret_cast<double2*>(F), (flags & QCD_FORCE_GRADIENT) != 0, c->st);
   }
   return sync_and_check(c, "fermion_force");
 }

@@ -134,9 +134,26 @@ __device__ __forceinline__ void store_block32(float4* base, int Vh, int h, int b
   for (int k = 0; k < 9; k++) q[(size_t)k * Vh] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
 }
 
+// 36 halves of block b at halves [36b, 36b+36) of the site's 72 ([9][Vh] uint4 layout)
+__device__ __forceinline__ void store_block16(uint4* base, int Vh, int h, int b, const double d[6], const C L[15]) {
+  uint16_t* q = reinterpret_cast<uint16_t*>(base);
+  float f[36];
+  for (int k = 0; k < 6; k++) f[k] = (float)d[k];
+  for (int k = 0; k < 15; k++) {
+    f[6 + 2 * k] = (float)L[k].re;
+    f[7 + 2 * k] = (float)L[k].im;
+  }
+  for (int k = 0; k < 36; k++) {
+    const int j = 36 * b + k;  // half index within the site
+    __half hv = __float2half_rn(f[k]);
+    q[((size_t)(j >> 3) * Vh + h) * 8 + (j & 7)] = *reinterpret_cast<uint16_t*>(&hv);
+  }
+}
+
 __global__ void __launch_bounds__(128) clover_build_kernel(Geom g, const double2* __restrict__ g64, double kappa,
                                                            double csw, double2* A64, double2* Ainv64, float4* A32,
-                                                           float4* Ainv32, int* notposdef) {
+                                                           float4* Ainv32, uint4* A16, uint4* Ainv16,
+                                                           int* notposdef) {
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= 2 * g.Vh) return;
   const int p = tid / g.Vh, h = tid - p * g.Vh;
@@ -185,6 +202,8 @@ __global__ void __launch_bounds__(128) clover_build_kernel(Geom g, const double2
     store_block64(I64p, g.Vh, h, b, di, Li);
     if (A32) store_block32(A32 + (size_t)p * 18 * g.Vh, g.Vh, h, b, d, L);
     if (Ainv32) store_block32(Ainv32 + (size_t)p * 18 * g.Vh, g.Vh, h, b, di, Li);
+    if (A16) store_block16(A16 + (size_t)p * 9 * g.Vh, g.Vh, h, b, d, L);
+    if (Ainv16) store_block16(Ainv16 + (size_t)p * 9 * g.Vh, g.Vh, h, b, di, Li);
   }
 }
 
@@ -197,7 +216,7 @@ __global__ void clover_apply_kernel(Geom g, const void* clov, const void* in, co
   const int r = tid % nrhs, h = tid / nrhs;
   cx<R> s[12], o[12];
   SpinorIO<P>::load(in, in_norm, g.Vh, r, h, s);
-  constexpr int CP = P == 64 ? 64 : 32;
+  constexpr int CP = P;
   CloverIO<CP>::apply(clov, g.Vh, h, 0, s, o);
   CloverIO<CP>::apply(clov, g.Vh, h, 1, s + 6, o + 6);
   SpinorIO<P>::store(out, out_norm, g.Vh, r, h, o);
@@ -206,13 +225,14 @@ __global__ void clover_apply_kernel(Geom g, const void* clov, const void* in, co
 }  // namespace
 
 void launch_clover_build(const Geom& g, const void* g64, double kappa, double csw, void* A64, void* Ainv64, void* A32,
-                         void* Ainv32, int* notposdef, cudaStream_t st) {
+                         void* Ainv32, void* A16, void* Ainv16, int* notposdef, cudaStream_t st) {
   g_kernel_launches += 1;
   const int B = 128;
   const int nb = (2 * g.Vh + B - 1) / B;
   clover_build_kernel<<<nb, B, 0, st>>>(g, static_cast<const double2*>(g64), kappa, csw, static_cast<double2*>(A64),
                                         static_cast<double2*>(Ainv64), static_cast<float4*>(A32),
-                                        static_cast<float4*>(Ainv32), notposdef);
+                                        static_cast<float4*>(Ainv32), static_cast<uint4*>(A16),
+                                        static_cast<uint4*>(Ainv16), notposdef);
 }
 
 void launch_clover_apply(int prec, const Geom& g, const void* clover, const void* in, const float* in_norm, void* out,

@@ -26,8 +26,14 @@ void launch_epi(int epi, const DslashArgs& a, cudaStream_t st) {
     switch (epi) {
       case EPI_NONE: dslash_split_kernel<P, RECON, EPI_NONE><<<nb, 128, 0, st>>>(a); break;
       case EPI_CLOVER_INV: dslash_split_kernel<P, RECON, EPI_CLOVER_INV><<<nb, 128, 0, st>>>(a); break;
+      case EPI_XPAY_CG: dslash_split_kernel<P, RECON, EPI_XPAY_CG><<<nb, 128, 0, st>>>(a); break;
       default: dslash_split_kernel<P, RECON, EPI_XPAY><<<nb, 128, 0, st>>>(a); break;
     }
+    return;
+  }
+  if (epi == EPI_XPAY_CG) {  // only the split kernel carries the fused CG update
+    const int nb = (a.g.Vh * a.nrhs + 31) / 32;
+    dslash_split_kernel<P, RECON, EPI_XPAY_CG><<<nb, 128, 0, st>>>(a);
     return;
   }
   const int nb = (a.g.Vh * a.nrhs + DB - 1) / DB;

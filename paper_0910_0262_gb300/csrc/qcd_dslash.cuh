@@ -18,6 +18,7 @@ enum Epilogue {
   EPI_NONE = 0,        // out = D in
   EPI_CLOVER_INV = 1,  // out = C (D in)            (C = A^-1 of the output parity)
   EPI_XPAY = 2,        // out = C x + a (D in)      (C = A of the output parity)
+  EPI_XPAY_CG = 3,     // Ap = C x + a (D in), not stored: x_lo += alpha p, r_lo -= alpha Ap, |r_lo|^2
 };
 
 struct DslashArgs {
@@ -39,6 +40,11 @@ struct DslashArgs {
   int do_norm;             // reduce |out|^2 per RHS
   ReduceArgs red;
   const int* halt;         // non-null: return immediately when *halt != 0
+  // EPI_XPAY_CG: the CG vectors (x_lo, r_lo in FP64 for P = 64, else FP32; p in precision P)
+  void* cg_x;
+  void* cg_r;
+  const void* cg_p;
+  const float* cg_p_norm;
 };
 
 // Spin projection (1 + sgn g_mu) psi -> half spinor h (spin rows 0 and 1).
@@ -170,7 +176,7 @@ struct CloverPrec<64> { static constexpr int CP = 64; };
 template <>
 struct CloverPrec<32> { static constexpr int CP = 32; };
 template <>
-struct CloverPrec<16> { static constexpr int CP = 32; };
+struct CloverPrec<16> { static constexpr int CP = 16; };
 
 template <int P, typename R>
 __device__ __forceinline__ void clover_apply(const void* clov, int Vh, int h, const cx<R> in[12], cx<R> out[12]) {
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
       for (int k = 0; k < 6; k++) res[k] = v[k];
     } else if (EPI == EPI_CLOVER_INV) {
       CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, v, res);
-    } else {
+    } else {  // EPI_XPAY, EPI_XPAY_CG
       cx<R> xs[6], cxs[6];
       SpinorIO<P>::load_block(A.x, A.x_norm, A.g.Vh, r, hh, b, xs);
       if (A.x_g5 && b == 1) {
@@ -290,15 +296,40 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
 #pragma unroll
       for (int k = 0; k < 6; k++) res[k] = -res[k];
     }
-    if (A.do_norm) {
+    if (EPI == EPI_XPAY_CG) {
+      // res = (A p)_b: advance x and r of this RHS with alpha from the <p, A p> reduction
+      constexpr int PR = P == 64 ? 64 : 32;
+      using RR = typename Real<PR>::T;
+      const CGState& st = A.red.cg[r];
+      if (st.active) {
+        const RR al = RR(st.alpha);
+        cx<R> ps[6];
+        cx<RR> xs[6], rs[6];
+        SpinorIO<P>::load_block(A.cg_p, A.cg_p_norm, A.g.Vh, r, hh, b, ps);
+        SpinorIO<PR>::load_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
+        SpinorIO<PR>::load_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
 #pragma unroll
-      for (int k = 0; k < 6; k++) nrm += double(res[k].re) * res[k].re + double(res[k].im) * res[k].im;
+        for (int k = 0; k < 6; k++) {
+          xs[k].re = fma(al, RR(ps[k].re), xs[k].re);
+          xs[k].im = fma(al, RR(ps[k].im), xs[k].im);
+          rs[k].re = fma(-al, RR(res[k].re), rs[k].re);
+          rs[k].im = fma(-al, RR(res[k].im), rs[k].im);
+          nrm += double(rs[k].re) * rs[k].re + double(rs[k].im) * rs[k].im;
+        }
+        SpinorIO<PR>::store_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
+        SpinorIO<PR>::store_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
+      }
+    } else {
+      if (A.do_norm) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) nrm += double(res[k].re) * res[k].re + double(res[k].im) * res[k].im;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; k++) part[0][6 * b + k][lane] = res[k];
     }
-#pragma unroll
-    for (int k = 0; k < 6; k++) part[0][6 * b + k][lane] = res[k];
   }
   __syncthreads();
-  if (valid) {
+  if (valid && EPI != EPI_XPAY_CG) {
     if (P == 64) {
       double2* q = static_cast<double2*>(A.out) + (size_t)r * 12 * A.g.Vh + hh;
 #pragma unroll
@@ -322,7 +353,7 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
       SpinorIO<16>::store(A.out, A.out_norm, A.g.Vh, r, hh, o);
     }
   }
-  if (A.do_norm) grid_reduce<128>(nrm, A.nrhs, A.red);
+  if (A.do_norm || EPI == EPI_XPAY_CG) grid_reduce<128>(nrm, A.nrhs, A.red);
 }
 
 }  // namespace qcd

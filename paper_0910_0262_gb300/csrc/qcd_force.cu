@@ -291,15 +291,23 @@ __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, in
 
 size_t force_clover_bytes(const Geom& g) { return (size_t)6 * 9 * 2 * g.Vh * sizeof(double2); }
 
-void launch_force(const Geom& g, double kappa, double csw, int nrhs, const void* g64, const double2* Xe,
-                  const double2* Xo, const double2* Ye, const double2* Yo, double2* Cbuf, double2* out,
-                  bool gradient, cudaStream_t st) {
-  g_kernel_launches += 2;
+void launch_force_coeff(const Geom& g, double kappa, double csw, int nrhs, const double2* Xe, const double2* Xo,
+                        const double2* Ye, const double2* Yo, double2* Cbuf, cudaStream_t st) {
+  g_kernel_launches += 1;
   const int V = 2 * g.Vh;
-  const double2* G = static_cast<const double2*>(g64);
   clover_coeff_kernel<<<(V + FB - 1) / FB, FB, 0, st>>>(g, kappa, csw, nrhs, Xe, Xo, Ye, Yo, Cbuf);
-  link_force_kernel<<<(int)((4LL * V + FB - 1) / FB), FB, 0, st>>>(g, kappa, nrhs, G, Xe, Xo, Ye, Yo, Cbuf, out,
-                                                                    gradient ? 1 : 0);
 }
+
+void launch_force_links(const Geom& g, double kappa, int nrhs, const void* g64, const double2* Xe, const double2* Xo,
+                        const double2* Ye, const double2* Yo, const double2* Cbuf, double2* out, bool gradient,
+                        cudaStream_t st) {
+  g_kernel_launches += 1;
+  const int V = 2 * g.Vh;
+  link_force_kernel<<<(int)((4LL * V + FB - 1) / FB), FB, 0, st>>>(g, kappa, nrhs, static_cast<const double2*>(g64),
+                                                                    Xe, Xo, Ye, Yo, Cbuf, out, gradient ? 1 : 0);
+}
+
+double force_link_flops(int nrhs) { return 6.0 * 1800.0 + 744.0 * nrhs + 274.0; }
+double force_coeff_flops(int nrhs) { return 6.0 * (4 * 3 * 3 * 8.0) * nrhs + 6.0 * 60.0; }
 
 }  // namespace qcd

@@ -12,11 +12,17 @@ extern long long g_kernel_launches;
 // bytes of one per-site, per-plane 3x3 complex field over the full lattice (6 planes)
 size_t force_clover_bytes(const Geom& g);
 
-// G or F = -1/2 P_TA(U G^dag) for S = sum_r phi_r^dag (Mhat^dag Mhat)^-1 phi_r, given per RHS
-// the native FP64 fields X_e, X_o = A_oo^-1 D_oe X_e, Y_e = Mhat X_e, Y_o = A_oo^-1 D_eo^dag Y_e.
-// Cbuf: work field of force_clover_bytes; out: canonical [V][4][3][3] complex128.
-void launch_force(const Geom& g, double kappa, double csw, int nrhs, const void* g64, const double2* Xe,
-                  const double2* Xo, const double2* Ye, const double2* Yo, double2* Cbuf, double2* out,
-                  bool gradient, cudaStream_t st);
+// Force for S = sum_r phi_r^dag (Mhat^dag Mhat)^-1 phi_r, given per RHS the native FP64 fields
+// X_e, X_o = A_oo^-1 D_oe X_e, Y_e = Mhat X_e, Y_o = A_oo^-1 D_eo^dag Y_e.
+// 1. C_{mu nu} per site and plane into Cbuf (force_clover_bytes).
+void launch_force_coeff(const Geom& g, double kappa, double csw, int nrhs, const double2* Xe, const double2* Xo,
+                        const double2* Ye, const double2* Yo, double2* Cbuf, cudaStream_t st);
+// 2. per link: G, or F = -1/2 P_TA(U G^dag), into out (canonical [V][4][3][3] complex128).
+void launch_force_links(const Geom& g, double kappa, int nrhs, const void* g64, const double2* Xe, const double2* Xo,
+                        const double2* Ye, const double2* Yo, const double2* Cbuf, double2* out, bool gradient,
+                        cudaStream_t st);
+// conventional FP64 flop counts: per link of kernel 2, per site of kernel 1
+double force_link_flops(int nrhs);
+double force_coeff_flops(int nrhs);
 
 }  // namespace qcd

@@ -143,6 +143,11 @@ struct SpinorIO<64> {
 #pragma unroll
     for (int c = 0; c < 12; c++) p[(size_t)c * Vh] = make_double2(s[c].re, s[c].im);
   }
+  __device__ static void store_block(void* base, float*, int Vh, int r, int h, int b, const cx<double> s[6]) {
+    double2* p = static_cast<double2*>(base) + (size_t)r * NVEC * Vh + (size_t)(6 * b) * Vh + h;
+#pragma unroll
+    for (int c = 0; c < 6; c++) p[(size_t)c * Vh] = make_double2(s[c].re, s[c].im);
+  }
   // components 6b..6b+5 (chiral block b: spins 2b, 2b+1)
   __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b, cx<double> s[6]) {
     const double2* p = static_cast<const double2*>(base) + (size_t)r * NVEC * Vh + (size_t)(6 * b) * Vh + h;
@@ -170,6 +175,12 @@ struct SpinorIO<32> {
     float4* p = static_cast<float4*>(base) + (size_t)r * NVEC * Vh + h;
 #pragma unroll
     for (int k = 0; k < 6; k++)
+      p[(size_t)k * Vh] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
+  }
+  __device__ static void store_block(void* base, float*, int Vh, int r, int h, int b, const cx<float> s[6]) {
+    float4* p = static_cast<float4*>(base) + (size_t)r * NVEC * Vh + (size_t)(3 * b) * Vh + h;
+#pragma unroll
+    for (int k = 0; k < 3; k++)
       p[(size_t)k * Vh] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
   }
   __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b, cx<float> s[6]) {
@@ -402,6 +413,38 @@ struct CloverIO<32> {
   }
 };
 
+// FP16 clover: 72 halves per site (block 0: halves 0..35, block 1: 36..71) in [9][Vh] uint4
+template <>
+struct CloverIO<16> {
+  static constexpr int NVEC = 9;  // uint4 per site
+  __device__ static void apply(const void* c, int Vh, int h, int b, const cx<float> x[6], cx<float> y[6]) {
+    const uint4* q = static_cast<const uint4*>(c) + h;
+    // block b occupies halves [36b, 36b+36): uint4 4b .. 4b+4 (the middle uint4 is shared)
+    float f[40];
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+      uint4 v = __ldg(q + (size_t)(4 * b + k) * Vh);
+      float2 a0 = h2f(v.x), a1 = h2f(v.y), a2 = h2f(v.z), a3 = h2f(v.w);
+      f[8 * k + 0] = a0.x;
+      f[8 * k + 1] = a0.y;
+      f[8 * k + 2] = a1.x;
+      f[8 * k + 3] = a1.y;
+      f[8 * k + 4] = a2.x;
+      f[8 * k + 5] = a2.y;
+      f[8 * k + 6] = a3.x;
+      f[8 * k + 7] = a3.y;
+    }
+    const int o = 4 * b;  // block 1 starts 4 halves into uint4 4
+    float d[6];
+    cx<float> L[15];
+#pragma unroll
+    for (int k = 0; k < 6; k++) d[k] = f[o + k];
+#pragma unroll
+    for (int k = 0; k < 15; k++) L[k] = cmk(f[o + 6 + 2 * k], f[o + 7 + 2 * k]);
+    hermitian6_accumulate(d, L, x, y);
+  }
+};
+
 // ---------------------------------------------------------- CG control ----
 // Per right-hand side state of the CG iteration, resident in device memory so
 // that the iteration runs without host round trips.
@@ -426,7 +469,7 @@ struct CGControl {
   int halt;             // set when any RHS wants a reliable update or on error
   int nan;              // non-finite reduction or breakdown
   int reliable_every;
-  int pad_;
+  int overflow;         // a reduction launch needed more partial slots than allocated (skipped)
   double delta2;        // reliable update when |r|^2 < delta2 * rr_reliable
 };
 
@@ -440,6 +483,7 @@ enum FinalizeMode {
 
 struct ReduceArgs {
   double* partials;        // [nrhs][gridDim.x]
+  long long capacity;      // slots in partials; a launch needing more records ctl->overflow
   unsigned int* counter;   // zero before the launch; the last block resets it
   double* result;          // [nrhs], FIN_STORE
   int mode;
@@ -539,7 +583,9 @@ __device__ __forceinline__ void grid_reduce(double v, int nrhs, const ReduceArgs
     double s = 0.0;
 #pragma unroll 1
     for (int w = 0; w < BLOCK / 32; w++) s += sm[w][threadIdx.x];
-    ra.partials[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = s;
+    const long long slot = (long long)threadIdx.x * gridDim.x + blockIdx.x;
+    if (slot < ra.capacity) ra.partials[slot] = s;
+    else ra.ctl->overflow = 1;
   }
   __threadfence();
   __syncthreads();
@@ -552,7 +598,10 @@ __device__ __forceinline__ void grid_reduce(double v, int nrhs, const ReduceArgs
   __threadfence();
   for (int r = 0; r < nrhs; r++) {
     double s = 0.0;
-    for (int j = threadIdx.x; j < (int)gridDim.x; j += BLOCK) s += __ldcg(ra.partials + (size_t)r * gridDim.x + j);
+    for (int j = threadIdx.x; j < (int)gridDim.x; j += BLOCK) {
+      const long long slot = (long long)r * gridDim.x + j;
+      if (slot < ra.capacity) s += __ldcg(ra.partials + slot);
+    }
     for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     __syncthreads();
     if (lane == 0) sm[warp][0] = s;

@@ -20,9 +20,9 @@ void launch_spinor_to_canon(int prec, const Geom& g, const void* nat, const floa
 void launch_check_finite(const double* data, size_t n, int* flag, cudaStream_t st);
 
 // ---- clover (qcd_clover.cu)
-// A (both parities) and A^-1 (both parities) in FP64 and FP32; flag set if a block is not positive definite.
+// A (both parities) and A^-1 (both parities) in FP64, FP32 and FP16; flag set if a block is not positive definite.
 void launch_clover_build(const Geom& g, const void* g64, double kappa, double csw, void* A64, void* Ainv64,
-                         void* A32, void* Ainv32, int* notposdef, cudaStream_t st);
+                         void* A32, void* Ainv32, void* A16, void* Ainv16, int* notposdef, cudaStream_t st);
 // out = C in for a site-local clover field C of parity-matched fields
 void launch_clover_apply(int prec, const Geom& g, const void* clover, const void* in, const float* in_norm,
                          void* out, float* out_norm, int nrhs, cudaStream_t st);

@@ -18,6 +18,8 @@ gauge configurations, which are not available):
 Lattice dims are (X, Y, Z, T); gauge arrays are complex128 [T, Z, Y, X, 4, 3, 3].
 """
 
+import os
+
 import numpy as np
 
 GELL_MANN = np.zeros((8, 3, 3), dtype=complex)
@@ -62,16 +64,35 @@ def project_su3(U):
     return np.stack([r0, r1, r2], axis=-2)
 
 
-def random_links(dims, eps, rng):
-    """Near-unit SU(3) links [T, Z, Y, X, 4, 3, 3] drawn from rng in [t][z][y][x][mu][a] order."""
+def _links_from_normals(h, eps):
+    """SU(3) links exp(i eps sum_a h_a T_a), projected, for a block of normal draws h [n, 8]."""
+    H = np.einsum('na,aij->nij', h, T_GEN)
+    return project_su3(_exp_i(H, eps))
+
+
+def random_links(dims, eps, rng, workers=None):
+    """Near-unit SU(3) links [T, Z, Y, X, 4, 3, 3] drawn from rng in [t][z][y][x][mu][a] order.
+
+    All normals are drawn first, in order; large lattices then turn them into links in
+    parallel worker processes (spawned), which does not change the result.
+    """
     X, Y, Z, T = dims
     n = X * Y * Z * T * 4
+    h = rng.standard_normal((n, 8))
     U = np.empty((n, 3, 3), dtype=complex)
-    for start in range(0, n, _CHUNK):
-        stop = min(n, start + _CHUNK)
-        h = rng.standard_normal((stop - start, 8))
-        H = np.einsum('na,aij->nij', h, T_GEN)
-        U[start:stop] = project_su3(_exp_i(H, eps))
+    chunks = [(start, min(n, start + _CHUNK)) for start in range(0, n, _CHUNK)]
+    if workers is None:
+        workers = min(16, os.cpu_count() or 1) if n > (1 << 22) else 1
+    if workers > 1:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            futs = [ex.submit(_links_from_normals, h[a:b], eps) for a, b in chunks]
+            for (a, b), f in zip(chunks, futs):
+                U[a:b] = f.result()
+    else:
+        for a, b in chunks:
+            U[a:b] = _links_from_normals(h[a:b], eps)
     return U.reshape(T, Z, Y, X, 4, 3, 3)
 
 
