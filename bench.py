@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison solve")
     ap.add_argument("--no-hbm", action="store_true", help="skip the large-volume Dslash bandwidth measurement")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 32^3x64 8-RHS batched-mixed vs sequential-FP64 solve comparison")
     ap.add_argument("--only", default=None, choices=[None, "dslash"],
                     help="dslash: only apply Mhat^dag Mhat (FP32 and FP64) a few times, for profiler captures")
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides for --only dslash")
@@ -303,8 +305,8 @@ def run_ours(args, world, rank, local):
     result["roofline_dslash_fp32_in_solve"] = {"bound": "hbm", "achieved": d32["gbs"], "peak": hbm_peak,
                                                "unit": "GB/s", "frac": d32["gbs"] / hbm_peak,
                                                "note": "16^4 working set is L2-resident inside a solve"}
-    if not args.no_hbm:
-        result["dslash_large_volume"] = dslash_large_volume(dev, hbm_peak)
+    if not args.no_hbm or not args.no_batched:
+        result.update(large_volume(dev, hbm_peak, not args.no_hbm, not args.no_batched))
     if not args.no_e2e:
         result["e2e"] = run_e2e(op, U_np, b_np, w, stream, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -313,40 +315,74 @@ def run_ours(args, world, rank, local):
     return result
 
 
-def dslash_large_volume(dev, hbm_peak, dims=(32, 32, 32, 64), reps=5):
-    """The hopping kernels on a 32^3 x 64 lattice (working set far above the 129 MB L2): Mhat^dag Mhat
-    in FP32 and FP16 (12-real links) with 1 and 8 right-hand sides, per-launch CUDA-event times on the
-    library's stream, algorithmic bytes per launch / duration against the measured HBM bandwidth."""
+def large_volume(dev, hbm_peak, do_hbm, do_batched, reps=5):
+    """32^3 x 64 lattice (eps 0.15, seed 4, 8 RHS; working set far above the 129 MB L2).
+
+    dslash_large_volume: Mhat^dag Mhat (4 hopping launches with fused clover epilogues) in FP32 and
+    FP16 with 12-real links, 1 and 8 RHS: per-launch CUDA-event times on the library's stream,
+    algorithmic bytes per launch / duration against the measured HBM bandwidth.
+    batched_solve: one batched mixed solve of the 8 RHS (FP16 inner, FP64 reliable updates) against
+    8 sequential plain FP64 solves, both to a true residual of 1e-8.
+    """
     import torch
     from paper_0910_0262_gb300 import synth
     from paper_0910_0262_gb300 import qcd as Q
-    U_np, b_np = synth.make_problem(dims, 0.15, 4, 8)
-    op = Q.CloverWilson(dims, -1.0, stream=torch.cuda.current_stream(dev))
+    w = synth.WORKLOADS["c3_32^3x64"]
+    dims = w["dims"]
+    U_np, b_np = synth.make_problem(dims, w["eps"], w["seed"], w["nrhs"])
+    stream = torch.cuda.current_stream(dev)
+    op = Q.CloverWilson(dims, -1.0, stream=stream)
     op.load_gauge(torch.from_numpy(U_np).to(dev), recon12=True)
     op.clover_build(0.12, 1.0)
     b = torch.from_numpy(b_np).to(dev)
-    out = {}
-    for prec in (32, 16):
-        for nrhs in (1, 8):
-            v = b[:nrhs].contiguous()
-            op.dslash(v, Q.QCD_OP_MDAGM, precision=prec)
-            torch.cuda.synchronize(dev)
-            op.profile(True)
-            for _ in range(reps):
+    res = {}
+    if do_hbm:
+        out = {}
+        for prec in (32, 16):
+            for nrhs in (1, 8):
+                v = b[:nrhs].contiguous()
                 op.dslash(v, Q.QCD_OP_MDAGM, precision=prec)
-            prof = op.profile_read()
-            op.profile(False)
-            rows = [p for p in prof if p["name"].startswith(f"dslash_p{prec}")]
-            ms = sum(p["total_ms"] for p in rows)
-            by = sum(p["bytes"] for p in rows)
-            fl = sum(p["flops"] for p in rows)
-            n = sum(p["launches"] for p in rows)
-            gbs = by / (ms * 1e-3) / 1e9
-            out[f"fp{prec}_rhs{nrhs}"] = {"launches": n, "avg_us": 1e3 * ms / n, "gbs": gbs, "frac_hbm": gbs / hbm_peak,
-                                          "gflops": fl / (ms * 1e-3) / 1e9, "bytes_per_launch": by / n}
+                torch.cuda.synchronize(dev)
+                op.profile(True)
+                for _ in range(reps):
+                    op.dslash(v, Q.QCD_OP_MDAGM, precision=prec)
+                prof = op.profile_read()
+                op.profile(False)
+                rows = [p for p in prof if p["name"].startswith(f"dslash_p{prec}")]
+                ms = sum(p["total_ms"] for p in rows)
+                by = sum(p["bytes"] for p in rows)
+                fl = sum(p["flops"] for p in rows)
+                n = sum(p["launches"] for p in rows)
+                gbs = by / (ms * 1e-3) / 1e9
+                out[f"fp{prec}_rhs{nrhs}"] = {"launches": n, "avg_us": 1e3 * ms / n, "gbs": gbs,
+                                              "frac_hbm": gbs / hbm_peak, "gflops": fl / (ms * 1e-3) / 1e9,
+                                              "bytes_per_launch": by / n}
+        res["dslash_large_volume"] = {"dims": list(dims), "op": "Mhat^dag Mhat (4 hopping launches with fused "
+                                      "clover epilogues)", "peak_gbs": hbm_peak, "results": out}
+    if do_batched:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kw = dict(tol=1e-8, reliable_every=50, reliable_delta=0.1)
+        op.cg_solve(b[:1], inner_prec=16, **kw)  # warm up graph capture
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        xb, stb, okb = op.cg_solve(b, inner_prec=16, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_batched = e0.elapsed_time(e1)
+        e0.record(stream)
+        seq = [op.cg_solve(b[r:r + 1].contiguous(), inner_prec=64, **kw) for r in range(b.shape[0])]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t_seq = e0.elapsed_time(e1)
+        res["batched_solve"] = {
+            "dims": list(dims), "nrhs": int(b.shape[0]),
+            "batched_mixed_fp16_ms": t_batched, "sequential_fp64_ms": t_seq, "speedup": t_seq / t_batched,
+            "batched_iters": [s["iters"] for s in stb], "batched_true_rel_resid": max(s["true_rel_resid"] for s in stb),
+            "sequential_iters": [s[1][0]["iters"] for s in seq],
+            "sequential_true_rel_resid": max(s[1][0]["true_rel_resid"] for s in seq),
+            "converged": bool(okb and all(s[2] for s in seq))}
     op.close()
-    return {"dims": list(dims), "op": "Mhat^dag Mhat (4 hopping launches with fused clover epilogues)",
-            "peak_gbs": hbm_peak, "results": out}
+    return res
 
 
 def run_e2e(op, U_np, b_np, w, stream, dev):

@@ -1086,11 +1086,19 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
   double2* Xo = Xe + (size_t)nrhs * 12 * g.Vh;
   double2* Ye = static_cast<double2*>(yf);
   double2* Yo = Ye + (size_t)nrhs * 12 * g.Vh;
-  launch_spinor_to_native(64, g, X, Xe, nullptr, nrhs, c->st);
-  int done = 0;
-  while (done < nrhs) {
+  // per batch (RHS interleaved within a batch): convert X, then Y_e, X_o, Y_o; the clover
+  // coefficients accumulate over the batches
+  const double V = 2.0 * g.Vh;
+  std::vector<std::pair<size_t, int>> batches;
+  for (int done = 0; done < nrhs;) {
     const int nb = batch_of(nrhs - done);
-    const size_t off = (size_t)done * 12 * g.Vh;
+    batches.push_back({(size_t)done * 12 * g.Vh, nb});
+    done += nb;
+  }
+  for (size_t k = 0; k < batches.size(); k++) {
+    const size_t off = batches[k].first;
+    const int nb = batches[k].second;
+    launch_spinor_to_native(64, g, X + off, Xe + off, nullptr, nb, c->st);
     // Y_e = Mhat X_e with X_o = A_oo^-1 D_oe X_e left in the odd temporary
     apply_mhat(c, 64, nb, false, Xe + off, nullptr, Ye + off, nullptr, Xo + off, nullptr, nullptr, nullptr);
     // Y_o = A_oo^-1 D_eo^dag Y_e = g5 A_oo^-1 D_oe g5 Y_e
@@ -1101,17 +1109,18 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
     a.in_g5 = 1;
     a.out_g5 = 1;
     run_dslash(c, 64, EPI_CLOVER_INV, a);
-    done += nb;
+    ProfScope ps(c, "force_clover_coeff", V * (nb * 2 * 192.0 + 6 * 144.0), V * force_coeff_flops(nb));
+    launch_force_coeff(g, c->kappa, c->csw, nb, Xe + off, Xo + off, Ye + off, Yo + off, static_cast<double2*>(clf),
+                       k > 0, c->st);
   }
-  const double V = 2.0 * g.Vh;
-  {
-    ProfScope ps(c, "force_clover_coeff", V * (nrhs * 2 * 192.0 + 6 * 144.0), V * force_coeff_flops(nrhs));
-    launch_force_coeff(g, c->kappa, c->csw, nrhs, Xe, Xo, Ye, Yo, static_cast<double2*>(clf), c->st);
-  }
-  {
-    ProfScope ps(c, "force_links", 4 * V * (504.0 + 96.0 * nrhs), 4 * V * force_link_flops(nrhs));
-    launch_force_links(g, c->kappa, nrhs, c->g64, Xe, Xo, Ye, Yo, static_cast<const double2*>(clf),
-                       reinterpret_cast<double2*>(F), (flags & QCD_FORCE_GRADIENT) != 0, c->st);
+  // per link: the hopping part of every batch, the clover part once (F is linear in G)
+  for (size_t k = 0; k < batches.size(); k++) {
+    const size_t off = batches[k].first;
+    const int nb = batches[k].second;
+    ProfScope ps(c, "force_links", 4 * V * (504.0 + 96.0 * nb), 4 * V * force_link_flops(nb, k == 0));
+    launch_force_links(g, c->kappa, nb, c->g64, Xe + off, Xo + off, Ye + off, Yo + off,
+                       static_cast<const double2*>(clf), reinterpret_cast<double2*>(F),
+                       (flags & QCD_FORCE_GRADIENT) != 0, k == 0, k > 0, c->st);
   }
   return sync_and_check(c, "fermion_force");
 }

@@ -27,10 +27,10 @@ __global__ void __launch_bounds__(BB) cg_update_kernel(Geom g, int nrhs, void* x
     const double alpha = red.cg[k].alpha;
     cx<RR> xs[12], rs[12];
     cx<RP> ps[12], aps[12];
-    SpinorIO<PR>::load(x, xn, g.Vh, k, h, xs);
-    SpinorIO<PR>::load(r, rn, g.Vh, k, h, rs);
-    SpinorIO<PP>::load(p, pn, g.Vh, k, h, ps);
-    SpinorIO<PP>::load(Ap, Apn, g.Vh, k, h, aps);
+    SpinorIO<PR>::load(x, xn, g.Vh, nrhs, k, h, xs);
+    SpinorIO<PR>::load(r, rn, g.Vh, nrhs, k, h, rs);
+    SpinorIO<PP>::load(p, pn, g.Vh, nrhs, k, h, ps);
+    SpinorIO<PP>::load(Ap, Apn, g.Vh, nrhs, k, h, aps);
     const RR a = RR(alpha);
 #pragma unroll
     for (int c = 0; c < 12; c++) {
@@ -40,8 +40,8 @@ __global__ void __launch_bounds__(BB) cg_update_kernel(Geom g, int nrhs, void* x
       rs[c].im = fma(-a, RR(aps[c].im), rs[c].im);
       v += double(rs[c].re) * rs[c].re + double(rs[c].im) * rs[c].im;
     }
-    SpinorIO<PR>::store(x, xn, g.Vh, k, h, xs);
-    SpinorIO<PR>::store(r, rn, g.Vh, k, h, rs);
+    SpinorIO<PR>::store(x, xn, g.Vh, nrhs, k, h, xs);
+    SpinorIO<PR>::store(r, rn, g.Vh, nrhs, k, h, rs);
   }
   grid_reduce<BB>(v, nrhs, red);
 }
@@ -58,15 +58,15 @@ __global__ void __launch_bounds__(BB) p_update_kernel(Geom g, int nrhs, const vo
   const RR beta = RR(cg[k].beta);
   cx<RR> rs[12];
   cx<RP> ps[12];
-  SpinorIO<PR>::load(r, rn, g.Vh, k, h, rs);
-  SpinorIO<PP>::load(p, pn, g.Vh, k, h, ps);
+  SpinorIO<PR>::load(r, rn, g.Vh, nrhs, k, h, rs);
+  SpinorIO<PP>::load(p, pn, g.Vh, nrhs, k, h, ps);
   cx<RP> out[12];
 #pragma unroll
   for (int c = 0; c < 12; c++) {
     out[c].re = RP(fma(beta, RR(ps[c].re), rs[c].re));
     out[c].im = RP(fma(beta, RR(ps[c].im), rs[c].im));
   }
-  SpinorIO<PP>::store(p, pn, g.Vh, k, h, out);
+  SpinorIO<PP>::store(p, pn, g.Vh, nrhs, k, h, out);
 }
 
 template <int PR>
@@ -77,16 +77,16 @@ __global__ void __launch_bounds__(BB) accumulate_x_kernel(Geom g, int nrhs, doub
   if (h >= g.Vh) return;
   cx<RR> lo[12];
   cx<double> hi[12];
-  SpinorIO<PR>::load(x_lo, xn, g.Vh, k, h, lo);
-  SpinorIO<64>::load(x_hi, nullptr, g.Vh, k, h, hi);
+  SpinorIO<PR>::load(x_lo, xn, g.Vh, nrhs, k, h, lo);
+  SpinorIO<64>::load(x_hi, nullptr, g.Vh, nrhs, k, h, hi);
 #pragma unroll
   for (int c = 0; c < 12; c++) {
     hi[c].re += double(lo[c].re);
     hi[c].im += double(lo[c].im);
     lo[c] = cmk(RR(0), RR(0));
   }
-  SpinorIO<64>::store(x_hi, nullptr, g.Vh, k, h, hi);
-  SpinorIO<PR>::store(x_lo, xn, g.Vh, k, h, lo);
+  SpinorIO<64>::store(x_hi, nullptr, g.Vh, nrhs, k, h, hi);
+  SpinorIO<PR>::store(x_lo, xn, g.Vh, nrhs, k, h, lo);
 }
 
 template <int PR>
@@ -98,8 +98,8 @@ __global__ void __launch_bounds__(BB) true_residual_kernel(Geom g, int nrhs, con
   double v = 0.0;
   if (h < g.Vh) {
     cx<double> bs[12], as[12];
-    SpinorIO<64>::load(b, nullptr, g.Vh, k, h, bs);
-    SpinorIO<64>::load(Ap, nullptr, g.Vh, k, h, as);
+    SpinorIO<64>::load(b, nullptr, g.Vh, nrhs, k, h, bs);
+    SpinorIO<64>::load(Ap, nullptr, g.Vh, nrhs, k, h, as);
     cx<RR> rs[12];
 #pragma unroll
     for (int c = 0; c < 12; c++) {
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(BB) true_residual_kernel(Geom g, int nrhs, con
       v += norm2(d);
       rs[c] = cmk(RR(d.re), RR(d.im));
     }
-    SpinorIO<PR>::store(r_lo, rn, g.Vh, k, h, rs);
+    SpinorIO<PR>::store(r_lo, rn, g.Vh, nrhs, k, h, rs);
   }
   grid_reduce<BB>(v, nrhs, red);
 }
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(BB) norm2_kernel(Geom g, int nrhs, const doubl
   double v = 0.0;
   if (h < g.Vh) {
     cx<double> s[12];
-    SpinorIO<64>::load(a, nullptr, g.Vh, k, h, s);
+    SpinorIO<64>::load(a, nullptr, g.Vh, nrhs, k, h, s);
 #pragma unroll
     for (int c = 0; c < 12; c++) v += norm2(s[c]);
   }
@@ -132,8 +132,8 @@ __global__ void __launch_bounds__(BB) redot_kernel(Geom g, int nrhs, const doubl
   double v = 0.0;
   if (h < g.Vh) {
     cx<double> s[12], t[12];
-    SpinorIO<64>::load(a, nullptr, g.Vh, k, h, s);
-    SpinorIO<64>::load(b, nullptr, g.Vh, k, h, t);
+    SpinorIO<64>::load(a, nullptr, g.Vh, nrhs, k, h, s);
+    SpinorIO<64>::load(b, nullptr, g.Vh, nrhs, k, h, t);
 #pragma unroll
     for (int c = 0; c < 12; c++) v += s[c].re * t[c].re + s[c].im * t[c].im;
   }

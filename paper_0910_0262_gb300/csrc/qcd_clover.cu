@@ -215,11 +215,11 @@ __global__ void clover_apply_kernel(Geom g, const void* clov, const void* in, co
   if (tid >= g.Vh * nrhs) return;
   const int r = tid % nrhs, h = tid / nrhs;
   cx<R> s[12], o[12];
-  SpinorIO<P>::load(in, in_norm, g.Vh, r, h, s);
+  SpinorIO<P>::load(in, in_norm, g.Vh, nrhs, r, h, s);
   constexpr int CP = P;
   CloverIO<CP>::apply(clov, g.Vh, h, 0, s, o);
   CloverIO<CP>::apply(clov, g.Vh, h, 1, s + 6, o + 6);
-  SpinorIO<P>::store(out, out_norm, g.Vh, r, h, o);
+  SpinorIO<P>::store(out, out_norm, g.Vh, nrhs, r, h, o);
 }
 
 }  // namespace

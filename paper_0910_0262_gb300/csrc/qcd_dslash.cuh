@@ -141,7 +141,7 @@ __device__ __forceinline__ void hop_direction(const DslashArgs& A, const Site& s
   {
     const int nb = neighbor_fwd(g, s, MU) >> 1;
     GaugeIO<P, RECON>::load(A.gauge, g.Vh, A.p, MU, s.i >> 1, u);
-    SpinorIO<P>::load(A.in, A.in_norm, g.Vh, r, nb, sp);
+    SpinorIO<P>::load(A.in, A.in_norm, g.Vh, A.nrhs, r, nb, sp);
     if (A.in_g5) apply_g5(sp);
     project<MU, -1>(sp, h);
     su3_mul(u, h, w);
@@ -156,7 +156,7 @@ __device__ __forceinline__ void hop_direction(const DslashArgs& A, const Site& s
   {
     const int nb = neighbor_bwd(g, s, MU) >> 1;
     GaugeIO<P, RECON>::load(A.gauge, g.Vh, q, MU, nb, u);
-    SpinorIO<P>::load(A.in, A.in_norm, g.Vh, r, nb, sp);
+    SpinorIO<P>::load(A.in, A.in_norm, g.Vh, A.nrhs, r, nb, sp);
     if (A.in_g5) apply_g5(sp);
     project<MU, +1>(sp, h);
     su3_adj_mul(u, h, w);
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs A) {
       clover_apply<P>(A.clover, A.g.Vh, hh, acc, res);
     } else {
       cx<R> xs[12], cxs[12];
-      SpinorIO<P>::load(A.x, A.x_norm, A.g.Vh, r, hh, xs);
+      SpinorIO<P>::load(A.x, A.x_norm, A.g.Vh, A.nrhs, r, hh, xs);
       if (A.x_g5) apply_g5(xs);
       clover_apply<P>(A.clover, A.g.Vh, hh, xs, cxs);
       const R a = R(A.a);
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs A) {
       }
     }
     if (A.out_g5) apply_g5(res);
-    SpinorIO<P>::store(A.out, A.out_norm, A.g.Vh, r, hh, res);
+    SpinorIO<P>::store(A.out, A.out_norm, A.g.Vh, A.nrhs, r, hh, res);
     if (A.do_norm) {
 #pragma unroll
       for (int c = 0; c < 12; c++) nrm += double(res[c].re) * res[c].re + double(res[c].im) * res[c].im;
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
       CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, v, res);
     } else {  // EPI_XPAY, EPI_XPAY_CG
       cx<R> xs[6], cxs[6];
-      SpinorIO<P>::load_block(A.x, A.x_norm, A.g.Vh, r, hh, b, xs);
+      SpinorIO<P>::load_block(A.x, A.x_norm, A.g.Vh, A.nrhs, r, hh, b, xs);
       if (A.x_g5 && b == 1) {
 #pragma unroll
         for (int k = 0; k < 6; k++) xs[k] = -xs[k];
@@ -305,9 +305,9 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
         const RR al = RR(st.alpha);
         cx<R> ps[6];
         cx<RR> xs[6], rs[6];
-        SpinorIO<P>::load_block(A.cg_p, A.cg_p_norm, A.g.Vh, r, hh, b, ps);
-        SpinorIO<PR>::load_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
-        SpinorIO<PR>::load_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
+        SpinorIO<P>::load_block(A.cg_p, A.cg_p_norm, A.g.Vh, A.nrhs, r, hh, b, ps);
+        SpinorIO<PR>::load_block(A.cg_x, nullptr, A.g.Vh, A.nrhs, r, hh, b, xs);
+        SpinorIO<PR>::load_block(A.cg_r, nullptr, A.g.Vh, A.nrhs, r, hh, b, rs);
 #pragma unroll
         for (int k = 0; k < 6; k++) {
           xs[k].re = fma(al, RR(ps[k].re), xs[k].re);
@@ -316,8 +316,8 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
           rs[k].im = fma(-al, RR(res[k].im), rs[k].im);
           nrm += double(rs[k].re) * rs[k].re + double(rs[k].im) * rs[k].im;
         }
-        SpinorIO<PR>::store_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
-        SpinorIO<PR>::store_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
+        SpinorIO<PR>::store_block(A.cg_x, nullptr, A.g.Vh, A.nrhs, r, hh, b, xs);
+        SpinorIO<PR>::store_block(A.cg_r, nullptr, A.g.Vh, A.nrhs, r, hh, b, rs);
       }
     } else {
       if (A.do_norm) {
@@ -331,26 +331,26 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
   __syncthreads();
   if (valid && EPI != EPI_XPAY_CG) {
     if (P == 64) {
-      double2* q = static_cast<double2*>(A.out) + (size_t)r * 12 * A.g.Vh + hh;
+      double2* q = static_cast<double2*>(A.out);
 #pragma unroll
       for (int k = 0; k < 3; k++) {
         const cx<R> v = part[0][3 * w + k][lane];
-        q[(size_t)(3 * w + k) * A.g.Vh] = make_double2(double(v.re), double(v.im));
+        q[sidx(3 * w + k, A.g.Vh, A.nrhs, r, hh)] = make_double2(double(v.re), double(v.im));
       }
     } else if (P == 32) {
       if (w < 3) {
-        float4* q = static_cast<float4*>(A.out) + (size_t)r * 6 * A.g.Vh + hh;
+        float4* q = static_cast<float4*>(A.out);
 #pragma unroll
         for (int k = 0; k < 2; k++) {
           const cx<R> v0 = part[0][4 * w + 2 * k][lane], v1 = part[0][4 * w + 2 * k + 1][lane];
-          q[(size_t)(2 * w + k) * A.g.Vh] = make_float4(float(v0.re), float(v0.im), float(v1.re), float(v1.im));
+          q[sidx(2 * w + k, A.g.Vh, A.nrhs, r, hh)] = make_float4(float(v0.re), float(v0.im), float(v1.re), float(v1.im));
         }
       }
     } else if (w == 0) {
       cx<float> o[12];
 #pragma unroll
       for (int c = 0; c < 12; c++) o[c] = cmk(float(part[0][c][lane].re), float(part[0][c][lane].im));
-      SpinorIO<16>::store(A.out, A.out_norm, A.g.Vh, r, hh, o);
+      SpinorIO<16>::store(A.out, A.out_norm, A.g.Vh, A.nrhs, r, hh, o);
     }
   }
   if (A.do_norm || EPI == EPI_XPAY_CG) grid_reduce<128>(nrm, A.nrhs, A.red);

@@ -46,8 +46,8 @@ __device__ __forceinline__ C coef_mul(int code, C v) {
   }
 }
 
-__device__ __forceinline__ void load_spinor64(const double2* f, int Vh, int r, int h, C s[12]) {
-  SpinorIO<64>::load(f, nullptr, Vh, r, h, s);
+__device__ __forceinline__ void load_spinor64(const double2* f, int Vh, int nrhs, int r, int h, C s[12]) {
+  SpinorIO<64>::load(f, nullptr, Vh, nrhs, r, h, s);
 }
 
 __device__ __forceinline__ void store_m3(double2* buf, int plane, size_t V, int i, const M3& m) {
@@ -87,7 +87,7 @@ __device__ __forceinline__ int lex_index(const Geom& g, int x, int y, int z, int
 // 1. C_{mu nu}(x) for the 6 planes at every site
 __global__ void __launch_bounds__(FB) clover_coeff_kernel(Geom g, double kappa, double csw, int nrhs,
                                                           const double2* Xe, const double2* Xo, const double2* Ye,
-                                                          const double2* Yo, double2* Cbuf) {
+                                                          const double2* Yo, double2* Cbuf, int accumulate) {
   const int i = blockIdx.x * FB + threadIdx.x;
   const int V = 2 * g.Vh;
   if (i >= V) return;
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(FB) clover_coeff_kernel(Geom g, double kappa, 
     for (int k = 0; k < 9; k++) S[pl].e[k] = cmk(0.0, 0.0);
   for (int r = 0; r < nrhs; r++) {
     C X[12], W[12];
-    load_spinor64(p == 0 ? Xe : Xo, g.Vh, r, h, X);
-    load_spinor64(p == 0 ? Ye : Yo, g.Vh, r, h, W);
+    load_spinor64(p == 0 ? Xe : Xo, g.Vh, nrhs, r, h, X);
+    load_spinor64(p == 0 ? Ye : Yo, g.Vh, nrhs, r, h, W);
     if (p == 1) {
 #pragma unroll
       for (int k = 0; k < 12; k++) W[k] = k2 * W[k];
@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(FB) clover_coeff_kernel(Geom g, double kappa, 
         const C h2 = S[pl].e[3 * a + b] + conj(S[pl].e[3 * b + a]);
         Cm.e[3 * a + b] = cmk(f * h2.im, -f * h2.re);  // -i f h2
       }
+    if (accumulate) Cm = m3_add(Cm, load_m3(Cbuf, pl, V, i));
     store_m3(Cbuf, pl, V, i, Cm);
   }
 }
@@ -194,7 +195,7 @@ __device__ __forceinline__ M3 corner_staple(const M3& s1, const M3& s2, const M3
 __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, int nrhs, const double2* g64,
                                                         const double2* Xe, const double2* Xo, const double2* Ye,
                                                         const double2* Yo, const double2* Cbuf, double2* out,
-                                                        int gradient) {
+                                                        int gradient, int with_clover, int accumulate) {
   const int V = 2 * g.Vh;
   const long long tid = (long long)blockIdx.x * FB + threadIdx.x;
   if (tid >= 4LL * V) return;
@@ -214,10 +215,10 @@ __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, in
   const double scale = 2.0 * kappa * kappa * sgn;
   for (int r = 0; r < nrhs; r++) {
     C Xy[12], Yy[12], Xn[12], Yn[12];
-    load_spinor64(p == 0 ? Xe : Xo, g.Vh, r, i >> 1, Xy);
-    load_spinor64(p == 0 ? Ye : Yo, g.Vh, r, i >> 1, Yy);
-    load_spinor64(p == 0 ? Xo : Xe, g.Vh, r, j >> 1, Xn);
-    load_spinor64(p == 0 ? Yo : Ye, g.Vh, r, j >> 1, Yn);
+    load_spinor64(p == 0 ? Xe : Xo, g.Vh, nrhs, r, i >> 1, Xy);
+    load_spinor64(p == 0 ? Ye : Yo, g.Vh, nrhs, r, i >> 1, Yy);
+    load_spinor64(p == 0 ? Xo : Xe, g.Vh, nrhs, r, j >> 1, Xn);
+    load_spinor64(p == 0 ? Yo : Ye, g.Vh, nrhs, r, j >> 1, Yn);
     switch (lam) {
       case 0: hop_terms<0>(Xy, Yy, Xn, Yn, scale, Ah, Bh); break;
       case 1: hop_terms<1>(Xy, Yy, Xn, Yn, scale, Ah, Bh); break;
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, in
     q[d2] += s2;
     return link_at(g, g64, q[0], q[1], q[2], q[3], dir);
   };
-  for (int pl = 0; pl < 6; pl++) {
+  for (int pl = 0; pl < 6 && with_clover; pl++) {
     int mu, nu;
     plane_dirs(pl, mu, nu);
     if (mu != lam && nu != lam) continue;
@@ -283,8 +284,16 @@ __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, in
     for (int a = 0; a < 3; a++) res.e[4 * a].im -= ti;
   }
   double2* q = out + ((size_t)i * 4 + lam) * 9;
+  if (accumulate) {
 #pragma unroll
-  for (int k = 0; k < 9; k++) q[k] = make_double2(res.e[k].re, res.e[k].im);
+    for (int k = 0; k < 9; k++) {
+      const double2 o = q[k];
+      q[k] = make_double2(o.x + res.e[k].re, o.y + res.e[k].im);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 9; k++) q[k] = make_double2(res.e[k].re, res.e[k].im);
+  }
 }
 
 }  // namespace
@@ -292,22 +301,24 @@ __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, in
 size_t force_clover_bytes(const Geom& g) { return (size_t)6 * 9 * 2 * g.Vh * sizeof(double2); }
 
 void launch_force_coeff(const Geom& g, double kappa, double csw, int nrhs, const double2* Xe, const double2* Xo,
-                        const double2* Ye, const double2* Yo, double2* Cbuf, cudaStream_t st) {
+                        const double2* Ye, const double2* Yo, double2* Cbuf, bool accumulate, cudaStream_t st) {
   g_kernel_launches += 1;
   const int V = 2 * g.Vh;
-  clover_coeff_kernel<<<(V + FB - 1) / FB, FB, 0, st>>>(g, kappa, csw, nrhs, Xe, Xo, Ye, Yo, Cbuf);
+  clover_coeff_kernel<<<(V + FB - 1) / FB, FB, 0, st>>>(g, kappa, csw, nrhs, Xe, Xo, Ye, Yo, Cbuf,
+                                                        accumulate ? 1 : 0);
 }
 
 void launch_force_links(const Geom& g, double kappa, int nrhs, const void* g64, const double2* Xe, const double2* Xo,
                         const double2* Ye, const double2* Yo, const double2* Cbuf, double2* out, bool gradient,
-                        cudaStream_t st) {
+                        bool with_clover, bool accumulate, cudaStream_t st) {
   g_kernel_launches += 1;
   const int V = 2 * g.Vh;
   link_force_kernel<<<(int)((4LL * V + FB - 1) / FB), FB, 0, st>>>(g, kappa, nrhs, static_cast<const double2*>(g64),
-                                                                    Xe, Xo, Ye, Yo, Cbuf, out, gradient ? 1 : 0);
+                                                                    Xe, Xo, Ye, Yo, Cbuf, out, gradient ? 1 : 0,
+                                                                    with_clover ? 1 : 0, accumulate ? 1 : 0);
 }
 
-double force_link_flops(int nrhs) { return 6.0 * 1800.0 + 744.0 * nrhs + 274.0; }
+double force_link_flops(int nrhs, bool with_clover) { return (with_clover ? 6.0 * 1800.0 : 0.0) + 744.0 * nrhs + 274.0; }
 double force_coeff_flops(int nrhs) { return 6.0 * (4 * 3 * 3 * 8.0) * nrhs + 6.0 * 60.0; }
 
 }  // namespace qcd

@@ -15,14 +15,17 @@ size_t force_clover_bytes(const Geom& g);
 // Force for S = sum_r phi_r^dag (Mhat^dag Mhat)^-1 phi_r, given per RHS the native FP64 fields
 // X_e, X_o = A_oo^-1 D_oe X_e, Y_e = Mhat X_e, Y_o = A_oo^-1 D_eo^dag Y_e.
 // 1. C_{mu nu} per site and plane into Cbuf (force_clover_bytes).
+// The fields of one batch of nrhs right-hand sides; accumulate adds to Cbuf (later batches).
 void launch_force_coeff(const Geom& g, double kappa, double csw, int nrhs, const double2* Xe, const double2* Xo,
-                        const double2* Ye, const double2* Yo, double2* Cbuf, cudaStream_t st);
-// 2. per link: G, or F = -1/2 P_TA(U G^dag), into out (canonical [V][4][3][3] complex128).
+                        const double2* Ye, const double2* Yo, double2* Cbuf, bool accumulate, cudaStream_t st);
+// 2. per link: G, or F = -1/2 P_TA(U G^dag) (linear in G), into out (canonical [V][4][3][3]
+// complex128): the hopping part of this batch, plus the clover part from Cbuf when with_clover;
+// accumulate adds to out.
 void launch_force_links(const Geom& g, double kappa, int nrhs, const void* g64, const double2* Xe, const double2* Xo,
                         const double2* Ye, const double2* Yo, const double2* Cbuf, double2* out, bool gradient,
-                        cudaStream_t st);
+                        bool with_clover, bool accumulate, cudaStream_t st);
 // conventional FP64 flop counts: per link of kernel 2, per site of kernel 1
-double force_link_flops(int nrhs);
+double force_link_flops(int nrhs, bool with_clover);
 double force_coeff_flops(int nrhs);
 
 }  // namespace qcd

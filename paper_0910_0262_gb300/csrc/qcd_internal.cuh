@@ -4,9 +4,9 @@
 //
 // Layout (all fields checkerboarded: parity p = (x+y+z+t) mod 2, half index
 // h = i >> 1 of the lexicographic index i = x + X (y + Y (z + Z t)); X even):
-//   spinor FP64 : [rhs][12][Vh] double2     component c = 3*spin + colour
-//   spinor FP32 : [rhs][6][Vh]  float4      two complex components per float4
-//   spinor FP16 : [rhs][3][Vh]  uint4 (8 halves = 4 complex) + [rhs][Vh] float norm
+//   spinor FP64 : [12][Vh][rhs] double2     component c = 3*spin + colour
+//   spinor FP32 : [6][Vh][rhs]  float4      two complex components per float4
+//   spinor FP16 : [3][Vh][rhs]  uint4 (8 halves = 4 complex) + [Vh][rhs] float norm
 //   gauge  FP64 : [p][mu][9][Vh] double2    element (i,j) at 3i+j
 //   gauge  FP32 : recon 18 [p][mu][9][Vh] float2, recon 12 [p][mu][3][Vh] float4
 //   gauge  FP16 : recon 18 [p][mu][9][Vh] half2,  recon 12 [p][mu][3][Vh] uint2
@@ -123,74 +123,85 @@ struct Real<32> { using T = float; };
 template <>
 struct Real<16> { using T = float; };
 
-// spinor accessors: 12 complex components, component c = 3*spin + colour
+// spinor accessors: 12 complex components, component c = 3*spin + colour.  A field of nrhs
+// right-hand sides is stored RHS-minor: vector k of (site h, RHS r) at (k * Vh + h) * nrhs + r, so
+// the lanes of a warp that cover consecutive (site, RHS) pairs read one contiguous run.
+__device__ __forceinline__ size_t sidx(int k, int Vh, int nrhs, int r, int h) {
+  return ((size_t)k * Vh + h) * nrhs + r;
+}
+
 template <int P>
 struct SpinorIO;
 
 template <>
 struct SpinorIO<64> {
   static constexpr int NVEC = 12;  // double2 per site
-  __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<double> s[12]) {
-    const double2* p = static_cast<const double2*>(base) + (size_t)r * NVEC * Vh + h;
+  __device__ static void load(const void* base, const float*, int Vh, int nrhs, int r, int h, cx<double> s[12]) {
+    const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 12; c++) {
-      double2 v = __ldg(p + (size_t)c * Vh);
+      double2 v = __ldg(p + sidx(c, Vh, nrhs, r, h));
       s[c] = cmk(v.x, v.y);
     }
   }
-  __device__ static void store(void* base, float*, int Vh, int r, int h, const cx<double> s[12]) {
-    double2* p = static_cast<double2*>(base) + (size_t)r * NVEC * Vh + h;
+  __device__ static void store(void* base, float*, int Vh, int nrhs, int r, int h, const cx<double> s[12]) {
+    double2* p = static_cast<double2*>(base);
 #pragma unroll
-    for (int c = 0; c < 12; c++) p[(size_t)c * Vh] = make_double2(s[c].re, s[c].im);
-  }
-  __device__ static void store_block(void* base, float*, int Vh, int r, int h, int b, const cx<double> s[6]) {
-    double2* p = static_cast<double2*>(base) + (size_t)r * NVEC * Vh + (size_t)(6 * b) * Vh + h;
-#pragma unroll
-    for (int c = 0; c < 6; c++) p[(size_t)c * Vh] = make_double2(s[c].re, s[c].im);
+    for (int c = 0; c < 12; c++) p[sidx(c, Vh, nrhs, r, h)] = make_double2(s[c].re, s[c].im);
   }
   // components 6b..6b+5 (chiral block b: spins 2b, 2b+1)
-  __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b, cx<double> s[6]) {
-    const double2* p = static_cast<const double2*>(base) + (size_t)r * NVEC * Vh + (size_t)(6 * b) * Vh + h;
+  __device__ static void load_block(const void* base, const float*, int Vh, int nrhs, int r, int h, int b,
+                                    cx<double> s[6]) {
+    const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 6; c++) {
-      double2 v = __ldg(p + (size_t)c * Vh);
+      double2 v = __ldg(p + sidx(6 * b + c, Vh, nrhs, r, h));
       s[c] = cmk(v.x, v.y);
     }
+  }
+  __device__ static void store_block(void* base, float*, int Vh, int nrhs, int r, int h, int b,
+                                     const cx<double> s[6]) {
+    double2* p = static_cast<double2*>(base);
+#pragma unroll
+    for (int c = 0; c < 6; c++) p[sidx(6 * b + c, Vh, nrhs, r, h)] = make_double2(s[c].re, s[c].im);
   }
 };
 
 template <>
 struct SpinorIO<32> {
   static constexpr int NVEC = 6;  // float4 per site
-  __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<float> s[12]) {
-    const float4* p = static_cast<const float4*>(base) + (size_t)r * NVEC * Vh + h;
+  __device__ static void load(const void* base, const float*, int Vh, int nrhs, int r, int h, cx<float> s[12]) {
+    const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 6; k++) {
-      float4 v = __ldg(p + (size_t)k * Vh);
+      float4 v = __ldg(p + sidx(k, Vh, nrhs, r, h));
       s[2 * k] = cmk(v.x, v.y);
       s[2 * k + 1] = cmk(v.z, v.w);
     }
   }
-  __device__ static void store(void* base, float*, int Vh, int r, int h, const cx<float> s[12]) {
-    float4* p = static_cast<float4*>(base) + (size_t)r * NVEC * Vh + h;
+  __device__ static void store(void* base, float*, int Vh, int nrhs, int r, int h, const cx<float> s[12]) {
+    float4* p = static_cast<float4*>(base);
 #pragma unroll
     for (int k = 0; k < 6; k++)
-      p[(size_t)k * Vh] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
+      p[sidx(k, Vh, nrhs, r, h)] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
   }
-  __device__ static void store_block(void* base, float*, int Vh, int r, int h, int b, const cx<float> s[6]) {
-    float4* p = static_cast<float4*>(base) + (size_t)r * NVEC * Vh + (size_t)(3 * b) * Vh + h;
-#pragma unroll
-    for (int k = 0; k < 3; k++)
-      p[(size_t)k * Vh] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
-  }
-  __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b, cx<float> s[6]) {
-    const float4* p = static_cast<const float4*>(base) + (size_t)r * NVEC * Vh + (size_t)(3 * b) * Vh + h;
+  __device__ static void load_block(const void* base, const float*, int Vh, int nrhs, int r, int h, int b,
+                                    cx<float> s[6]) {
+    const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      float4 v = __ldg(p + (size_t)k * Vh);
+      float4 v = __ldg(p + sidx(3 * b + k, Vh, nrhs, r, h));
       s[2 * k] = cmk(v.x, v.y);
       s[2 * k + 1] = cmk(v.z, v.w);
     }
+  }
+  __device__ static void store_block(void* base, float*, int Vh, int nrhs, int r, int h, int b,
+                                     const cx<float> s[6]) {
+    float4* p = static_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; k++)
+      p[sidx(3 * b + k, Vh, nrhs, r, h)] =
+          make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
   }
 };
 
@@ -203,16 +214,17 @@ __device__ __forceinline__ uint32_t f2h(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// FP16 spinor: each real is stored as half(v / n) with n = max |v| over the site's 24 reals
+// FP16 spinor: each real is stored as half(v / n) with n = max |v| over the site's 24 reals;
+// the norms of a field are stored [Vh][nrhs]
 template <>
 struct SpinorIO<16> {
   static constexpr int NVEC = 3;  // uint4 per site
-  __device__ static void load(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
-    const uint4* p = static_cast<const uint4*>(base) + (size_t)r * NVEC * Vh + h;
-    float n = __ldg(nrm + (size_t)r * Vh + h);
+  __device__ static void load(const void* base, const float* nrm, int Vh, int nrhs, int r, int h, cx<float> s[12]) {
+    const uint4* p = static_cast<const uint4*>(base);
+    const float n = __ldg(nrm + (size_t)h * nrhs + r);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint4 v = __ldg(p + (size_t)k * Vh);
+      uint4 v = __ldg(p + sidx(k, Vh, nrhs, r, h));
       float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
       s[4 * k + 0] = cmk(a.x * n, a.y * n);
       s[4 * k + 1] = cmk(b.x * n, b.y * n);
@@ -220,12 +232,12 @@ struct SpinorIO<16> {
       s[4 * k + 3] = cmk(d.x * n, d.y * n);
     }
   }
-  __device__ static void store(void* base, float* nrm, int Vh, int r, int h, const cx<float> s[12]) {
+  __device__ static void store(void* base, float* nrm, int Vh, int nrhs, int r, int h, const cx<float> s[12]) {
     float m = 0.f;
 #pragma unroll
     for (int c = 0; c < 12; c++) m = fmaxf(m, fmaxf(fabsf(s[c].re), fabsf(s[c].im)));
     float inv = m > 0.f ? 1.0f / m : 0.f;
-    uint4* p = static_cast<uint4*>(base) + (size_t)r * NVEC * Vh + h;
+    uint4* p = static_cast<uint4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
       uint4 v;
@@ -233,16 +245,17 @@ struct SpinorIO<16> {
       v.y = f2h(s[4 * k + 1].re * inv, s[4 * k + 1].im * inv);
       v.z = f2h(s[4 * k + 2].re * inv, s[4 * k + 2].im * inv);
       v.w = f2h(s[4 * k + 3].re * inv, s[4 * k + 3].im * inv);
-      p[(size_t)k * Vh] = v;
+      p[sidx(k, Vh, nrhs, r, h)] = v;
     }
-    nrm[(size_t)r * Vh + h] = m;
+    nrm[(size_t)h * nrhs + r] = m;
   }
   // block 0 = chunk 0 and the first half of chunk 1; block 1 = the second half of chunk 1 and chunk 2
-  __device__ static void load_block(const void* base, const float* nrm, int Vh, int r, int h, int b, cx<float> s[6]) {
-    const uint4* p = static_cast<const uint4*>(base) + (size_t)r * NVEC * Vh + h;
-    const float n = __ldg(nrm + (size_t)r * Vh + h);
-    const uint4 mid = __ldg(p + (size_t)Vh);
-    const uint4 end = __ldg(p + (size_t)(b == 0 ? 0 : 2) * Vh);
+  __device__ static void load_block(const void* base, const float* nrm, int Vh, int nrhs, int r, int h, int b,
+                                    cx<float> s[6]) {
+    const uint4* p = static_cast<const uint4*>(base);
+    const float n = __ldg(nrm + (size_t)h * nrhs + r);
+    const uint4 mid = __ldg(p + sidx(1, Vh, nrhs, r, h));
+    const uint4 end = __ldg(p + sidx(b == 0 ? 0 : 2, Vh, nrhs, r, h));
     float2 e0 = h2f(end.x), e1 = h2f(end.y), e2 = h2f(end.z), e3 = h2f(end.w);
     if (b == 0) {
       float2 m0 = h2f(mid.x), m1 = h2f(mid.y);
