@@ -560,11 +560,14 @@ qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
     CUDA_TRY(cudaMalloc(&c->A16, (size_t)2 * 9 * g.Vh * sizeof(uint4)));
     CUDA_TRY(cudaMalloc(&c->Ainv16, (size_t)2 * 9 * g.Vh * sizeof(uint4)));
   }
+  void* work;
+  if ((s = ws_get(c, S_F_CL, force_clover_bytes(g), &work))) return s;
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->st));
   {
-    ProfScope ps(c, "clover_build", 0, 0);
-    launch_clover_build(g, c->g64, kappa, csw, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, c->flags,
-                        c->st);
+    // 6 planes x 4 leaves x 3 products of 3x3 complex matrices per site, plus the two inversions
+    ProfScope ps(c, "clover_build", 0, 2.0 * g.Vh * (72 * 216.0 + 2 * 1000.0));
+    launch_clover_build(g, c->g64, kappa, csw, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, work,
+                        c->flags, c->st);
   }
   CUDA_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   if ((s = sync_and_check(c, "clover_build"))) return s;

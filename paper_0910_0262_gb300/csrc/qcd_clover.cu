@@ -150,6 +150,86 @@ __device__ __forceinline__ void store_block16(uint4* base, int Vh, int h, int b,
   }
 }
 
+// F_{mu nu} for one (site, plane) per thread into Fbuf[plane][9][V] (V = all sites, lexicographic)
+__global__ void __launch_bounds__(128) field_strength_kernel(Geom g, const double2* __restrict__ g64, double2* Fbuf) {
+  const int V = 2 * g.Vh;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= 6LL * V) return;
+  const int pl = (int)(tid / V), i = (int)(tid - (long long)pl * V);
+  const int PM[6] = {0, 0, 0, 1, 1, 2}, PN[6] = {1, 2, 3, 2, 3, 3};
+  int c[4];
+  c[0] = i % g.X;
+  int rest = i / g.X;
+  c[1] = rest % g.Y;
+  rest /= g.Y;
+  c[2] = rest % g.Z;
+  c[3] = rest / g.Z;
+  const M3 F = field_strength(g, g64, c, PM[pl], PN[pl]);
+  double2* q = Fbuf + (size_t)pl * 9 * V + i;
+#pragma unroll
+  for (int k = 0; k < 9; k++) q[(size_t)k * V] = make_double2(F.e[k].re, F.e[k].im);
+}
+
+// A's chiral block b and its inverse for one (site, block) per thread, from the six F_{mu nu}
+__global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const double2* __restrict__ Fbuf, double kappa,
+                                                              double csw, double2* A64, double2* Ainv64, float4* A32,
+                                                              float4* Ainv32, uint4* A16, uint4* Ainv16,
+                                                              int* notposdef) {
+  const int V = 2 * g.Vh;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= 2 * V) return;
+  const int b = tid / V, i = tid - b * V;  // block b of lexicographic site i
+  int c[4];
+  c[0] = i % g.X;
+  int rest = i / g.X;
+  c[1] = rest % g.Y;
+  rest /= g.Y;
+  c[2] = rest % g.Z;
+  c[3] = rest / g.Z;
+  const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const int h = i >> 1;
+  auto Fe = [&](int pl, int e) {
+    const double2 v = __ldg(Fbuf + ((size_t)pl * 9 + e) * V + i);
+    return cmk(v.x, v.y);
+  };
+  // planes xy xz xt yz yt zt = 0..5
+  const double sg = b == 0 ? -1.0 : 1.0;
+  C B1[9], B2[9], B3[9];
+  for (int e = 0; e < 9; e++) {
+    B1[e] = Fe(3, e) + sg * Fe(2, e);
+    B2[e] = Fe(1, e) - sg * Fe(4, e);
+    B3[e] = Fe(0, e) + sg * Fe(5, e);
+  }
+  const double kc = kappa * csw;
+  double d[6];
+  C L[15];
+  for (int ii6 = 0; ii6 < 6; ii6++) {
+    const int ii = ii6 % 3;
+    d[ii6] = 1.0 - kc * (ii6 < 3 ? B3[4 * ii].re : -B3[4 * ii].re);
+    for (int j = 0; j < ii6; j++) {
+      const int jj = j % 3;
+      C hv;
+      if (ii6 < 3) hv = B3[3 * ii + jj];
+      else if (j < 3) hv = B1[3 * ii + jj] + times_i(B2[3 * ii + jj]);
+      else hv = -B3[3 * ii + jj];
+      L[tri(ii6, j)] = cmk(-kc * hv.re, -kc * hv.im);
+    }
+  }
+  double di[6];
+  C Li[15];
+  if (!invert6(d, L, di, Li)) {
+    *notposdef = 1;
+    for (int k = 0; k < 6; k++) di[k] = 0.0;
+    for (int k = 0; k < 15; k++) Li[k] = cmk(0.0, 0.0);
+  }
+  store_block64(A64 + (size_t)p * 36 * g.Vh, g.Vh, h, b, d, L);
+  store_block64(Ainv64 + (size_t)p * 36 * g.Vh, g.Vh, h, b, di, Li);
+  if (A32) store_block32(A32 + (size_t)p * 18 * g.Vh, g.Vh, h, b, d, L);
+  if (Ainv32) store_block32(Ainv32 + (size_t)p * 18 * g.Vh, g.Vh, h, b, di, Li);
+  if (A16) store_block16(A16 + (size_t)p * 9 * g.Vh, g.Vh, h, b, d, L);
+  if (Ainv16) store_block16(Ainv16 + (size_t)p * 9 * g.Vh, g.Vh, h, b, di, Li);
+}
+
 __global__ void __launch_bounds__(128) clover_build_kernel(Geom g, const double2* __restrict__ g64, double kappa,
                                                            double csw, double2* A64, double2* Ainv64, float4* A32,
                                                            float4* Ainv32, uint4* A16, uint4* Ainv16,
@@ -215,19 +295,31 @@ __global__ void clover_apply_kernel(Geom g, const void* clov, const void* in, co
   if (tid >= g.Vh * nrhs) return;
   const int r = tid % nrhs, h = tid / nrhs;
   cx<R> s[12], o[12];
-  SpinorIO<P>::load(in, in_norm, g.Vh, nrhs, r, h, s);
+  SpinorIO<P>::load(in, in_norm, g.Vh, r, h, s);
   constexpr int CP = P;
   CloverIO<CP>::apply(clov, g.Vh, h, 0, s, o);
   CloverIO<CP>::apply(clov, g.Vh, h, 1, s + 6, o + 6);
-  SpinorIO<P>::store(out, out_norm, g.Vh, nrhs, r, h, o);
+  SpinorIO<P>::store(out, out_norm, g.Vh, r, h, o);
 }
 
 }  // namespace
 
 void launch_clover_build(const Geom& g, const void* g64, double kappa, double csw, void* A64, void* Ainv64, void* A32,
-                         void* Ainv32, void* A16, void* Ainv16, int* notposdef, cudaStream_t st) {
-  g_kernel_launches += 1;
+                         void* Ainv32, void* A16, void* Ainv16, void* work, int* notposdef, cudaStream_t st) {
   const int B = 128;
+  const long long V = 2LL * g.Vh;
+  if (work) {
+    // F per (site, plane), then one chiral block per thread
+    g_kernel_launches += 2;
+    field_strength_kernel<<<(int)((6 * V + B - 1) / B), B, 0, st>>>(g, static_cast<const double2*>(g64),
+                                                                      static_cast<double2*>(work));
+    clover_assemble_kernel<<<(int)((2 * V + B - 1) / B), B, 0, st>>>(
+        g, static_cast<const double2*>(work), kappa, csw, static_cast<double2*>(A64), static_cast<double2*>(Ainv64),
+        static_cast<float4*>(A32), static_cast<float4*>(Ainv32), static_cast<uint4*>(A16),
+        static_cast<uint4*>(Ainv16), notposdef);
+    return;
+  }
+  g_kernel_launches += 1;
   const int nb = (2 * g.Vh + B - 1) / B;
   clover_build_kernel<<<nb, B, 0, st>>>(g, static_cast<const double2*>(g64), kappa, csw, static_cast<double2*>(A64),
                                         static_cast<double2*>(Ainv64), static_cast<float4*>(A32),

@@ -131,42 +131,64 @@ __device__ __forceinline__ void apply_g5(cx<R> s[12]) {
   for (int c = 6; c < 12; c++) s[c] = -s[c];
 }
 
+// The two links along mu used by one output site, with the neighbours' half indices and the
+// time-boundary factors; loaded (and, for 12-real storage, reconstructed) once per site.
+template <typename R>
+struct DirLinks {
+  cx<R> uf[9], ub[9];  // U_mu(x), U_mu(x - mu)
+  int nbf, nbb;        // half indices of x + mu, x - mu
+  R sf, sb;            // boundary factors of the two hops
+};
+
 template <int P, int RECON, int MU>
-__device__ __forceinline__ void hop_direction(const DslashArgs& A, const Site& s, int r, cx<typename Real<P>::T> acc[12]) {
+__device__ __forceinline__ void load_dir(const DslashArgs& A, const Site& s, DirLinks<typename Real<P>::T>& L) {
   using R = typename Real<P>::T;
   const Geom& g = A.g;
-  const int q = 1 - A.p;
-  cx<R> u[9], sp[12], h[6], w[6];
-  // forward: (1 - g_mu) U_mu(x) psi(x + mu)
-  {
-    const int nb = neighbor_fwd(g, s, MU) >> 1;
-    GaugeIO<P, RECON>::load(A.gauge, g.Vh, A.p, MU, s.i >> 1, u);
-    SpinorIO<P>::load(A.in, A.in_norm, g.Vh, A.nrhs, r, nb, sp);
-    if (A.in_g5) apply_g5(sp);
-    project<MU, -1>(sp, h);
-    su3_mul(u, h, w);
-    if (MU == 3 && s.t == g.T - 1) {
-      const R sg = R(g.t_bc);
+  L.nbf = neighbor_fwd(g, s, MU) >> 1;
+  L.nbb = neighbor_bwd(g, s, MU) >> 1;
+  GaugeIO<P, RECON>::load(A.gauge, g.Vh, A.p, MU, s.i >> 1, L.uf);
+  GaugeIO<P, RECON>::load(A.gauge, g.Vh, 1 - A.p, MU, L.nbb, L.ub);
+  L.sf = (MU == 3 && s.t == g.T - 1) ? R(g.t_bc) : R(1);
+  L.sb = (MU == 3 && s.t == 0) ? R(g.t_bc) : R(1);
+}
+
+// psi_r at half index nb; returns the factor still to be applied (the FP16 per-site scale, which
+// commutes with the spin projection and the link multiply, so it is applied once to the result)
+template <int P>
+__device__ __forceinline__ typename Real<P>::T load_neighbor(const DslashArgs& A, int r, int nb,
+                                                             cx<typename Real<P>::T> sp[12]) {
+  using R = typename Real<P>::T;
+  if (P == 16) return SpinorIO<16>::load_unscaled(A.in, A.in_norm, A.g.Vh, r, nb, reinterpret_cast<cx<float>*>(sp));
+  SpinorIO<P>::load(A.in, A.in_norm, A.g.Vh, r, nb, sp);
+  return R(1);
+}
+
+// acc += (1 - g_mu) U_mu(x) psi_r(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi_r(x-mu)
+template <int P, int MU>
+__device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<typename Real<P>::T>& L, int r,
+                                        cx<typename Real<P>::T> acc[12]) {
+  using R = typename Real<P>::T;
+  cx<R> sp[12], h[6], w[6];
+  R f = load_neighbor<P>(A, r, L.nbf, sp);
+  if (A.in_g5) apply_g5(sp);
+  project<MU, -1>(sp, h);
+  su3_mul(L.uf, h, w);
+  if (MU == 3) f *= L.sf;
+  if (MU == 3 || P == 16) {
 #pragma unroll
-      for (int k = 0; k < 6; k++) w[k] = sg * w[k];
-    }
-    accumulate<MU, -1>(w, acc);
+    for (int k = 0; k < 6; k++) w[k] = f * w[k];
   }
-  // backward: (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)
-  {
-    const int nb = neighbor_bwd(g, s, MU) >> 1;
-    GaugeIO<P, RECON>::load(A.gauge, g.Vh, q, MU, nb, u);
-    SpinorIO<P>::load(A.in, A.in_norm, g.Vh, A.nrhs, r, nb, sp);
-    if (A.in_g5) apply_g5(sp);
-    project<MU, +1>(sp, h);
-    su3_adj_mul(u, h, w);
-    if (MU == 3 && s.t == 0) {
-      const R sg = R(g.t_bc);
+  accumulate<MU, -1>(w, acc);
+  f = load_neighbor<P>(A, r, L.nbb, sp);
+  if (A.in_g5) apply_g5(sp);
+  project<MU, +1>(sp, h);
+  su3_adj_mul(L.ub, h, w);
+  if (MU == 3) f *= L.sb;
+  if (MU == 3 || P == 16) {
 #pragma unroll
-      for (int k = 0; k < 6; k++) w[k] = sg * w[k];
-    }
-    accumulate<MU, +1>(w, acc);
+    for (int k = 0; k < 6; k++) w[k] = f * w[k];
   }
+  accumulate<MU, +1>(w, acc);
 }
 
 template <int P>
@@ -178,182 +200,160 @@ struct CloverPrec<32> { static constexpr int CP = 32; };
 template <>
 struct CloverPrec<16> { static constexpr int CP = 16; };
 
-template <int P, typename R>
-__device__ __forceinline__ void clover_apply(const void* clov, int Vh, int h, const cx<R> in[12], cx<R> out[12]) {
-  CloverIO<CloverPrec<P>::CP>::apply(clov, Vh, h, 0, in, out);
-  CloverIO<CloverPrec<P>::CP>::apply(clov, Vh, h, 1, in + 6, out + 6);
-}
-
-template <int P, int RECON, int EPI, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) dslash_kernel(DslashArgs A) {
-  using R = typename Real<P>::T;
-  if (A.halt && *A.halt) return;
-  const int gid = blockIdx.x * BLOCK + threadIdx.x;
-  const int r = gid % A.nrhs;
-  const int hh = gid / A.nrhs;
-  const bool valid = hh < A.g.Vh;
-  double nrm = 0.0;
-  if (valid) {
-    const Site s = site_of(A.g, A.p, hh);
-    cx<R> acc[12];
-#pragma unroll
-    for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
-    hop_direction<P, RECON, 0>(A, s, r, acc);
-    hop_direction<P, RECON, 1>(A, s, r, acc);
-    hop_direction<P, RECON, 2>(A, s, r, acc);
-    hop_direction<P, RECON, 3>(A, s, r, acc);
-    cx<R> res[12];
-    if (EPI == EPI_NONE) {
-#pragma unroll
-      for (int c = 0; c < 12; c++) res[c] = acc[c];
-    } else if (EPI == EPI_CLOVER_INV) {
-      clover_apply<P>(A.clover, A.g.Vh, hh, acc, res);
-    } else {
-      cx<R> xs[12], cxs[12];
-      SpinorIO<P>::load(A.x, A.x_norm, A.g.Vh, A.nrhs, r, hh, xs);
-      if (A.x_g5) apply_g5(xs);
-      clover_apply<P>(A.clover, A.g.Vh, hh, xs, cxs);
-      const R a = R(A.a);
-#pragma unroll
-      for (int c = 0; c < 12; c++) {
-        res[c].re = fma(a, acc[c].re, cxs[c].re);
-        res[c].im = fma(a, acc[c].im, cxs[c].im);
-      }
-    }
-    if (A.out_g5) apply_g5(res);
-    SpinorIO<P>::store(A.out, A.out_norm, A.g.Vh, A.nrhs, r, hh, res);
-    if (A.do_norm) {
-#pragma unroll
-      for (int c = 0; c < 12; c++) nrm += double(res[c].re) * res[c].re + double(res[c].im) * res[c].im;
-    }
-  }
-  if (A.do_norm) grid_reduce<BLOCK>(nrm, A.nrhs, A.red);
-}
-
-// Direction-split variant: a block of 128 threads handles 32 (site, RHS) pairs; warp w
-// computes the two hops along mu = w for its lane's pair (uniform per warp, no divergence), the
-// four partial sums meet in shared memory, warps 0 and 1 finish chiral block 0 and 1 (sum,
-// clover epilogue, gamma_5, norm), and the warps share the stores.  Four times the threads of
-// the one-site-per-thread kernel, so small lattices fill the GPU and each thread keeps fewer
-// live registers.
-template <int P, int RECON, int EPI>
+// Hopping kernel.  A block of 128 threads handles 32 consecutive output sites: warp w computes
+// the two hops along mu = w for its lane's site (uniform per warp, no divergence), the four
+// partial sums meet in shared memory, warps 0 and 1 finish chiral block 0 and 1 (sum, clover
+// epilogue, gamma_5, norm or CG update), and the warps share the stores.  The links of a site
+// are loaded (and reconstructed) once and reused for every right-hand side, which the kernel
+// loops over (MULTI instantiations, nrhs > 1); FP64 reloads them per RHS to keep its register
+// count low, and so does the single-RHS instantiation.
+template <int P, int RECON, int EPI, bool MULTI>
 __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
   using R = typename Real<P>::T;
+  constexpr bool KEEP_LINKS = MULTI && P != 64;
   __shared__ cx<R> part[4][12][32];
   if (A.halt && *A.halt) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int pair = blockIdx.x * 32 + lane;
-  const int r = pair % A.nrhs;
-  const int hh = pair / A.nrhs;
+  const int hh = blockIdx.x * 32 + lane;
   const bool valid = hh < A.g.Vh;
-  {
-    cx<R> acc[12];
-#pragma unroll
-    for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
-    if (valid) {
-      const Site s = site_of(A.g, A.p, hh);
+  Site s;
+  DirLinks<R> L;
+  if (valid) {
+    s = site_of(A.g, A.p, hh);
+    if (KEEP_LINKS) {
       switch (w) {
-        case 0: hop_direction<P, RECON, 0>(A, s, r, acc); break;
-        case 1: hop_direction<P, RECON, 1>(A, s, r, acc); break;
-        case 2: hop_direction<P, RECON, 2>(A, s, r, acc); break;
-        default: hop_direction<P, RECON, 3>(A, s, r, acc); break;
+        case 0: load_dir<P, RECON, 0>(A, s, L); break;
+        case 1: load_dir<P, RECON, 1>(A, s, L); break;
+        case 2: load_dir<P, RECON, 2>(A, s, L); break;
+        default: load_dir<P, RECON, 3>(A, s, L); break;
       }
     }
-#pragma unroll
-    for (int c = 0; c < 12; c++) part[w][c][lane] = acc[c];
   }
-  __syncthreads();
-  double nrm = 0.0;
-  if (w < 2 && valid) {
-    const int b = w;
-    cx<R> v[6], res[6];
+  const bool reduce = A.do_norm || EPI == EPI_XPAY_CG;
+  for (int r = 0; r < A.nrhs; r++) {
+    {
+      cx<R> acc[12];
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
-      const int c = 6 * b + k;
-      v[k] = (part[0][c][lane] + part[1][c][lane]) + (part[2][c][lane] + part[3][c][lane]);
-    }
-    if (EPI == EPI_NONE) {
-#pragma unroll
-      for (int k = 0; k < 6; k++) res[k] = v[k];
-    } else if (EPI == EPI_CLOVER_INV) {
-      CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, v, res);
-    } else {  // EPI_XPAY, EPI_XPAY_CG
-      cx<R> xs[6], cxs[6];
-      SpinorIO<P>::load_block(A.x, A.x_norm, A.g.Vh, A.nrhs, r, hh, b, xs);
-      if (A.x_g5 && b == 1) {
-#pragma unroll
-        for (int k = 0; k < 6; k++) xs[k] = -xs[k];
+      for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
+      if (valid) {
+        switch (w) {
+          case 0:
+            if (!KEEP_LINKS) load_dir<P, RECON, 0>(A, s, L);
+            hop_dir<P, 0>(A, L, r, acc);
+            break;
+          case 1:
+            if (!KEEP_LINKS) load_dir<P, RECON, 1>(A, s, L);
+            hop_dir<P, 1>(A, L, r, acc);
+            break;
+          case 2:
+            if (!KEEP_LINKS) load_dir<P, RECON, 2>(A, s, L);
+            hop_dir<P, 2>(A, L, r, acc);
+            break;
+          default:
+            if (!KEEP_LINKS) load_dir<P, RECON, 3>(A, s, L);
+            hop_dir<P, 3>(A, L, r, acc);
+            break;
+        }
       }
-      CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, xs, cxs);
-      const R a = R(A.a);
+#pragma unroll
+      for (int c = 0; c < 12; c++) part[w][c][lane] = acc[c];
+    }
+    __syncthreads();
+    double nrm = 0.0;
+    if (w < 2 && valid) {
+      const int b = w;
+      cx<R> v[6], res[6];
 #pragma unroll
       for (int k = 0; k < 6; k++) {
-        res[k].re = fma(a, v[k].re, cxs[k].re);
-        res[k].im = fma(a, v[k].im, cxs[k].im);
+        const int c = 6 * b + k;
+        v[k] = (part[0][c][lane] + part[1][c][lane]) + (part[2][c][lane] + part[3][c][lane]);
       }
-    }
-    if (A.out_g5 && b == 1) {
+      if (EPI == EPI_NONE) {
 #pragma unroll
-      for (int k = 0; k < 6; k++) res[k] = -res[k];
-    }
-    if (EPI == EPI_XPAY_CG) {
-      // res = (A p)_b: advance x and r of this RHS with alpha from the <p, A p> reduction
-      constexpr int PR = P == 64 ? 64 : 32;
-      using RR = typename Real<PR>::T;
-      const CGState& st = A.red.cg[r];
-      if (st.active) {
-        const RR al = RR(st.alpha);
-        cx<R> ps[6];
-        cx<RR> xs[6], rs[6];
-        SpinorIO<P>::load_block(A.cg_p, A.cg_p_norm, A.g.Vh, A.nrhs, r, hh, b, ps);
-        SpinorIO<PR>::load_block(A.cg_x, nullptr, A.g.Vh, A.nrhs, r, hh, b, xs);
-        SpinorIO<PR>::load_block(A.cg_r, nullptr, A.g.Vh, A.nrhs, r, hh, b, rs);
+        for (int k = 0; k < 6; k++) res[k] = v[k];
+      } else if (EPI == EPI_CLOVER_INV) {
+        CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, v, res);
+      } else {  // EPI_XPAY, EPI_XPAY_CG
+        cx<R> xs[6], cxs[6];
+        SpinorIO<P>::load_block(A.x, A.x_norm, A.g.Vh, r, hh, b, xs);
+        if (A.x_g5 && b == 1) {
+#pragma unroll
+          for (int k = 0; k < 6; k++) xs[k] = -xs[k];
+        }
+        CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, xs, cxs);
+        const R a = R(A.a);
 #pragma unroll
         for (int k = 0; k < 6; k++) {
-          xs[k].re = fma(al, RR(ps[k].re), xs[k].re);
-          xs[k].im = fma(al, RR(ps[k].im), xs[k].im);
-          rs[k].re = fma(-al, RR(res[k].re), rs[k].re);
-          rs[k].im = fma(-al, RR(res[k].im), rs[k].im);
-          nrm += double(rs[k].re) * rs[k].re + double(rs[k].im) * rs[k].im;
-        }
-        SpinorIO<PR>::store_block(A.cg_x, nullptr, A.g.Vh, A.nrhs, r, hh, b, xs);
-        SpinorIO<PR>::store_block(A.cg_r, nullptr, A.g.Vh, A.nrhs, r, hh, b, rs);
-      }
-    } else {
-      if (A.do_norm) {
-#pragma unroll
-        for (int k = 0; k < 6; k++) nrm += double(res[k].re) * res[k].re + double(res[k].im) * res[k].im;
-      }
-#pragma unroll
-      for (int k = 0; k < 6; k++) part[0][6 * b + k][lane] = res[k];
-    }
-  }
-  __syncthreads();
-  if (valid && EPI != EPI_XPAY_CG) {
-    if (P == 64) {
-      double2* q = static_cast<double2*>(A.out);
-#pragma unroll
-      for (int k = 0; k < 3; k++) {
-        const cx<R> v = part[0][3 * w + k][lane];
-        q[sidx(3 * w + k, A.g.Vh, A.nrhs, r, hh)] = make_double2(double(v.re), double(v.im));
-      }
-    } else if (P == 32) {
-      if (w < 3) {
-        float4* q = static_cast<float4*>(A.out);
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-          const cx<R> v0 = part[0][4 * w + 2 * k][lane], v1 = part[0][4 * w + 2 * k + 1][lane];
-          q[sidx(2 * w + k, A.g.Vh, A.nrhs, r, hh)] = make_float4(float(v0.re), float(v0.im), float(v1.re), float(v1.im));
+          res[k].re = fma(a, v[k].re, cxs[k].re);
+          res[k].im = fma(a, v[k].im, cxs[k].im);
         }
       }
-    } else if (w == 0) {
-      cx<float> o[12];
+      if (A.out_g5 && b == 1) {
 #pragma unroll
-      for (int c = 0; c < 12; c++) o[c] = cmk(float(part[0][c][lane].re), float(part[0][c][lane].im));
-      SpinorIO<16>::store(A.out, A.out_norm, A.g.Vh, A.nrhs, r, hh, o);
+        for (int k = 0; k < 6; k++) res[k] = -res[k];
+      }
+      if (EPI == EPI_XPAY_CG) {
+        // res = (A p)_b: advance x and r of this RHS with alpha from the <p, A p> reduction
+        constexpr int PR = P == 64 ? 64 : 32;
+        using RR = typename Real<PR>::T;
+        const CGState& st = A.red.cg[r];
+        if (st.active) {
+          const RR al = RR(st.alpha);
+          cx<R> ps[6];
+          cx<RR> xs[6], rs[6];
+          SpinorIO<P>::load_block(A.cg_p, A.cg_p_norm, A.g.Vh, r, hh, b, ps);
+          SpinorIO<PR>::load_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
+          SpinorIO<PR>::load_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
+#pragma unroll
+          for (int k = 0; k < 6; k++) {
+            xs[k].re = fma(al, RR(ps[k].re), xs[k].re);
+            xs[k].im = fma(al, RR(ps[k].im), xs[k].im);
+            rs[k].re = fma(-al, RR(res[k].re), rs[k].re);
+            rs[k].im = fma(-al, RR(res[k].im), rs[k].im);
+            nrm += double(rs[k].re) * rs[k].re + double(rs[k].im) * rs[k].im;
+          }
+          SpinorIO<PR>::store_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
+          SpinorIO<PR>::store_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
+        }
+      } else {
+        if (A.do_norm) {
+#pragma unroll
+          for (int k = 0; k < 6; k++) nrm += double(res[k].re) * res[k].re + double(res[k].im) * res[k].im;
+        }
+#pragma unroll
+        for (int k = 0; k < 6; k++) part[0][6 * b + k][lane] = res[k];
+      }
     }
+    __syncthreads();
+    if (valid && EPI != EPI_XPAY_CG) {
+      if (P == 64) {
+        double2* q = static_cast<double2*>(A.out);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+          const cx<R> v = part[0][3 * w + k][lane];
+          q[sidx<12>(3 * w + k, A.g.Vh, r, hh)] = make_double2(double(v.re), double(v.im));
+        }
+      } else if (P == 32) {
+        if (w < 3) {
+          float4* q = static_cast<float4*>(A.out);
+#pragma unroll
+          for (int k = 0; k < 2; k++) {
+            const cx<R> v0 = part[0][4 * w + 2 * k][lane], v1 = part[0][4 * w + 2 * k + 1][lane];
+            q[sidx<6>(2 * w + k, A.g.Vh, r, hh)] =
+                make_float4(float(v0.re), float(v0.im), float(v1.re), float(v1.im));
+          }
+        }
+      } else if (w == 0) {
+        cx<float> o[12];
+#pragma unroll
+        for (int c = 0; c < 12; c++) o[c] = cmk(float(part[0][c][lane].re), float(part[0][c][lane].im));
+        SpinorIO<16>::store(A.out, A.out_norm, A.g.Vh, r, hh, o);
+      }
+    }
+    if (reduce) block_partial<128>(nrm, r, blockIdx.x, gridDim.x, A.red);  // contains __syncthreads
+    else __syncthreads();
   }
-  if (A.do_norm || EPI == EPI_XPAY_CG) grid_reduce<128>(nrm, A.nrhs, A.red);
+  if (reduce) grid_finish<128>(A.nrhs, gridDim.x, gridDim.x, A.red);
 }
 
 }  // namespace qcd

@@ -46,8 +46,8 @@ __device__ __forceinline__ C coef_mul(int code, C v) {
   }
 }
 
-__device__ __forceinline__ void load_spinor64(const double2* f, int Vh, int nrhs, int r, int h, C s[12]) {
-  SpinorIO<64>::load(f, nullptr, Vh, nrhs, r, h, s);
+__device__ __forceinline__ void load_spinor64(const double2* f, int Vh, int r, int h, C s[12]) {
+  SpinorIO<64>::load(f, nullptr, Vh, r, h, s);
 }
 
 __device__ __forceinline__ void store_m3(double2* buf, int plane, size_t V, int i, const M3& m) {
@@ -103,8 +103,8 @@ __global__ void __launch_bounds__(FB) clover_coeff_kernel(Geom g, double kappa, 
     for (int k = 0; k < 9; k++) S[pl].e[k] = cmk(0.0, 0.0);
   for (int r = 0; r < nrhs; r++) {
     C X[12], W[12];
-    load_spinor64(p == 0 ? Xe : Xo, g.Vh, nrhs, r, h, X);
-    load_spinor64(p == 0 ? Ye : Yo, g.Vh, nrhs, r, h, W);
+    load_spinor64(p == 0 ? Xe : Xo, g.Vh, r, h, X);
+    load_spinor64(p == 0 ? Ye : Yo, g.Vh, r, h, W);
     if (p == 1) {
 #pragma unroll
       for (int k = 0; k < 12; k++) W[k] = k2 * W[k];
@@ -215,10 +215,10 @@ __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, in
   const double scale = 2.0 * kappa * kappa * sgn;
   for (int r = 0; r < nrhs; r++) {
     C Xy[12], Yy[12], Xn[12], Yn[12];
-    load_spinor64(p == 0 ? Xe : Xo, g.Vh, nrhs, r, i >> 1, Xy);
-    load_spinor64(p == 0 ? Ye : Yo, g.Vh, nrhs, r, i >> 1, Yy);
-    load_spinor64(p == 0 ? Xo : Xe, g.Vh, nrhs, r, j >> 1, Xn);
-    load_spinor64(p == 0 ? Yo : Ye, g.Vh, nrhs, r, j >> 1, Yn);
+    load_spinor64(p == 0 ? Xe : Xo, g.Vh, r, i >> 1, Xy);
+    load_spinor64(p == 0 ? Ye : Yo, g.Vh, r, i >> 1, Yy);
+    load_spinor64(p == 0 ? Xo : Xe, g.Vh, r, j >> 1, Xn);
+    load_spinor64(p == 0 ? Yo : Ye, g.Vh, r, j >> 1, Yn);
     switch (lam) {
       case 0: hop_terms<0>(Xy, Yy, Xn, Yn, scale, Ah, Bh); break;
       case 1: hop_terms<1>(Xy, Yy, Xn, Yn, scale, Ah, Bh); break;

@@ -4,9 +4,9 @@
 //
 // Layout (all fields checkerboarded: parity p = (x+y+z+t) mod 2, half index
 // h = i >> 1 of the lexicographic index i = x + X (y + Y (z + Z t)); X even):
-//   spinor FP64 : [12][Vh][rhs] double2     component c = 3*spin + colour
-//   spinor FP32 : [6][Vh][rhs]  float4      two complex components per float4
-//   spinor FP16 : [3][Vh][rhs]  uint4 (8 halves = 4 complex) + [Vh][rhs] float norm
+//   spinor FP64 : [rhs][12][Vh] double2     component c = 3*spin + colour
+//   spinor FP32 : [rhs][6][Vh]  float4      two complex components per float4
+//   spinor FP16 : [rhs][3][Vh]  uint4 (8 halves = 4 complex) + [rhs][Vh] float norm
 //   gauge  FP64 : [p][mu][9][Vh] double2    element (i,j) at 3i+j
 //   gauge  FP32 : recon 18 [p][mu][9][Vh] float2, recon 12 [p][mu][3][Vh] float4
 //   gauge  FP16 : recon 18 [p][mu][9][Vh] half2,  recon 12 [p][mu][3][Vh] uint2
@@ -124,10 +124,11 @@ template <>
 struct Real<16> { using T = float; };
 
 // spinor accessors: 12 complex components, component c = 3*spin + colour.  A field of nrhs
-// right-hand sides is stored RHS-minor: vector k of (site h, RHS r) at (k * Vh + h) * nrhs + r, so
-// the lanes of a warp that cover consecutive (site, RHS) pairs read one contiguous run.
-__device__ __forceinline__ size_t sidx(int k, int Vh, int nrhs, int r, int h) {
-  return ((size_t)k * Vh + h) * nrhs + r;
+// right-hand sides is stored RHS-major: vector k of (RHS r, site h) at (r * NVEC + k) * Vh + h, so
+// the lanes of a warp (consecutive sites of one RHS) read one contiguous run.
+template <int NV>
+__device__ __forceinline__ size_t sidx(int k, int Vh, int r, int h) {
+  return ((size_t)r * NV + k) * Vh + h;
 }
 
 template <int P>
@@ -136,71 +137,71 @@ struct SpinorIO;
 template <>
 struct SpinorIO<64> {
   static constexpr int NVEC = 12;  // double2 per site
-  __device__ static void load(const void* base, const float*, int Vh, int nrhs, int r, int h, cx<double> s[12]) {
+  __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<double> s[12]) {
     const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 12; c++) {
-      double2 v = __ldg(p + sidx(c, Vh, nrhs, r, h));
+      double2 v = __ldg(p + sidx<NVEC>(c, Vh, r, h));
       s[c] = cmk(v.x, v.y);
     }
   }
-  __device__ static void store(void* base, float*, int Vh, int nrhs, int r, int h, const cx<double> s[12]) {
+  __device__ static void store(void* base, float*, int Vh, int r, int h, const cx<double> s[12]) {
     double2* p = static_cast<double2*>(base);
 #pragma unroll
-    for (int c = 0; c < 12; c++) p[sidx(c, Vh, nrhs, r, h)] = make_double2(s[c].re, s[c].im);
+    for (int c = 0; c < 12; c++) p[sidx<NVEC>(c, Vh, r, h)] = make_double2(s[c].re, s[c].im);
   }
   // components 6b..6b+5 (chiral block b: spins 2b, 2b+1)
-  __device__ static void load_block(const void* base, const float*, int Vh, int nrhs, int r, int h, int b,
+  __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b,
                                     cx<double> s[6]) {
     const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 6; c++) {
-      double2 v = __ldg(p + sidx(6 * b + c, Vh, nrhs, r, h));
+      double2 v = __ldg(p + sidx<NVEC>(6 * b + c, Vh, r, h));
       s[c] = cmk(v.x, v.y);
     }
   }
-  __device__ static void store_block(void* base, float*, int Vh, int nrhs, int r, int h, int b,
+  __device__ static void store_block(void* base, float*, int Vh, int r, int h, int b,
                                      const cx<double> s[6]) {
     double2* p = static_cast<double2*>(base);
 #pragma unroll
-    for (int c = 0; c < 6; c++) p[sidx(6 * b + c, Vh, nrhs, r, h)] = make_double2(s[c].re, s[c].im);
+    for (int c = 0; c < 6; c++) p[sidx<NVEC>(6 * b + c, Vh, r, h)] = make_double2(s[c].re, s[c].im);
   }
 };
 
 template <>
 struct SpinorIO<32> {
   static constexpr int NVEC = 6;  // float4 per site
-  __device__ static void load(const void* base, const float*, int Vh, int nrhs, int r, int h, cx<float> s[12]) {
+  __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<float> s[12]) {
     const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 6; k++) {
-      float4 v = __ldg(p + sidx(k, Vh, nrhs, r, h));
+      float4 v = __ldg(p + sidx<NVEC>(k, Vh, r, h));
       s[2 * k] = cmk(v.x, v.y);
       s[2 * k + 1] = cmk(v.z, v.w);
     }
   }
-  __device__ static void store(void* base, float*, int Vh, int nrhs, int r, int h, const cx<float> s[12]) {
+  __device__ static void store(void* base, float*, int Vh, int r, int h, const cx<float> s[12]) {
     float4* p = static_cast<float4*>(base);
 #pragma unroll
     for (int k = 0; k < 6; k++)
-      p[sidx(k, Vh, nrhs, r, h)] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
+      p[sidx<NVEC>(k, Vh, r, h)] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
   }
-  __device__ static void load_block(const void* base, const float*, int Vh, int nrhs, int r, int h, int b,
+  __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b,
                                     cx<float> s[6]) {
     const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      float4 v = __ldg(p + sidx(3 * b + k, Vh, nrhs, r, h));
+      float4 v = __ldg(p + sidx<NVEC>(3 * b + k, Vh, r, h));
       s[2 * k] = cmk(v.x, v.y);
       s[2 * k + 1] = cmk(v.z, v.w);
     }
   }
-  __device__ static void store_block(void* base, float*, int Vh, int nrhs, int r, int h, int b,
+  __device__ static void store_block(void* base, float*, int Vh, int r, int h, int b,
                                      const cx<float> s[6]) {
     float4* p = static_cast<float4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++)
-      p[sidx(3 * b + k, Vh, nrhs, r, h)] =
+      p[sidx<NVEC>(3 * b + k, Vh, r, h)] =
           make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
   }
 };
@@ -215,16 +216,16 @@ __device__ __forceinline__ uint32_t f2h(float a, float b) {
 }
 
 // FP16 spinor: each real is stored as half(v / n) with n = max |v| over the site's 24 reals;
-// the norms of a field are stored [Vh][nrhs]
+// the norms of a field are stored [nrhs][Vh]
 template <>
 struct SpinorIO<16> {
   static constexpr int NVEC = 3;  // uint4 per site
-  __device__ static void load(const void* base, const float* nrm, int Vh, int nrhs, int r, int h, cx<float> s[12]) {
+  __device__ static void load(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
     const uint4* p = static_cast<const uint4*>(base);
-    const float n = __ldg(nrm + (size_t)h * nrhs + r);
+    const float n = __ldg(nrm + (size_t)r * Vh + h);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint4 v = __ldg(p + sidx(k, Vh, nrhs, r, h));
+      uint4 v = __ldg(p + sidx<NVEC>(k, Vh, r, h));
       float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
       s[4 * k + 0] = cmk(a.x * n, a.y * n);
       s[4 * k + 1] = cmk(b.x * n, b.y * n);
@@ -232,7 +233,21 @@ struct SpinorIO<16> {
       s[4 * k + 3] = cmk(d.x * n, d.y * n);
     }
   }
-  __device__ static void store(void* base, float* nrm, int Vh, int nrhs, int r, int h, const cx<float> s[12]) {
+  // the stored values v / n without the per-site scale n, which is returned
+  __device__ static float load_unscaled(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
+    const uint4* p = static_cast<const uint4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      uint4 v = __ldg(p + sidx<NVEC>(k, Vh, r, h));
+      float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+      s[4 * k + 0] = cmk(a.x, a.y);
+      s[4 * k + 1] = cmk(b.x, b.y);
+      s[4 * k + 2] = cmk(c.x, c.y);
+      s[4 * k + 3] = cmk(d.x, d.y);
+    }
+    return __ldg(nrm + (size_t)r * Vh + h);
+  }
+  __device__ static void store(void* base, float* nrm, int Vh, int r, int h, const cx<float> s[12]) {
     float m = 0.f;
 #pragma unroll
     for (int c = 0; c < 12; c++) m = fmaxf(m, fmaxf(fabsf(s[c].re), fabsf(s[c].im)));
@@ -245,17 +260,17 @@ struct SpinorIO<16> {
       v.y = f2h(s[4 * k + 1].re * inv, s[4 * k + 1].im * inv);
       v.z = f2h(s[4 * k + 2].re * inv, s[4 * k + 2].im * inv);
       v.w = f2h(s[4 * k + 3].re * inv, s[4 * k + 3].im * inv);
-      p[sidx(k, Vh, nrhs, r, h)] = v;
+      p[sidx<NVEC>(k, Vh, r, h)] = v;
     }
-    nrm[(size_t)h * nrhs + r] = m;
+    nrm[(size_t)r * Vh + h] = m;
   }
   // block 0 = chunk 0 and the first half of chunk 1; block 1 = the second half of chunk 1 and chunk 2
-  __device__ static void load_block(const void* base, const float* nrm, int Vh, int nrhs, int r, int h, int b,
+  __device__ static void load_block(const void* base, const float* nrm, int Vh, int r, int h, int b,
                                     cx<float> s[6]) {
     const uint4* p = static_cast<const uint4*>(base);
-    const float n = __ldg(nrm + (size_t)h * nrhs + r);
-    const uint4 mid = __ldg(p + sidx(1, Vh, nrhs, r, h));
-    const uint4 end = __ldg(p + sidx(b == 0 ? 0 : 2, Vh, nrhs, r, h));
+    const float n = __ldg(nrm + (size_t)r * Vh + h);
+    const uint4 mid = __ldg(p + sidx<NVEC>(1, Vh, r, h));
+    const uint4 end = __ldg(p + sidx<NVEC>(b == 0 ? 0 : 2, Vh, r, h));
     float2 e0 = h2f(end.x), e1 = h2f(end.y), e2 = h2f(end.z), e3 = h2f(end.w);
     if (b == 0) {
       float2 m0 = h2f(mid.x), m1 = h2f(mid.y);
@@ -430,13 +445,14 @@ struct CloverIO<32> {
 template <>
 struct CloverIO<16> {
   static constexpr int NVEC = 9;  // uint4 per site
-  __device__ static void apply(const void* c, int Vh, int h, int b, const cx<float> x[6], cx<float> y[6]) {
+  // block B occupies halves [36B, 36B+36): uint4 4B .. 4B+4 (the middle uint4 is shared)
+  template <int B>
+  __device__ static void apply_block(const void* c, int Vh, int h, const cx<float> x[6], cx<float> y[6]) {
     const uint4* q = static_cast<const uint4*>(c) + h;
-    // block b occupies halves [36b, 36b+36): uint4 4b .. 4b+4 (the middle uint4 is shared)
     float f[40];
 #pragma unroll
     for (int k = 0; k < 5; k++) {
-      uint4 v = __ldg(q + (size_t)(4 * b + k) * Vh);
+      uint4 v = __ldg(q + (size_t)(4 * B + k) * Vh);
       float2 a0 = h2f(v.x), a1 = h2f(v.y), a2 = h2f(v.z), a3 = h2f(v.w);
       f[8 * k + 0] = a0.x;
       f[8 * k + 1] = a0.y;
@@ -447,7 +463,7 @@ struct CloverIO<16> {
       f[8 * k + 6] = a3.x;
       f[8 * k + 7] = a3.y;
     }
-    const int o = 4 * b;  // block 1 starts 4 halves into uint4 4
+    constexpr int o = 4 * B;  // block 1 starts 4 halves into uint4 4
     float d[6];
     cx<float> L[15];
 #pragma unroll
@@ -455,6 +471,10 @@ struct CloverIO<16> {
 #pragma unroll
     for (int k = 0; k < 15; k++) L[k] = cmk(f[o + 6 + 2 * k], f[o + 7 + 2 * k]);
     hermitian6_accumulate(d, L, x, y);
+  }
+  __device__ static void apply(const void* c, int Vh, int h, int b, const cx<float> x[6], cx<float> y[6]) {
+    if (b == 0) apply_block<0>(c, Vh, h, x, y);
+    else apply_block<1>(c, Vh, h, x, y);
   }
 };
 
@@ -580,48 +600,56 @@ __device__ __forceinline__ void finalize_total(const ReduceArgs& ra, int r, doub
   }
 }
 
-// Grid-wide deterministic sum of one double per thread, per right-hand side
-// (rhs = global thread index mod nrhs; nrhs divides 32, blockDim a multiple of
-// 32).  Warp shuffles, then shared memory, then per-block partials; the last
-// block to finish sums the partials in a fixed order and runs finalize_total.
+// Grid-wide deterministic sums, one per right-hand side, in two parts.  block_partial: the block's
+// sum of one double per thread for RHS r (warp shuffles, then shared memory) into slot
+// r * nblk + blk of the partials.  grid_finish: after all of a block's partials are written, the
+// last block of the grid to finish (blk_total blocks) sums every RHS's nblk partials in a fixed
+// order and runs finalize_total.  Both are called by all threads of the block.
 template <int BLOCK>
-__device__ __forceinline__ void grid_reduce(double v, int nrhs, const ReduceArgs& ra) {
-  __shared__ double sm[BLOCK / 32][8];
-  __shared__ bool is_last;
+__device__ __forceinline__ void block_partial(double v, int r, int blk, int nblk, const ReduceArgs& ra) {
+  __shared__ double sm[BLOCK / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int off = 16; off >= nrhs; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  if (lane < nrhs) sm[warp][lane] = v;
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if (lane == 0) sm[warp] = v;
   __syncthreads();
-  if (threadIdx.x < nrhs) {
+  if (threadIdx.x == 0) {
     double s = 0.0;
 #pragma unroll 1
-    for (int w = 0; w < BLOCK / 32; w++) s += sm[w][threadIdx.x];
-    const long long slot = (long long)threadIdx.x * gridDim.x + blockIdx.x;
+    for (int w = 0; w < BLOCK / 32; w++) s += sm[w];
+    const long long slot = (long long)r * nblk + blk;
     if (slot < ra.capacity) ra.partials[slot] = s;
     else ra.ctl->overflow = 1;
   }
+  __syncthreads();
+}
+
+template <int BLOCK>
+__device__ __forceinline__ void grid_finish(int nrhs, long long blk_total, int nblk, const ReduceArgs& ra) {
+  __shared__ double sm[BLOCK / 32];
+  __shared__ bool is_last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned int ticket = atomicAdd(ra.counter, 1u);
-    is_last = (ticket == gridDim.x - 1);
+    const unsigned int ticket = atomicAdd(ra.counter, 1u);
+    is_last = (ticket == blk_total - 1);
   }
   __syncthreads();
   if (!is_last) return;
   __threadfence();
   for (int r = 0; r < nrhs; r++) {
     double s = 0.0;
-    for (int j = threadIdx.x; j < (int)gridDim.x; j += BLOCK) {
-      const long long slot = (long long)r * gridDim.x + j;
+    for (int j = threadIdx.x; j < nblk; j += BLOCK) {
+      const long long slot = (long long)r * nblk + j;
       if (slot < ra.capacity) s += __ldcg(ra.partials + slot);
     }
     for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     __syncthreads();
-    if (lane == 0) sm[warp][0] = s;
+    if (lane == 0) sm[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
       double tot = 0.0;
-      for (int w = 0; w < BLOCK / 32; w++) tot += sm[w][0];
+      for (int w = 0; w < BLOCK / 32; w++) tot += sm[w];
       finalize_total(ra, r, tot);
     }
   }

@@ -21,8 +21,11 @@ void launch_check_finite(const double* data, size_t n, int* flag, cudaStream_t s
 
 // ---- clover (qcd_clover.cu)
 // A (both parities) and A^-1 (both parities) in FP64, FP32 and FP16; flag set if a block is not positive definite.
+// work: 6 * 9 * V double2 for the field strengths (two kernels: F per site and plane, then one chiral
+// block per thread); null: a single kernel with one site per thread.
 void launch_clover_build(const Geom& g, const void* g64, double kappa, double csw, void* A64, void* Ainv64,
-                         void* A32, void* Ainv32, void* A16, void* Ainv16, int* notposdef, cudaStream_t st);
+                         void* A32, void* Ainv32, void* A16, void* Ainv16, void* work, int* notposdef,
+                         cudaStream_t st);
 // out = C in for a site-local clover field C of parity-matched fields
 void launch_clover_apply(int prec, const Geom& g, const void* clover, const void* in, const float* in_norm,
                          void* out, float* out_norm, int nrhs, cudaStream_t st);
@@ -30,15 +33,8 @@ void launch_clover_apply(int prec, const Geom& g, const void* clover, const void
 // ---- hopping term (qcd_dslash.cu)
 struct DslashArgs;
 void launch_dslash(int prec, int recon, int epi, const DslashArgs& a, cudaStream_t st);
-int dslash_block();
 
-// ---- BLAS-1 and CG steps (qcd_blas.cu)
-int blas_block();
-int blas_grid(const Geom& g, int nrhs);
-// x += alpha p ; r -= alpha Ap ; |r|^2 -> FIN_CG_RR
-void launch_cg_update(int prec_r, int prec_p, const Geom& g, int nrhs, void* x, float* xn, void* r, float* rn,
-                      const void* p, const float* pn, const void* Ap, const float* Apn, const ReduceArgs& red,
-                      const int* halt, cudaStream_t st);
+// ---- BLAS-1 and CG steps (qcd_blas.cu); 2-D grids (sites x RHS)
 // p = r + beta p
 void launch_p_update(int prec_r, int prec_p, const Geom& g, int nrhs, const void* r, const float* rn, void* p,
                      float* pn, const CGState* cg, const int* halt, cudaStream_t st);

@@ -84,7 +84,7 @@ __global__ void spinor_to_native_kernel(Geom g, const double2* __restrict__ cano
     double2 v = src[c];
     s[c] = cmk(R(v.x), R(v.y));
   }
-  SpinorIO<P>::store(nat, norm, g.Vh, nrhs, r, h, s);
+  SpinorIO<P>::store(nat, norm, g.Vh, r, h, s);
 }
 
 template <int P>
@@ -94,7 +94,7 @@ __global__ void spinor_to_canon_kernel(Geom g, const void* nat, const float* nor
   if (tid >= g.Vh * nrhs) return;
   const int r = tid / g.Vh, h = tid - r * g.Vh;
   cx<R> s[12];
-  SpinorIO<P>::load(nat, norm, g.Vh, nrhs, r, h, s);
+  SpinorIO<P>::load(nat, norm, g.Vh, r, h, s);
   double2* dst = canon + (size_t)tid * 12;
 #pragma unroll
   for (int c = 0; c < 12; c++) dst[c] = make_double2(double(s[c].re), double(s[c].im));
