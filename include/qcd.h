@@ -55,7 +55,7 @@ typedef enum {
   QCD_ERR_NOT_POSDEF = 5,    /* a clover block is not positive definite */
   QCD_ERR_NOT_CONVERGED = 6, /* CG hit max_iter; best x and stats are still written */
   QCD_ERR_NAN = 7,           /* non-finite input or a non-finite reduction */
-  QCD_ERR_TIMEOUT = 8        /* reserved: a bounded device-side wait gave up */
+  QCD_ERR_TIMEOUT = 8        /* a bounded device-side wait (grid barrier of the persistent CG kernel) gave up */
 } qcd_status;
 
 /* qcd_load_gauge flags */
@@ -203,6 +203,15 @@ qcd_status qcd_profile_read(qcd_ctx* ctx, qcd_kernel_stat* out, int max_entries,
  */
 #define QCD_STATIC_SCRATCH_BYTES (24u << 20)
 qcd_status qcd_mhat_static(qcd_ctx* ctx, double* out, const double* in, int dagger);
+
+/*
+ * Failure-path self-test of the bounded grid barrier used by the persistent single-RHS CG kernel:
+ * launches a two-block cooperative kernel in which one block never reaches the barrier, so the
+ * other block's wait runs out (after about a second) and sets the context's error word.  Returns
+ * QCD_ERR_TIMEOUT when the wait gave up as intended (QCD_OK would mean it did not); the context
+ * stays usable.  Synchronises the context's stream.
+ */
+qcd_status qcd_selftest_barrier_timeout(qcd_ctx* ctx);
 
 /* Message describing the last failed call on this thread ("" if none). */
 const char* qcd_last_error(void);

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -150,6 +151,16 @@ struct qcd_ctx {
   std::vector<ItGraph*> graphs;
   std::vector<std::pair<ItGraph*, int>> launched;  // graphs launched since the last collection, with iteration offset
   double last_rho = 0.0;                            // per-iteration |r|^2 ratio seen by the last solve
+  // persistent single-RHS iteration: per-block partial sums and the grid barrier words
+  double* pc_part = nullptr;   // 2 x pc_slots
+  int pc_slots = 0;
+  unsigned* pc_bar = nullptr;  // [0] count, [1] generation, [2] error
+  bool persistent = true;
+  struct {
+    cudaEvent_t a, b;
+    double bytes_per_iter, flops_per_iter;
+  } pc_pending{};
+  bool pc_has_pending = false;
 };
 
 namespace {
@@ -468,6 +479,22 @@ qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* strea
   cudaMemset(c->counter, 0, sizeof(unsigned));
   cudaMemset(c->flags, 0, 4 * sizeof(int));
   cudaMemset(c->ctl, 0, sizeof(CGControl));
+  {
+    int sms = 0, coop = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    c->pc_slots = sms * 16;  // 16 resident 128-thread blocks per SM at most
+    c->persistent = coop != 0;
+    const char* e = getenv("QCD_CG_PERSISTENT");
+    if (e && e[0] == '0') c->persistent = false;
+    if (cudaMalloc(&c->pc_part, sizeof(double) * 2 * c->pc_slots) != cudaSuccess ||
+        cudaMalloc(&c->pc_bar, 4 * sizeof(unsigned)) != cudaSuccess) {
+      cudaGetLastError();
+      qcd_destroy(c);
+      return fail(QCD_ERR_NOMEM, "context allocation failed");
+    }
+    cudaMemset(c->pc_bar, 0, 4 * sizeof(unsigned));
+  }
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     qcd_destroy(c);
@@ -488,6 +515,7 @@ qcd_status qcd_destroy(qcd_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   void* dev[] = {c->g64, c->g32, c->g16, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, c->flags,
+                 c->pc_part, c->pc_bar,
                  c->partials, c->counter, c->results, c->cg, c->ctl};
   for (void* p : dev)
     if (p) cudaFree(p);
@@ -866,7 +894,62 @@ qcd_status launch_iterations(qcd_ctx* c, const SolverFields& f, int nrhs, int n)
 qcd_status read_state(qcd_ctx* c, int nrhs) {
   cudaMemcpyAsync(c->h_cg, c->cg, sizeof(CGState) * nrhs, cudaMemcpyDeviceToHost, c->st);
   cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(CGControl), cudaMemcpyDeviceToHost, c->st);
+  cudaMemcpyAsync(c->h_flags + 2, c->pc_bar + 2, sizeof(int), cudaMemcpyDeviceToHost, c->st);
   return sync_and_check(c, "cg state");
+}
+
+// lattices up to this half volume run single-RHS iterations in the persistent kernel
+const int PERSISTENT_MAX_VH = 1 << 18;
+
+// One segment of CG iterations of a single RHS in the persistent kernel: it stops itself at the
+// next reliable-update or convergence trigger, or after max_iters iterations.
+qcd_status launch_persistent(qcd_ctx* c, const SolverFields& f, int max_iters) {
+  const Geom& g = c->g;
+  PersistentCGArgs q;
+  memset(&q, 0, sizeof q);
+  q.g = g;
+  q.gauge = gauge_ptr(c, f.pp);
+  q.clover_inv_odd = clover_ptr(c, f.pp, true, 1);
+  q.clover_even = clover_ptr(c, f.pp, false, 0);
+  q.p = f.p;
+  q.t = f.t;
+  q.y = f.y;
+  q.p_n = f.p_n;
+  q.t_n = f.t_n;
+  q.y_n = f.y_n;
+  q.x = f.x_lo;
+  q.r = f.r_lo;
+  q.k2 = c->kappa * c->kappa;
+  q.cg = c->cg;
+  q.ctl = c->ctl;
+  q.part_pap = c->pc_part;
+  q.part_rr = c->pc_part + c->pc_slots;
+  q.slots = c->pc_slots;
+  q.bar_count = c->pc_bar;
+  q.bar_gen = c->pc_bar + 1;
+  q.bar_err = reinterpret_cast<int*>(c->pc_bar + 2);
+  q.max_iters = max_iters < 1 ? 1 : max_iters;
+  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, sizeof(unsigned), c->st));
+  CUDA_TRY(cudaMemsetAsync(c->pc_bar + 2, 0, sizeof(unsigned), c->st));
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (c->prof_on) {
+    ea = prof_event(c);
+    cudaEventRecord(ea, c->st);
+  }
+  CUDA_TRY(launch_cg_persistent(f.pp, f.pp == 64 ? 18 : c->recon, q, c->st));
+  if (c->prof_on) {
+    eb = prof_event(c);
+    cudaEventRecord(eb, c->st);
+    // bytes and flops are attributed per iteration when the segment's length is known
+    double b1, f1, b2, f2, bx, fx;
+    dslash_cost(c, f.pp, EPI_CLOVER_INV, 1, &b1, &f1);
+    dslash_cost(c, f.pp, EPI_XPAY, 1, &b2, &f2);
+    dslash_cost(c, f.pp, EPI_XPAY_CG, 1, &bx, &fx);
+    const double sp = 24.0 * real_bytes(f.pp) + (f.pp == 16 ? 4 : 0), sr = 24.0 * real_bytes(f.pr);
+    c->pc_pending = {ea, eb, 2 * b1 + b2 + bx + (double)g.Vh * (sr + 2 * sp), 2 * f1 + f2 + fx};
+    c->pc_has_pending = true;
+  }
+  return QCD_OK;
 }
 
 // Iterations to enqueue before the next look at the solver state: the fewest, over the active
@@ -943,6 +1026,8 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
   launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->st);
 
   std::vector<double> rho(nrhs, c->last_rho);
+  // one RHS on a lattice whose iteration is launch-bound: the persistent kernel runs each segment
+  const bool use_pc = c->persistent && nrhs == 1 && g.Vh <= PERSISTENT_MAX_VH;
   qcd_status result = QCD_OK;
   bool after_reliable = true;
   int done_iters = 0;
@@ -950,9 +1035,14 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
   while (true) {
     // the state is only known after a synchronisation; right after the set-up or a reliable
     // update the host copy is stale, which predict_iterations accounts for
-    const int n = std::min(predict_iterations(c, nrhs, rho, after_reliable), std::max(1, prm->max_iter - done_iters));
-    if ((s = launch_iterations(c, f, nrhs, n))) return s;
+    if (use_pc) {
+      if ((s = launch_persistent(c, f, prm->max_iter - done_iters))) return s;
+    } else {
+      const int n = std::min(predict_iterations(c, nrhs, rho, after_reliable), std::max(1, prm->max_iter - done_iters));
+      if ((s = launch_iterations(c, f, nrhs, n))) return s;
+    }
     if ((s = read_state(c, nrhs))) return s;
+    if (use_pc && c->h_flags[2]) return fail(QCD_ERR_TIMEOUT, "a grid barrier of the persistent CG kernel timed out");
     int max_it = 0;
     bool active = false, candidate = false;
     for (int r = 0; r < nrhs; r++) {
@@ -964,6 +1054,23 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
         rho[r] = pow(st.rr / st.rr_reliable, 1.0 / st.since_reliable);
     }
     if (c->prof_on) collect_graphs(c, max_it - done_iters);
+    if (c->pc_has_pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->pc_pending.a, c->pc_pending.b) == cudaSuccess) {
+        ProfClass& pc = c->prof[prof_class(c, f.pp == 64 ? "cg_persistent_p64" : (f.pp == 32 ? "cg_persistent_p32"
+                                                                                               : "cg_persistent_p16"))];
+        const int n_it = max_it - done_iters;
+        pc.launches += 1;
+        pc.ms += ms;
+        pc.bytes += n_it * c->pc_pending.bytes_per_iter;
+        pc.flops += n_it * c->pc_pending.flops_per_iter;
+      } else {
+        cudaGetLastError();
+      }
+      c->ev_free.push_back(c->pc_pending.a);
+      c->ev_free.push_back(c->pc_pending.b);
+      c->pc_has_pending = false;
+    }
     done_iters = max_it;
     if (c->h_ctl->overflow) return fail(QCD_ERR_CUDA, "reduction buffer too small (internal sizing error)");
     if (c->h_ctl->nan) {
@@ -1126,6 +1233,18 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
                        (flags & QCD_FORCE_GRADIENT) != 0, k == 0, k > 0, c->st);
   }
   return sync_and_check(c, "fermion_force");
+}
+
+qcd_status qcd_selftest_barrier_timeout(qcd_ctx* c) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 4 * sizeof(unsigned), c->st));
+  CUDA_TRY(launch_barrier_probe(c->pc_bar, c->pc_bar + 1, reinterpret_cast<int*>(c->pc_bar + 2), c->st));
+  CUDA_TRY(cudaMemcpyAsync(c->h_flags + 2, c->pc_bar + 2, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  if ((s = sync_and_check(c, "barrier self-test"))) return s;
+  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 4 * sizeof(unsigned), c->st));
+  if (c->h_flags[2]) return fail(QCD_ERR_TIMEOUT, "grid barrier wait gave up as intended");
+  return QCD_OK;
 }
 
 qcd_status qcd_profile(qcd_ctx* c, int enable) {

@@ -1,0 +1,280 @@
+// Persistent CG iteration for one right-hand side.
+//
+// On small lattices the inner CG iteration is bound by kernel launch latency and ramp-up, not by
+// memory bandwidth: its five launches (four hopping passes, the p update) each touch a working set
+// that fits in L2.  This cooperative kernel keeps every block resident and runs the iteration's
+// five phases back to back, separated by grid barriers, until a reliable-update or convergence
+// trigger (or an iteration cap) -- the same arithmetic, in the same order, as the graph of launches.
+//
+//   phase 1  t  = A_oo^-1 D_oe p
+//   phase 2  y  = A_ee p - kappa^2 D_eo t,     |y|^2 = <p, Mhat^dag Mhat p>  -> alpha
+//   phase 3  t  = A_oo^-1 D_oe g5 y
+//   phase 4  Ap = g5 (A_ee g5 y - kappa^2 D_eo t), x += alpha p, r -= alpha Ap, |r|^2 -> beta
+//   phase 5  p  = r + beta p
+//
+// Sums are formed per block over a fixed set of site blocks and then, after the barrier, added in
+// block order by every block, so all blocks hold the same alpha and beta.  Fields written inside
+// the kernel are read through L2 only.  Every barrier wait is bounded: a block that has waited too
+// long sets an error word and all blocks return (the host reports QCD_ERR_TIMEOUT).
+#include "qcd_dslash.cuh"
+#include "qcd_kernels.h"
+
+namespace qcd {
+
+namespace {
+
+constexpr unsigned BARRIER_SPIN_LIMIT = 1u << 22;  // polls of an L2 word: about a second or more
+
+// Grid-wide barrier of a cooperative launch.  Returns false (on every thread of the block) if this
+// block gave up waiting or another block reported an error.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = gen;
+    volatile int* verr = err;
+    const unsigned g0 = *vgen;
+    __threadfence();
+    ok = 1;
+    if (atomicAdd(count, 1u) + 1 == gridDim.x) {
+      atomicExch(count, 0u);
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      unsigned spins = 0;
+      while (*vgen == g0) {
+        if (*verr) {
+          ok = 0;
+          break;
+        }
+        if (++spins > BARRIER_SPIN_LIMIT) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// sum of one double per thread over the block (thread 0 gets it)
+__device__ __forceinline__ double block_sum128(double v) {
+  __shared__ double sm[4];
+  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) s = (sm[0] + sm[1]) + (sm[2] + sm[3]);
+  __syncthreads();
+  return s;
+}
+
+// sum of the gridDim.x per-block partials, on every thread: each thread adds a fixed strided
+// subset, then a fixed shuffle / shared-memory tree, so every block gets the same bits
+__device__ __forceinline__ double grid_total(const double* part) {
+  __shared__ double sm[4];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < (int)gridDim.x; j += 128) s += __ldcg(part + j);
+  for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  const double t = (sm[0] + sm[1]) + (sm[2] + sm[3]);
+  __syncthreads();
+  return t;
+}
+
+template <int P, int RECON, int EPI>
+__device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Real<P>::T> (*part)[12][32], double alpha) {
+  using R = typename Real<P>::T;
+  const int nsb = (A.g.Vh + 31) / 32;
+  double v = 0.0;
+  for (int sb = blockIdx.x; sb < nsb; sb += gridDim.x) {
+    int hh;
+    bool valid;
+    Site s;
+    DirLinks<R> L;
+    split_prologue<P, RECON, false>(A, sb, hh, valid, s, L);
+    v += split_unit<P, RECON, EPI, false, true>(A, hh, valid, s, L, 0, true, alpha, part);
+  }
+  return v;
+}
+
+template <int P, int RECON>
+__global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) {
+  using R = typename Real<P>::T;
+  constexpr int PR = P == 64 ? 64 : 32;
+  using RR = typename Real<PR>::T;
+  __shared__ cx<R> part[4][12][32];
+  const CGState st0 = *Q.cg;
+  if (!st0.active || Q.ctl->halt) return;
+  double rr = st0.rr, rr_prev = st0.rr_prev;
+  int iters = st0.iters, since = st0.since_reliable;
+  const int every = Q.ctl->reliable_every;
+  const double delta2 = Q.ctl->delta2;
+  const int Vh = Q.g.Vh;
+
+  DslashArgs a1;  // t = A_oo^-1 D_oe (g5) v
+  memset(&a1, 0, sizeof a1);
+  a1.g = Q.g;
+  a1.p = 1;
+  a1.nrhs = 1;
+  a1.gauge = Q.gauge;
+  a1.out = Q.t;
+  a1.out_norm = Q.t_n;
+  a1.clover = Q.clover_inv_odd;
+  DslashArgs a2 = a1;  // even output, clover A_ee
+  a2.p = 0;
+  a2.clover = Q.clover_even;
+  a2.a = -Q.k2;
+  a2.in = Q.t;
+  a2.in_norm = Q.t_n;
+
+  double alpha = 0.0, beta = 0.0, pAp = 0.0;
+  for (int it = 0; it < Q.max_iters; it++) {
+    // phase 1
+    a1.in = Q.p;
+    a1.in_norm = Q.p_n;
+    a1.in_g5 = 0;
+    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, 0.0);
+    if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+    // phase 2
+    {
+      DslashArgs a = a2;
+      a.x = Q.p;
+      a.x_norm = Q.p_n;
+      a.out = Q.y;
+      a.out_norm = Q.y_n;
+      a.do_norm = 1;
+      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY>(a, part, 0.0));
+      if (threadIdx.x == 0) Q.part_pap[blockIdx.x] = v;
+    }
+    if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+    pAp = grid_total(Q.part_pap);
+    if (!(pAp > 0.0) || !isfinite(pAp)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Q.ctl->nan = 1;
+        Q.ctl->halt = 1;
+      }
+      return;
+    }
+    alpha = rr / pAp;
+    // phase 3
+    a1.in = Q.y;
+    a1.in_norm = Q.y_n;
+    a1.in_g5 = 1;
+    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, 0.0);
+    if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+    // phase 4
+    {
+      DslashArgs a = a2;
+      a.x = Q.y;
+      a.x_norm = Q.y_n;
+      a.x_g5 = 1;
+      a.out_g5 = 1;
+      a.cg_x = Q.x;
+      a.cg_r = Q.r;
+      a.cg_p = Q.p;
+      a.cg_p_norm = Q.p_n;
+      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY_CG>(a, part, alpha));
+      if (threadIdx.x == 0) Q.part_rr[blockIdx.x] = v;
+    }
+    if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+    const double rr_new = grid_total(Q.part_rr);
+    if (!isfinite(rr_new)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        Q.ctl->nan = 1;
+        Q.ctl->halt = 1;
+      }
+      return;
+    }
+    beta = rr_new / rr;
+    rr_prev = rr;
+    rr = rr_new;
+    iters += 1;
+    since += 1;
+    const bool want = rr_new <= st0.tol2 || since >= every || rr_new < delta2 * st0.rr_reliable;
+    if (!want) {
+      // phase 5
+      for (int h = blockIdx.x * 128 + threadIdx.x; h < Vh; h += gridDim.x * 128) {
+        cx<RR> rs[12];
+        cx<R> ps[12], out[12];
+        SpinorIO<PR>::template load<true>(Q.r, nullptr, Vh, 0, h, rs);
+        SpinorIO<P>::template load<true>(Q.p, Q.p_n, Vh, 0, h, ps);
+        const RR b = RR(beta);
+#pragma unroll
+        for (int c = 0; c < 12; c++) {
+          out[c].re = R(fma(b, RR(ps[c].re), rs[c].re));
+          out[c].im = R(fma(b, RR(ps[c].im), rs[c].im));
+        }
+        SpinorIO<P>::store(Q.p, Q.p_n, Vh, 0, h, out);
+      }
+      if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+    }
+    if (want || it == Q.max_iters - 1) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        CGState& s = *Q.cg;
+        s.rr = rr;
+        s.rr_prev = rr_prev;
+        s.pAp = pAp;
+        s.alpha = alpha;
+        s.beta = beta;
+        s.iters = iters;
+        s.since_reliable = since;
+        if (want) {
+          s.pending = 1;
+          Q.ctl->halt = 1;
+        }
+      }
+      return;
+    }
+  }
+}
+
+// Two blocks meet at one grid barrier, except that block `absent` returns first: the other
+// block's wait must run out, set *err and return.
+__global__ void barrier_probe_kernel(unsigned* count, unsigned* gen, int* err, int absent) {
+  if ((int)blockIdx.x == absent) return;
+  grid_barrier(count, gen, err);
+}
+
+template <int P, int RECON>
+cudaError_t launch_pc(const PersistentCGArgs& q, cudaStream_t st) {
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_persistent_kernel<P, RECON>, 128, 0);
+    if (per_sm < 1) per_sm = 0;
+  }
+  if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+  const int nsb = (q.g.Vh + 31) / 32;
+  int grid = per_sm * sms;
+  if (grid > nsb) grid = nsb;
+  if (grid > q.slots) grid = q.slots;
+  PersistentCGArgs a = q;
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(cg_persistent_kernel<P, RECON>), dim3(grid), dim3(128),
+                                     args, 0, st);
+}
+
+}  // namespace
+
+cudaError_t launch_barrier_probe(unsigned* count, unsigned* gen, int* err, cudaStream_t st) {
+  g_kernel_launches += 1;
+  int absent = 1;
+  void* args[] = {&count, &gen, &err, &absent};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(barrier_probe_kernel), dim3(2), dim3(32), args, 0, st);
+}
+
+cudaError_t launch_cg_persistent(int prec, int recon, const PersistentCGArgs& q, cudaStream_t st) {
+  g_kernel_launches += 1;
+  if (prec == 64) return launch_pc<64, 18>(q, st);
+  if (prec == 32) return recon == 12 ? launch_pc<32, 12>(q, st) : launch_pc<32, 18>(q, st);
+  return recon == 12 ? launch_pc<16, 12>(q, st) : launch_pc<16, 18>(q, st);
+}
+
+}  // namespace qcd

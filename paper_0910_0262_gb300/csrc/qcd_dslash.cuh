@@ -154,22 +154,24 @@ __device__ __forceinline__ void load_dir(const DslashArgs& A, const Site& s, Dir
 
 // psi_r at half index nb; returns the factor still to be applied (the FP16 per-site scale, which
 // commutes with the spin projection and the link multiply, so it is applied once to the result)
-template <int P>
+template <int P, bool COH>
 __device__ __forceinline__ typename Real<P>::T load_neighbor(const DslashArgs& A, int r, int nb,
                                                              cx<typename Real<P>::T> sp[12]) {
   using R = typename Real<P>::T;
-  if (P == 16) return SpinorIO<16>::load_unscaled(A.in, A.in_norm, A.g.Vh, r, nb, reinterpret_cast<cx<float>*>(sp));
-  SpinorIO<P>::load(A.in, A.in_norm, A.g.Vh, r, nb, sp);
+  if (P == 16)
+    return SpinorIO<16>::template load_unscaled<COH>(A.in, A.in_norm, A.g.Vh, r, nb,
+                                                     reinterpret_cast<cx<float>*>(sp));
+  SpinorIO<P>::template load<COH>(A.in, A.in_norm, A.g.Vh, r, nb, sp);
   return R(1);
 }
 
 // acc += (1 - g_mu) U_mu(x) psi_r(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi_r(x-mu)
-template <int P, int MU>
+template <int P, int MU, bool COH = false>
 __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<typename Real<P>::T>& L, int r,
                                         cx<typename Real<P>::T> acc[12]) {
   using R = typename Real<P>::T;
   cx<R> sp[12], h[6], w[6];
-  R f = load_neighbor<P>(A, r, L.nbf, sp);
+  R f = load_neighbor<P, COH>(A, r, L.nbf, sp);
   if (A.in_g5) apply_g5(sp);
   project<MU, -1>(sp, h);
   su3_mul(L.uf, h, w);
@@ -179,7 +181,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
     for (int k = 0; k < 6; k++) w[k] = f * w[k];
   }
   accumulate<MU, -1>(w, acc);
-  f = load_neighbor<P>(A, r, L.nbb, sp);
+  f = load_neighbor<P, COH>(A, r, L.nbb, sp);
   if (A.in_g5) apply_g5(sp);
   project<MU, +1>(sp, h);
   su3_adj_mul(L.ub, h, w);
@@ -200,24 +202,149 @@ struct CloverPrec<32> { static constexpr int CP = 32; };
 template <>
 struct CloverPrec<16> { static constexpr int CP = 16; };
 
-// Hopping kernel.  A block of 128 threads handles 32 consecutive output sites: warp w computes
-// the two hops along mu = w for its lane's site (uniform per warp, no divergence), the four
-// partial sums meet in shared memory, warps 0 and 1 finish chiral block 0 and 1 (sum, clover
-// epilogue, gamma_5, norm or CG update), and the warps share the stores.  The links of a site
-// are loaded (and reconstructed) once and reused for every right-hand side, which the kernel
-// loops over (MULTI instantiations, nrhs > 1); FP64 reloads them per RHS to keep its register
-// count low, and so does the single-RHS instantiation.
-template <int P, int RECON, int EPI, bool MULTI>
-__global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
+// One (block of 32 output sites, RHS r) of the hopping operator on a 128-thread block: warp w
+// computes the two hops along mu = w for its lane's site (uniform per warp, no divergence), the
+// four partial sums meet in shared memory (part), warps 0 and 1 finish chiral block 0 and 1 (sum,
+// clover epilogue, gamma_5, norm or CG update) and the warps share the stores.  Links come from L
+// when KEEP_LINKS, else are loaded here.  COH reads spinors through L2 only (a persistent kernel
+// reading fields written by other blocks).  Returns the thread's share of |out|^2 (do_norm) or of
+// |r|^2 (EPI_XPAY_CG, with cg_alpha applied when cg_active).  All threads must call it; it
+// synchronises the block and leaves part free for the next call.
+template <int P, int RECON, int EPI, bool KEEP_LINKS, bool COH>
+__device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool valid, const Site& s,
+                                             DirLinks<typename Real<P>::T>& L, int r, bool cg_active,
+                                             double cg_alpha, cx<typename Real<P>::T> (*part)[12][32]) {
   using R = typename Real<P>::T;
-  constexpr bool KEEP_LINKS = MULTI && P != 64;
-  __shared__ cx<R> part[4][12][32];
-  if (A.halt && *A.halt) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int hh = blockIdx.x * 32 + lane;
-  const bool valid = hh < A.g.Vh;
-  Site s;
-  DirLinks<R> L;
+  {
+    cx<R> acc[12];
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
+    if (valid) {
+      switch (w) {
+        case 0:
+          if (!KEEP_LINKS) load_dir<P, RECON, 0>(A, s, L);
+          hop_dir<P, 0, COH>(A, L, r, acc);
+          break;
+        case 1:
+          if (!KEEP_LINKS) load_dir<P, RECON, 1>(A, s, L);
+          hop_dir<P, 1, COH>(A, L, r, acc);
+          break;
+        case 2:
+          if (!KEEP_LINKS) load_dir<P, RECON, 2>(A, s, L);
+          hop_dir<P, 2, COH>(A, L, r, acc);
+          break;
+        default:
+          if (!KEEP_LINKS) load_dir<P, RECON, 3>(A, s, L);
+          hop_dir<P, 3, COH>(A, L, r, acc);
+          break;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 12; c++) part[w][c][lane] = acc[c];
+  }
+  __syncthreads();
+  double nrm = 0.0;
+  if (w < 2 && valid) {
+    const int b = w;
+    cx<R> v[6], res[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const int c = 6 * b + k;
+      v[k] = (part[0][c][lane] + part[1][c][lane]) + (part[2][c][lane] + part[3][c][lane]);
+    }
+    if (EPI == EPI_NONE) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = v[k];
+    } else if (EPI == EPI_CLOVER_INV) {
+      CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, v, res);
+    } else {  // EPI_XPAY, EPI_XPAY_CG
+      cx<R> xs[6], cxs[6];
+      SpinorIO<P>::template load_block<COH>(A.x, A.x_norm, A.g.Vh, r, hh, b, xs);
+      if (A.x_g5 && b == 1) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) xs[k] = -xs[k];
+      }
+      CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, xs, cxs);
+      const R a = R(A.a);
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        res[k].re = fma(a, v[k].re, cxs[k].re);
+        res[k].im = fma(a, v[k].im, cxs[k].im);
+      }
+    }
+    if (A.out_g5 && b == 1) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = -res[k];
+    }
+    if (EPI == EPI_XPAY_CG) {
+      // res = (A p)_b: advance x and r of this RHS with alpha from the <p, A p> reduction
+      constexpr int PR = P == 64 ? 64 : 32;
+      using RR = typename Real<PR>::T;
+      if (cg_active) {
+        const RR al = RR(cg_alpha);
+        cx<R> ps[6];
+        cx<RR> xs[6], rs[6];
+        SpinorIO<P>::template load_block<COH>(A.cg_p, A.cg_p_norm, A.g.Vh, r, hh, b, ps);
+        SpinorIO<PR>::template load_block<COH>(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
+        SpinorIO<PR>::template load_block<COH>(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+          xs[k].re = fma(al, RR(ps[k].re), xs[k].re);
+          xs[k].im = fma(al, RR(ps[k].im), xs[k].im);
+          rs[k].re = fma(-al, RR(res[k].re), rs[k].re);
+          rs[k].im = fma(-al, RR(res[k].im), rs[k].im);
+          nrm += double(rs[k].re) * rs[k].re + double(rs[k].im) * rs[k].im;
+        }
+        SpinorIO<PR>::store_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
+        SpinorIO<PR>::store_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
+      }
+    } else {
+      if (A.do_norm) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) nrm += double(res[k].re) * res[k].re + double(res[k].im) * res[k].im;
+      }
+#pragma unroll
+      for (int k = 0; k < 6; k++) part[0][6 * b + k][lane] = res[k];
+    }
+  }
+  __syncthreads();
+  if (valid && EPI != EPI_XPAY_CG) {
+    if (P == 64) {
+      double2* q = static_cast<double2*>(A.out);
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const cx<R> v = part[0][3 * w + k][lane];
+        q[sidx<12>(3 * w + k, A.g.Vh, r, hh)] = make_double2(double(v.re), double(v.im));
+      }
+    } else if (P == 32) {
+      if (w < 3) {
+        float4* q = static_cast<float4*>(A.out);
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+          const cx<R> v0 = part[0][4 * w + 2 * k][lane], v1 = part[0][4 * w + 2 * k + 1][lane];
+          q[sidx<6>(2 * w + k, A.g.Vh, r, hh)] =
+              make_float4(float(v0.re), float(v0.im), float(v1.re), float(v1.im));
+        }
+      }
+    } else if (w == 0) {
+      cx<float> o[12];
+#pragma unroll
+      for (int c = 0; c < 12; c++) o[c] = cmk(float(part[0][c][lane].re), float(part[0][c][lane].im));
+      SpinorIO<16>::store(A.out, A.out_norm, A.g.Vh, r, hh, o);
+    }
+  }
+  __syncthreads();
+  return nrm;
+}
+
+// Site and links of a lane in the block of 32 sites starting at 32 * sb.
+template <int P, int RECON, bool KEEP_LINKS>
+__device__ __forceinline__ void split_prologue(const DslashArgs& A, int sb, int& hh, bool& valid, Site& s,
+                                               DirLinks<typename Real<P>::T>& L) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  hh = sb * 32 + lane;
+  valid = hh < A.g.Vh;
   if (valid) {
     s = site_of(A.g, A.p, hh);
     if (KEEP_LINKS) {
@@ -229,129 +356,33 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
       }
     }
   }
+}
+
+// Hopping kernel: one block per 32 output sites, looping over the right-hand sides.  The links of
+// a site are loaded (and reconstructed) once and reused for every RHS in the multi-RHS
+// instantiations (MULTI); FP64 and the single-RHS instantiations reload them per RHS to keep the
+// register count low.
+template <int P, int RECON, int EPI, bool MULTI>
+__global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
+  using R = typename Real<P>::T;
+  constexpr bool KEEP_LINKS = MULTI && P != 64;
+  __shared__ cx<R> part[4][12][32];
+  if (A.halt && *A.halt) return;
+  int hh;
+  bool valid;
+  Site s;
+  DirLinks<R> L;
+  split_prologue<P, RECON, KEEP_LINKS>(A, blockIdx.x, hh, valid, s, L);
   const bool reduce = A.do_norm || EPI == EPI_XPAY_CG;
   for (int r = 0; r < A.nrhs; r++) {
-    {
-      cx<R> acc[12];
-#pragma unroll
-      for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
-      if (valid) {
-        switch (w) {
-          case 0:
-            if (!KEEP_LINKS) load_dir<P, RECON, 0>(A, s, L);
-            hop_dir<P, 0>(A, L, r, acc);
-            break;
-          case 1:
-            if (!KEEP_LINKS) load_dir<P, RECON, 1>(A, s, L);
-            hop_dir<P, 1>(A, L, r, acc);
-            break;
-          case 2:
-            if (!KEEP_LINKS) load_dir<P, RECON, 2>(A, s, L);
-            hop_dir<P, 2>(A, L, r, acc);
-            break;
-          default:
-            if (!KEEP_LINKS) load_dir<P, RECON, 3>(A, s, L);
-            hop_dir<P, 3>(A, L, r, acc);
-            break;
-        }
-      }
-#pragma unroll
-      for (int c = 0; c < 12; c++) part[w][c][lane] = acc[c];
+    bool act = false;
+    double al = 0.0;
+    if (EPI == EPI_XPAY_CG) {
+      act = A.red.cg[r].active != 0;
+      al = A.red.cg[r].alpha;
     }
-    __syncthreads();
-    double nrm = 0.0;
-    if (w < 2 && valid) {
-      const int b = w;
-      cx<R> v[6], res[6];
-#pragma unroll
-      for (int k = 0; k < 6; k++) {
-        const int c = 6 * b + k;
-        v[k] = (part[0][c][lane] + part[1][c][lane]) + (part[2][c][lane] + part[3][c][lane]);
-      }
-      if (EPI == EPI_NONE) {
-#pragma unroll
-        for (int k = 0; k < 6; k++) res[k] = v[k];
-      } else if (EPI == EPI_CLOVER_INV) {
-        CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, v, res);
-      } else {  // EPI_XPAY, EPI_XPAY_CG
-        cx<R> xs[6], cxs[6];
-        SpinorIO<P>::load_block(A.x, A.x_norm, A.g.Vh, r, hh, b, xs);
-        if (A.x_g5 && b == 1) {
-#pragma unroll
-          for (int k = 0; k < 6; k++) xs[k] = -xs[k];
-        }
-        CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, xs, cxs);
-        const R a = R(A.a);
-#pragma unroll
-        for (int k = 0; k < 6; k++) {
-          res[k].re = fma(a, v[k].re, cxs[k].re);
-          res[k].im = fma(a, v[k].im, cxs[k].im);
-        }
-      }
-      if (A.out_g5 && b == 1) {
-#pragma unroll
-        for (int k = 0; k < 6; k++) res[k] = -res[k];
-      }
-      if (EPI == EPI_XPAY_CG) {
-        // res = (A p)_b: advance x and r of this RHS with alpha from the <p, A p> reduction
-        constexpr int PR = P == 64 ? 64 : 32;
-        using RR = typename Real<PR>::T;
-        const CGState& st = A.red.cg[r];
-        if (st.active) {
-          const RR al = RR(st.alpha);
-          cx<R> ps[6];
-          cx<RR> xs[6], rs[6];
-          SpinorIO<P>::load_block(A.cg_p, A.cg_p_norm, A.g.Vh, r, hh, b, ps);
-          SpinorIO<PR>::load_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
-          SpinorIO<PR>::load_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
-#pragma unroll
-          for (int k = 0; k < 6; k++) {
-            xs[k].re = fma(al, RR(ps[k].re), xs[k].re);
-            xs[k].im = fma(al, RR(ps[k].im), xs[k].im);
-            rs[k].re = fma(-al, RR(res[k].re), rs[k].re);
-            rs[k].im = fma(-al, RR(res[k].im), rs[k].im);
-            nrm += double(rs[k].re) * rs[k].re + double(rs[k].im) * rs[k].im;
-          }
-          SpinorIO<PR>::store_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
-          SpinorIO<PR>::store_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
-        }
-      } else {
-        if (A.do_norm) {
-#pragma unroll
-          for (int k = 0; k < 6; k++) nrm += double(res[k].re) * res[k].re + double(res[k].im) * res[k].im;
-        }
-#pragma unroll
-        for (int k = 0; k < 6; k++) part[0][6 * b + k][lane] = res[k];
-      }
-    }
-    __syncthreads();
-    if (valid && EPI != EPI_XPAY_CG) {
-      if (P == 64) {
-        double2* q = static_cast<double2*>(A.out);
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-          const cx<R> v = part[0][3 * w + k][lane];
-          q[sidx<12>(3 * w + k, A.g.Vh, r, hh)] = make_double2(double(v.re), double(v.im));
-        }
-      } else if (P == 32) {
-        if (w < 3) {
-          float4* q = static_cast<float4*>(A.out);
-#pragma unroll
-          for (int k = 0; k < 2; k++) {
-            const cx<R> v0 = part[0][4 * w + 2 * k][lane], v1 = part[0][4 * w + 2 * k + 1][lane];
-            q[sidx<6>(2 * w + k, A.g.Vh, r, hh)] =
-                make_float4(float(v0.re), float(v0.im), float(v1.re), float(v1.im));
-          }
-        }
-      } else if (w == 0) {
-        cx<float> o[12];
-#pragma unroll
-        for (int c = 0; c < 12; c++) o[c] = cmk(float(part[0][c][lane].re), float(part[0][c][lane].im));
-        SpinorIO<16>::store(A.out, A.out_norm, A.g.Vh, r, hh, o);
-      }
-    }
-    if (reduce) block_partial<128>(nrm, r, blockIdx.x, gridDim.x, A.red);  // contains __syncthreads
-    else __syncthreads();
+    const double nrm = split_unit<P, RECON, EPI, KEEP_LINKS, false>(A, hh, valid, s, L, r, act, al, part);
+    if (reduce) block_partial<128>(nrm, r, blockIdx.x, gridDim.x, A.red);
   }
   if (reduce) grid_finish<128>(A.nrhs, gridDim.x, gridDim.x, A.red);
 }

@@ -123,6 +123,14 @@ struct Real<32> { using T = float; };
 template <>
 struct Real<16> { using T = float; };
 
+// Loads of spinor data: through the read-only path by default; COH = true reads through L2 only,
+// for data that other blocks of the same (persistent) kernel have written.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldv(const T* p) {
+  if (COH) return __ldcg(p);
+  return __ldg(p);
+}
+
 // spinor accessors: 12 complex components, component c = 3*spin + colour.  A field of nrhs
 // right-hand sides is stored RHS-major: vector k of (RHS r, site h) at (r * NVEC + k) * Vh + h, so
 // the lanes of a warp (consecutive sites of one RHS) read one contiguous run.
@@ -137,11 +145,12 @@ struct SpinorIO;
 template <>
 struct SpinorIO<64> {
   static constexpr int NVEC = 12;  // double2 per site
+  template <bool COH = false>
   __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<double> s[12]) {
     const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 12; c++) {
-      double2 v = __ldg(p + sidx<NVEC>(c, Vh, r, h));
+      double2 v = ldv<COH>(p + sidx<NVEC>(c, Vh, r, h));
       s[c] = cmk(v.x, v.y);
     }
   }
@@ -151,12 +160,13 @@ struct SpinorIO<64> {
     for (int c = 0; c < 12; c++) p[sidx<NVEC>(c, Vh, r, h)] = make_double2(s[c].re, s[c].im);
   }
   // components 6b..6b+5 (chiral block b: spins 2b, 2b+1)
+  template <bool COH = false>
   __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b,
                                     cx<double> s[6]) {
     const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 6; c++) {
-      double2 v = __ldg(p + sidx<NVEC>(6 * b + c, Vh, r, h));
+      double2 v = ldv<COH>(p + sidx<NVEC>(6 * b + c, Vh, r, h));
       s[c] = cmk(v.x, v.y);
     }
   }
@@ -171,11 +181,12 @@ struct SpinorIO<64> {
 template <>
 struct SpinorIO<32> {
   static constexpr int NVEC = 6;  // float4 per site
+  template <bool COH = false>
   __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<float> s[12]) {
     const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 6; k++) {
-      float4 v = __ldg(p + sidx<NVEC>(k, Vh, r, h));
+      float4 v = ldv<COH>(p + sidx<NVEC>(k, Vh, r, h));
       s[2 * k] = cmk(v.x, v.y);
       s[2 * k + 1] = cmk(v.z, v.w);
     }
@@ -186,12 +197,13 @@ struct SpinorIO<32> {
     for (int k = 0; k < 6; k++)
       p[sidx<NVEC>(k, Vh, r, h)] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
   }
+  template <bool COH = false>
   __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b,
                                     cx<float> s[6]) {
     const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      float4 v = __ldg(p + sidx<NVEC>(3 * b + k, Vh, r, h));
+      float4 v = ldv<COH>(p + sidx<NVEC>(3 * b + k, Vh, r, h));
       s[2 * k] = cmk(v.x, v.y);
       s[2 * k + 1] = cmk(v.z, v.w);
     }
@@ -220,12 +232,13 @@ __device__ __forceinline__ uint32_t f2h(float a, float b) {
 template <>
 struct SpinorIO<16> {
   static constexpr int NVEC = 3;  // uint4 per site
+  template <bool COH = false>
   __device__ static void load(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
     const uint4* p = static_cast<const uint4*>(base);
-    const float n = __ldg(nrm + (size_t)r * Vh + h);
+    const float n = ldv<COH>(nrm + (size_t)r * Vh + h);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint4 v = __ldg(p + sidx<NVEC>(k, Vh, r, h));
+      uint4 v = ldv<COH>(p + sidx<NVEC>(k, Vh, r, h));
       float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
       s[4 * k + 0] = cmk(a.x * n, a.y * n);
       s[4 * k + 1] = cmk(b.x * n, b.y * n);
@@ -234,18 +247,19 @@ struct SpinorIO<16> {
     }
   }
   // the stored values v / n without the per-site scale n, which is returned
+  template <bool COH = false>
   __device__ static float load_unscaled(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
     const uint4* p = static_cast<const uint4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint4 v = __ldg(p + sidx<NVEC>(k, Vh, r, h));
+      uint4 v = ldv<COH>(p + sidx<NVEC>(k, Vh, r, h));
       float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
       s[4 * k + 0] = cmk(a.x, a.y);
       s[4 * k + 1] = cmk(b.x, b.y);
       s[4 * k + 2] = cmk(c.x, c.y);
       s[4 * k + 3] = cmk(d.x, d.y);
     }
-    return __ldg(nrm + (size_t)r * Vh + h);
+    return ldv<COH>(nrm + (size_t)r * Vh + h);
   }
   __device__ static void store(void* base, float* nrm, int Vh, int r, int h, const cx<float> s[12]) {
     float m = 0.f;
@@ -265,12 +279,13 @@ struct SpinorIO<16> {
     nrm[(size_t)r * Vh + h] = m;
   }
   // block 0 = chunk 0 and the first half of chunk 1; block 1 = the second half of chunk 1 and chunk 2
+  template <bool COH = false>
   __device__ static void load_block(const void* base, const float* nrm, int Vh, int r, int h, int b,
                                     cx<float> s[6]) {
     const uint4* p = static_cast<const uint4*>(base);
-    const float n = __ldg(nrm + (size_t)r * Vh + h);
-    const uint4 mid = __ldg(p + sidx<NVEC>(1, Vh, r, h));
-    const uint4 end = __ldg(p + sidx<NVEC>(b == 0 ? 0 : 2, Vh, r, h));
+    const float n = ldv<COH>(nrm + (size_t)r * Vh + h);
+    const uint4 mid = ldv<COH>(p + sidx<NVEC>(1, Vh, r, h));
+    const uint4 end = ldv<COH>(p + sidx<NVEC>(b == 0 ? 0 : 2, Vh, r, h));
     float2 e0 = h2f(end.x), e1 = h2f(end.y), e2 = h2f(end.z), e3 = h2f(end.w);
     if (b == 0) {
       float2 m0 = h2f(mid.x), m1 = h2f(mid.y);

@@ -10,6 +10,28 @@ namespace qcd {
 // kernels launched by the library since the last reset (profiling)
 extern long long g_kernel_launches;
 
+// ---- persistent single-RHS CG iteration (qcd_cg_persistent.cu)
+struct PersistentCGArgs {
+  Geom g;
+  const void* gauge;           // links of the inner precision
+  const void* clover_inv_odd;  // A_oo^-1 of the inner precision
+  const void* clover_even;     // A_ee of the inner precision
+  void *p, *t, *y;             // inner-precision fields (t odd, p and y even)
+  float *p_n, *t_n, *y_n;      // FP16 norms (null otherwise)
+  void *x, *r;                 // x_lo, r_lo (FP64 for inner 64, else FP32)
+  double k2;                   // kappa^2
+  CGState* cg;                 // state of the single RHS
+  CGControl* ctl;
+  double *part_pap, *part_rr;  // one slot per block
+  int slots;                   // slots in each; the grid never exceeds it
+  unsigned *bar_count, *bar_gen;
+  int* bar_err;                // set when a barrier wait gave up
+  int max_iters;               // iterations this launch may run
+};
+cudaError_t launch_cg_persistent(int prec, int recon, const PersistentCGArgs& q, cudaStream_t st);
+// one grid barrier that a block never reaches (the wait must give up and set *err)
+cudaError_t launch_barrier_probe(unsigned* count, unsigned* gen, int* err, cudaStream_t st);
+
 // ---- layout (qcd_layout.cu)
 void launch_pack_gauge(const Geom& g, const double2* canon, void* g64, void* g32, int recon32, void* g16,
                        int recon16, cudaStream_t st);

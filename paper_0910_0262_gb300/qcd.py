@@ -69,6 +69,7 @@ _SIGNATURES = {
     "qcd_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "qcd_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "qcd_mhat_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
+    "qcd_selftest_barrier_timeout": (ctypes.c_int, [_P]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -149,6 +150,11 @@ def qcd_profile_read(ctx, max_entries=64):
 def qcd_mhat_static(ctx, out_ptr, in_ptr, dagger=0):
     """Mhat (or Mhat^dag) in FP64 on one field with no device allocation (see include/qcd.h)."""
     return _check(lib().qcd_mhat_static(ctx, out_ptr, in_ptr, int(dagger)))
+
+
+def qcd_selftest_barrier_timeout(ctx):
+    """Returns the status of the barrier self-test (QCD_ERR_TIMEOUT = 8 when the wait gave up)."""
+    return lib().qcd_selftest_barrier_timeout(ctx)
 
 
 def qcd_last_error():

@@ -109,3 +109,15 @@ def test_host_gauge_pointer_matches_device(Q):
     c2.load_gauge(torch.from_numpy(U.copy()))
     xb = to_dev(b)
     assert torch.equal(c1.dslash(xb, Q.QCD_OP_DSLASH_OE), c2.dslash(xb, Q.QCD_OP_DSLASH_OE))
+
+
+def test_barrier_wait_runs_out_and_context_survives(Q):
+    """A grid-barrier wait with a block that never arrives gives up and reports QCD_ERR_TIMEOUT."""
+    c = Q.CloverWilson((4, 4, 4, 4))
+    assert Q.qcd_selftest_barrier_timeout(c.ctx) == 8
+    assert "gave up" in Q.qcd_last_error()
+    U, b = synth.make_problem((4, 4, 4, 4), 0.2, 3)
+    c.load_gauge(to_dev(U))
+    c.clover_build(0.12, 1.0)
+    x, stats, ok = c.cg_solve(to_dev(b))
+    assert ok and stats[0]["true_rel_resid"] <= 1e-8
