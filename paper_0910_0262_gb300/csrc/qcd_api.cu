@@ -154,7 +154,7 @@ struct qcd_ctx {
   // persistent single-RHS iteration: per-block partial sums and the grid barrier words
   double* pc_part = nullptr;   // 2 x pc_slots
   int pc_slots = 0;
-  unsigned* pc_bar = nullptr;  // [0] count, [1] generation, [2] error
+  unsigned* pc_bar = nullptr;  // [0] barrier arrivals, [2] error
   bool persistent = true;
   struct {
     cudaEvent_t a, b;
@@ -926,7 +926,6 @@ qcd_status launch_persistent(qcd_ctx* c, const SolverFields& f, int max_iters) {
   q.part_rr = c->pc_part + c->pc_slots;
   q.slots = c->pc_slots;
   q.bar_count = c->pc_bar;
-  q.bar_gen = c->pc_bar + 1;
   q.bar_err = reinterpret_cast<int*>(c->pc_bar + 2);
   q.max_iters = max_iters < 1 ? 1 : max_iters;
   CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, sizeof(unsigned), c->st));
@@ -1239,7 +1238,7 @@ qcd_status qcd_selftest_barrier_timeout(qcd_ctx* c) {
   qcd_status s = check_ctx(c);
   if (s) return s;
   CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 4 * sizeof(unsigned), c->st));
-  CUDA_TRY(launch_barrier_probe(c->pc_bar, c->pc_bar + 1, reinterpret_cast<int*>(c->pc_bar + 2), c->st));
+  CUDA_TRY(launch_barrier_probe(c->pc_bar, reinterpret_cast<int*>(c->pc_bar + 2), c->st));
   CUDA_TRY(cudaMemcpyAsync(c->h_flags + 2, c->pc_bar + 2, sizeof(int), cudaMemcpyDeviceToHost, c->st));
   if ((s = sync_and_check(c, "barrier self-test"))) return s;
   CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 4 * sizeof(unsigned), c->st));

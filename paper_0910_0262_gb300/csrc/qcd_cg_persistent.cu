@@ -14,8 +14,9 @@
 //
 // Sums are formed per block over a fixed set of site blocks and then, after the barrier, added in
 // block order by every block, so all blocks hold the same alpha and beta.  Fields written inside
-// the kernel are read through L2 only.  Every barrier wait is bounded: a block that has waited too
-// long sets an error word and all blocks return (the host reports QCD_ERR_TIMEOUT).
+// the kernel are read with ordinary loads after the barrier.  Every barrier wait is bounded: a
+// block that has waited too long sets an error word and all blocks return (the host reports
+// QCD_ERR_TIMEOUT).
 #include "qcd_dslash.cuh"
 #include "qcd_kernels.h"
 
@@ -25,29 +26,30 @@ namespace {
 
 constexpr unsigned BARRIER_SPIN_LIMIT = 1u << 22;  // polls of an L2 word: about a second or more
 
-// Grid-wide barrier of a cooperative launch.  Returns false (on every thread of the block) if this
-// block gave up waiting or another block reported an error.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* err) {
+// Grid-wide barrier of a cooperative launch.  Arrivals count up one word, which the host zeroes
+// before the launch; the k-th barrier of the launch is passed when the word reaches k * gridDim.x.
+// target holds that value for this block and is advanced here.  The arrival is a release and the
+// poll an acquire at GPU scope, so the block's earlier writes are visible to every block after the
+// barrier.  Returns false (on every thread of the block) if this block gave up waiting or another
+// block reported an error.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& target, int* err) {
   __shared__ int ok;
+  target += gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = gen;
-    volatile int* verr = err;
-    const unsigned g0 = *vgen;
-    __threadfence();
     ok = 1;
-    if (atomicAdd(count, 1u) + 1 == gridDim.x) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      unsigned spins = 0;
-      while (*vgen == g0) {
-        if (*verr) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+    unsigned spins = 0;
+    while (true) {
+      unsigned v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+      if ((int)(v - target) >= 0) break;
+      if ((++spins & 31) == 0) {
+        if (*reinterpret_cast<volatile int*>(err)) {
           ok = 0;
           break;
         }
-        if (++spins > BARRIER_SPIN_LIMIT) {
+        if (spins > BARRIER_SPIN_LIMIT) {
           atomicExch(err, 1);
           ok = 0;
           break;
@@ -73,11 +75,21 @@ __device__ __forceinline__ double block_sum128(double v) {
 }
 
 // sum of the gridDim.x per-block partials, on every thread: each thread adds a fixed strided
-// subset, then a fixed shuffle / shared-memory tree, so every block gets the same bits
+// subset (its loads issued together), then a fixed shuffle / shared-memory tree, so every block
+// gets the same bits
 __device__ __forceinline__ double grid_total(const double* part) {
   __shared__ double sm[4];
   double s = 0.0;
-  for (int j = threadIdx.x; j < (int)gridDim.x; j += 128) s += __ldcg(part + j);
+  for (int base = 0; base < (int)gridDim.x; base += 8 * 128) {
+    double v[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const int j = base + (int)threadIdx.x + 128 * i;
+      v[i] = j < (int)gridDim.x ? __ldcg(part + j) : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) s += v[i];
+  }
   for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -86,8 +98,13 @@ __device__ __forceinline__ double grid_total(const double* part) {
   return t;
 }
 
+// load mode of the fields the kernel writes: cached in L1, which the acquire of each grid barrier
+// invalidates, so neighbours shared by the sites of a block are read from L2 once
+constexpr int LDM = LD_CA;
+
 template <int P, int RECON, int EPI>
-__device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Real<P>::T> (*part)[12][32], double alpha) {
+__device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Real<P>::T> (*part)[12][32],
+                                            uint4* stage, double alpha) {
   using R = typename Real<P>::T;
   const int nsb = (A.g.Vh + 31) / 32;
   double v = 0.0;
@@ -97,7 +114,7 @@ __device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Rea
     Site s;
     DirLinks<R> L;
     split_prologue<P, RECON, false>(A, sb, hh, valid, s, L);
-    v += split_unit<P, RECON, EPI, false, true>(A, hh, valid, s, L, 0, true, alpha, part);
+    v += split_unit<P, RECON, EPI, false, LDM>(A, hh, valid, s, L, 0, true, alpha, part, stage, true);
   }
   return v;
 }
@@ -108,6 +125,7 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
   constexpr int PR = P == 64 ? 64 : 32;
   using RR = typename Real<PR>::T;
   __shared__ cx<R> part[4][12][32];
+  __shared__ uint4 stage[Stage<P, EPI_XPAY_CG>::U4];  // the largest staging of the three epilogues
   const CGState st0 = *Q.cg;
   if (!st0.active || Q.ctl->halt) return;
   double rr = st0.rr, rr_prev = st0.rr_prev;
@@ -133,13 +151,14 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
   a2.in_norm = Q.t_n;
 
   double alpha = 0.0, beta = 0.0, pAp = 0.0;
+  unsigned bar_target = 0;
   for (int it = 0; it < Q.max_iters; it++) {
     // phase 1
     a1.in = Q.p;
     a1.in_norm = Q.p_n;
     a1.in_g5 = 0;
-    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, 0.0);
-    if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, stage, 0.0);
+    if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     // phase 2
     {
       DslashArgs a = a2;
@@ -148,10 +167,10 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
       a.out = Q.y;
       a.out_norm = Q.y_n;
       a.do_norm = 1;
-      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY>(a, part, 0.0));
+      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY>(a, part, stage, 0.0));
       if (threadIdx.x == 0) Q.part_pap[blockIdx.x] = v;
     }
-    if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+    if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     pAp = grid_total(Q.part_pap);
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -165,8 +184,8 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
     a1.in = Q.y;
     a1.in_norm = Q.y_n;
     a1.in_g5 = 1;
-    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, 0.0);
-    if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, stage, 0.0);
+    if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     // phase 4
     {
       DslashArgs a = a2;
@@ -178,10 +197,10 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
       a.cg_r = Q.r;
       a.cg_p = Q.p;
       a.cg_p_norm = Q.p_n;
-      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY_CG>(a, part, alpha));
+      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY_CG>(a, part, stage, alpha));
       if (threadIdx.x == 0) Q.part_rr[blockIdx.x] = v;
     }
-    if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+    if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     const double rr_new = grid_total(Q.part_rr);
     if (!isfinite(rr_new)) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -201,8 +220,8 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
       for (int h = blockIdx.x * 128 + threadIdx.x; h < Vh; h += gridDim.x * 128) {
         cx<RR> rs[12];
         cx<R> ps[12], out[12];
-        SpinorIO<PR>::template load<true>(Q.r, nullptr, Vh, 0, h, rs);
-        SpinorIO<P>::template load<true>(Q.p, Q.p_n, Vh, 0, h, ps);
+        SpinorIO<PR>::template load<LDM>(Q.r, nullptr, Vh, 0, h, rs);
+        SpinorIO<P>::template load<LDM>(Q.p, Q.p_n, Vh, 0, h, ps);
         const RR b = RR(beta);
 #pragma unroll
         for (int c = 0; c < 12; c++) {
@@ -211,7 +230,7 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
         }
         SpinorIO<P>::store(Q.p, Q.p_n, Vh, 0, h, out);
       }
-      if (!grid_barrier(Q.bar_count, Q.bar_gen, Q.bar_err)) return;
+      if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     }
     if (want || it == Q.max_iters - 1) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -235,9 +254,10 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
 
 // Two blocks meet at one grid barrier, except that block `absent` returns first: the other
 // block's wait must run out, set *err and return.
-__global__ void barrier_probe_kernel(unsigned* count, unsigned* gen, int* err, int absent) {
+__global__ void barrier_probe_kernel(unsigned* count, int* err, int absent) {
   if ((int)blockIdx.x == absent) return;
-  grid_barrier(count, gen, err);
+  unsigned target = 0;
+  grid_barrier(count, target, err);
 }
 
 template <int P, int RECON>
@@ -263,10 +283,10 @@ cudaError_t launch_pc(const PersistentCGArgs& q, cudaStream_t st) {
 
 }  // namespace
 
-cudaError_t launch_barrier_probe(unsigned* count, unsigned* gen, int* err, cudaStream_t st) {
+cudaError_t launch_barrier_probe(unsigned* count, int* err, cudaStream_t st) {
   g_kernel_launches += 1;
   int absent = 1;
-  void* args[] = {&count, &gen, &err, &absent};
+  void* args[] = {&count, &err, &absent};
   return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(barrier_probe_kernel), dim3(2), dim3(32), args, 0, st);
 }
 

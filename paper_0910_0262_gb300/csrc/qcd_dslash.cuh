@@ -154,7 +154,7 @@ __device__ __forceinline__ void load_dir(const DslashArgs& A, const Site& s, Dir
 
 // psi_r at half index nb; returns the factor still to be applied (the FP16 per-site scale, which
 // commutes with the spin projection and the link multiply, so it is applied once to the result)
-template <int P, bool COH>
+template <int P, int COH>
 __device__ __forceinline__ typename Real<P>::T load_neighbor(const DslashArgs& A, int r, int nb,
                                                              cx<typename Real<P>::T> sp[12]) {
   using R = typename Real<P>::T;
@@ -166,7 +166,7 @@ __device__ __forceinline__ typename Real<P>::T load_neighbor(const DslashArgs& A
 }
 
 // acc += (1 - g_mu) U_mu(x) psi_r(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi_r(x-mu)
-template <int P, int MU, bool COH = false>
+template <int P, int MU, int COH = LD_NC>
 __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<typename Real<P>::T>& L, int r,
                                         cx<typename Real<P>::T> acc[12]) {
   using R = typename Real<P>::T;
@@ -202,20 +202,85 @@ struct CloverPrec<32> { static constexpr int CP = 32; };
 template <>
 struct CloverPrec<16> { static constexpr int CP = 16; };
 
+// Staging of the epilogue's operands.  The clover blocks, the local term x and the CG vectors of a
+// unit's 32 sites do not depend on the hopping sum, so the unit starts by copying them into shared
+// memory with cp.async (through L2 only); they arrive while the hops are computed and the epilogue
+// reads them from shared memory.  Rows of 32 consecutive 16-byte elements, in the order: clover
+// pair, x (+ 32 norms for FP16), p (+ norms), x_lo, r_lo.  FP64 units (bound by the FP64 pipe)
+// load their operands directly.
+template <int P, int EPI>
+struct Stage {
+  static constexpr bool ON = P != 64 && EPI != EPI_NONE;
+  static constexpr int CL = P == 32 ? 18 : 9;               // rows of the clover pair
+  static constexpr int SP = P == 32 ? 6 : 3;                // rows of a spinor of precision P
+  static constexpr int SPN = SP * 32 + (P == 16 ? 8 : 0);   // elements, with the norms
+  static constexpr bool XR = EPI == EPI_XPAY || EPI == EPI_XPAY_CG;
+  static constexpr bool CG = EPI == EPI_XPAY_CG;
+  static constexpr int OFF_X = CL * 32;
+  static constexpr int OFF_P = OFF_X + (XR ? SPN : 0);
+  static constexpr int OFF_CX = OFF_P + (CG ? SPN : 0);
+  static constexpr int OFF_CR = OFF_CX + (CG ? 6 * 32 : 0);
+  static constexpr int U4 = ON ? OFF_CR + (CG ? 6 * 32 : 0) : 1;  // uint4 elements of the buffer
+};
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ROWS rows of 32 16-byte elements, row j read from src + j * stride; only the first n elements of
+// a row (the unit's valid sites) are copied
+template <int ROWS>
+__device__ __forceinline__ void stage_rows(uint4* dst, const uint4* src, size_t stride, int n) {
+#pragma unroll
+  for (int k = 0; k < (ROWS * 32 + 127) / 128; k++) {
+    const int i = threadIdx.x + 128 * k;
+    if (i < ROWS * 32 && (i & 31) < n) cp_async16(dst + i, src + (size_t)(i >> 5) * stride + (i & 31));
+  }
+}
+
+// a spinor of precision P (RHS r, sites hh0 .. hh0+n-1) and, for FP16, its norms
+template <int P>
+__device__ __forceinline__ void stage_spinor(uint4* dst, const void* base, const float* nrm, int Vh, int r, int hh0,
+                                             int n) {
+  constexpr int SP = P == 32 ? 6 : 3;
+  stage_rows<SP>(dst, static_cast<const uint4*>(base) + sidx<SP>(0, Vh, r, hh0), Vh, n);
+  // 32 norms = 8 16-byte pieces; n is a multiple of 8 (Vh is), the source 16-byte aligned
+  if (P == 16 && threadIdx.x < 8 && 4 * (int)threadIdx.x < n)
+    cp_async16(dst + SP * 32 + threadIdx.x, nrm + (size_t)r * Vh + hh0 + 4 * threadIdx.x);
+}
+
 // One (block of 32 output sites, RHS r) of the hopping operator on a 128-thread block: warp w
 // computes the two hops along mu = w for its lane's site (uniform per warp, no divergence), the
 // four partial sums meet in shared memory (part), warps 0 and 1 finish chiral block 0 and 1 (sum,
 // clover epilogue, gamma_5, norm or CG update) and the warps share the stores.  Links come from L
-// when KEEP_LINKS, else are loaded here.  COH reads spinors through L2 only (a persistent kernel
-// reading fields written by other blocks).  Returns the thread's share of |out|^2 (do_norm) or of
-// |r|^2 (EPI_XPAY_CG, with cg_alpha applied when cg_active).  All threads must call it; it
-// synchronises the block and leaves part free for the next call.
-template <int P, int RECON, int EPI, bool KEEP_LINKS, bool COH>
+// when KEEP_LINKS, else are loaded here.  COH is the load mode of the spinor fields (LD_NC, or a
+// coherent mode for a persistent kernel reading fields that other blocks wrote).  Returns the thread's share of |out|^2 (do_norm) or of
+// |r|^2 (EPI_XPAY_CG, with cg_alpha applied when cg_active).  The epilogue's operands are staged in
+// stage (Stage<P, EPI>); the clover pair only when fetch_clover (it is kept from an earlier call on
+// the same sites otherwise).  All threads must call it; it synchronises the block and leaves part
+// and stage free for the next call.
+template <int P, int RECON, int EPI, bool KEEP_LINKS, int COH>
 __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool valid, const Site& s,
                                              DirLinks<typename Real<P>::T>& L, int r, bool cg_active,
-                                             double cg_alpha, cx<typename Real<P>::T> (*part)[12][32]) {
+                                             double cg_alpha, cx<typename Real<P>::T> (*part)[12][32],
+                                             uint4* stage, bool fetch_clover) {
   using R = typename Real<P>::T;
+  using ST = Stage<P, EPI>;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (ST::ON) {
+    const int hh0 = hh - lane, n = min(32, A.g.Vh - hh0);
+    if (fetch_clover) stage_rows<ST::CL>(stage, static_cast<const uint4*>(A.clover) + hh0, A.g.Vh, n);
+    if (ST::XR) stage_spinor<P>(stage + ST::OFF_X, A.x, A.x_norm, A.g.Vh, r, hh0, n);
+    if (ST::CG && cg_active) {
+      stage_spinor<P>(stage + ST::OFF_P, A.cg_p, A.cg_p_norm, A.g.Vh, r, hh0, n);
+      stage_spinor<32>(stage + ST::OFF_CX, A.cg_x, nullptr, A.g.Vh, r, hh0, n);
+      stage_spinor<32>(stage + ST::OFF_CR, A.cg_r, nullptr, A.g.Vh, r, hh0, n);
+    }
+    cp_async_commit();
+  }
   {
     cx<R> acc[12];
 #pragma unroll
@@ -243,8 +308,11 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
 #pragma unroll
     for (int c = 0; c < 12; c++) part[w][c][lane] = acc[c];
   }
+  if (ST::ON) cp_async_wait_all();
   __syncthreads();
   double nrm = 0.0;
+  const float* st_xn = reinterpret_cast<const float*>(stage + ST::OFF_X + ST::SP * 32);
+  const float* st_pn = reinterpret_cast<const float*>(stage + ST::OFF_P + ST::SP * 32);
   if (w < 2 && valid) {
     const int b = w;
     cx<R> v[6], res[6];
@@ -257,15 +325,18 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
 #pragma unroll
       for (int k = 0; k < 6; k++) res[k] = v[k];
     } else if (EPI == EPI_CLOVER_INV) {
-      CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, v, res);
+      if (ST::ON) CloverIO<CloverPrec<P>::CP>::template apply<LD_SM>(stage, 32, lane, b, v, res);
+      else CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, v, res);
     } else {  // EPI_XPAY, EPI_XPAY_CG
       cx<R> xs[6], cxs[6];
-      SpinorIO<P>::template load_block<COH>(A.x, A.x_norm, A.g.Vh, r, hh, b, xs);
+      if (ST::ON) SpinorIO<P>::template load_block<LD_SM>(stage + ST::OFF_X, st_xn, 32, 0, lane, b, xs);
+      else SpinorIO<P>::template load_block<COH>(A.x, A.x_norm, A.g.Vh, r, hh, b, xs);
       if (A.x_g5 && b == 1) {
 #pragma unroll
         for (int k = 0; k < 6; k++) xs[k] = -xs[k];
       }
-      CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, xs, cxs);
+      if (ST::ON) CloverIO<CloverPrec<P>::CP>::template apply<LD_SM>(stage, 32, lane, b, xs, cxs);
+      else CloverIO<CloverPrec<P>::CP>::apply(A.clover, A.g.Vh, hh, b, xs, cxs);
       const R a = R(A.a);
 #pragma unroll
       for (int k = 0; k < 6; k++) {
@@ -285,9 +356,15 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
         const RR al = RR(cg_alpha);
         cx<R> ps[6];
         cx<RR> xs[6], rs[6];
-        SpinorIO<P>::template load_block<COH>(A.cg_p, A.cg_p_norm, A.g.Vh, r, hh, b, ps);
-        SpinorIO<PR>::template load_block<COH>(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
-        SpinorIO<PR>::template load_block<COH>(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
+        if (ST::ON) {
+          SpinorIO<P>::template load_block<LD_SM>(stage + ST::OFF_P, st_pn, 32, 0, lane, b, ps);
+          SpinorIO<PR>::template load_block<LD_SM>(stage + ST::OFF_CX, nullptr, 32, 0, lane, b, xs);
+          SpinorIO<PR>::template load_block<LD_SM>(stage + ST::OFF_CR, nullptr, 32, 0, lane, b, rs);
+        } else {
+          SpinorIO<P>::template load_block<COH>(A.cg_p, A.cg_p_norm, A.g.Vh, r, hh, b, ps);
+          SpinorIO<PR>::template load_block<COH>(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
+          SpinorIO<PR>::template load_block<COH>(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
+        }
 #pragma unroll
         for (int k = 0; k < 6; k++) {
           xs[k].re = fma(al, RR(ps[k].re), xs[k].re);
@@ -367,6 +444,7 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
   using R = typename Real<P>::T;
   constexpr bool KEEP_LINKS = MULTI && P != 64;
   __shared__ cx<R> part[4][12][32];
+  __shared__ uint4 stage[Stage<P, EPI>::U4];
   if (A.halt && *A.halt) return;
   int hh;
   bool valid;
@@ -381,7 +459,8 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
       act = A.red.cg[r].active != 0;
       al = A.red.cg[r].alpha;
     }
-    const double nrm = split_unit<P, RECON, EPI, KEEP_LINKS, false>(A, hh, valid, s, L, r, act, al, part);
+    const double nrm =
+        split_unit<P, RECON, EPI, KEEP_LINKS, LD_NC>(A, hh, valid, s, L, r, act, al, part, stage, r == 0);
     if (reduce) block_partial<128>(nrm, r, blockIdx.x, gridDim.x, A.red);
   }
   if (reduce) grid_finish<128>(A.nrhs, gridDim.x, gridDim.x, A.red);

@@ -123,11 +123,16 @@ struct Real<32> { using T = float; };
 template <>
 struct Real<16> { using T = float; };
 
-// Loads of spinor data: through the read-only path by default; COH = true reads through L2 only,
-// for data that other blocks of the same (persistent) kernel have written.
-template <bool COH, typename T>
+// Load modes of the field accessors: LD_NC through the read-only path (fields no block of the
+// kernel writes); LD_CG through L2 only; LD_CA an ordinary load cached in L1 and L2, for fields
+// that other blocks of the same (persistent) kernel wrote before a grid barrier whose GPU-scope
+// acquire makes their writes visible; LD_SM a plain load, for copies staged in shared memory.
+enum : int { LD_NC = 0, LD_CG = 1, LD_SM = 2, LD_CA = 3 };
+template <int LD, typename T>
 __device__ __forceinline__ T ldv(const T* p) {
-  if (COH) return __ldcg(p);
+  if (LD == LD_CG) return __ldcg(p);
+  if (LD == LD_CA) return __ldca(p);
+  if (LD == LD_SM) return *p;
   return __ldg(p);
 }
 
@@ -145,12 +150,12 @@ struct SpinorIO;
 template <>
 struct SpinorIO<64> {
   static constexpr int NVEC = 12;  // double2 per site
-  template <bool COH = false>
+  template <int LD = LD_NC>
   __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<double> s[12]) {
     const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 12; c++) {
-      double2 v = ldv<COH>(p + sidx<NVEC>(c, Vh, r, h));
+      double2 v = ldv<LD>(p + sidx<NVEC>(c, Vh, r, h));
       s[c] = cmk(v.x, v.y);
     }
   }
@@ -160,13 +165,13 @@ struct SpinorIO<64> {
     for (int c = 0; c < 12; c++) p[sidx<NVEC>(c, Vh, r, h)] = make_double2(s[c].re, s[c].im);
   }
   // components 6b..6b+5 (chiral block b: spins 2b, 2b+1)
-  template <bool COH = false>
+  template <int LD = LD_NC>
   __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b,
                                     cx<double> s[6]) {
     const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 6; c++) {
-      double2 v = ldv<COH>(p + sidx<NVEC>(6 * b + c, Vh, r, h));
+      double2 v = ldv<LD>(p + sidx<NVEC>(6 * b + c, Vh, r, h));
       s[c] = cmk(v.x, v.y);
     }
   }
@@ -181,12 +186,12 @@ struct SpinorIO<64> {
 template <>
 struct SpinorIO<32> {
   static constexpr int NVEC = 6;  // float4 per site
-  template <bool COH = false>
+  template <int LD = LD_NC>
   __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<float> s[12]) {
     const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 6; k++) {
-      float4 v = ldv<COH>(p + sidx<NVEC>(k, Vh, r, h));
+      float4 v = ldv<LD>(p + sidx<NVEC>(k, Vh, r, h));
       s[2 * k] = cmk(v.x, v.y);
       s[2 * k + 1] = cmk(v.z, v.w);
     }
@@ -197,13 +202,13 @@ struct SpinorIO<32> {
     for (int k = 0; k < 6; k++)
       p[sidx<NVEC>(k, Vh, r, h)] = make_float4(s[2 * k].re, s[2 * k].im, s[2 * k + 1].re, s[2 * k + 1].im);
   }
-  template <bool COH = false>
+  template <int LD = LD_NC>
   __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b,
                                     cx<float> s[6]) {
     const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      float4 v = ldv<COH>(p + sidx<NVEC>(3 * b + k, Vh, r, h));
+      float4 v = ldv<LD>(p + sidx<NVEC>(3 * b + k, Vh, r, h));
       s[2 * k] = cmk(v.x, v.y);
       s[2 * k + 1] = cmk(v.z, v.w);
     }
@@ -232,13 +237,13 @@ __device__ __forceinline__ uint32_t f2h(float a, float b) {
 template <>
 struct SpinorIO<16> {
   static constexpr int NVEC = 3;  // uint4 per site
-  template <bool COH = false>
+  template <int LD = LD_NC>
   __device__ static void load(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
     const uint4* p = static_cast<const uint4*>(base);
-    const float n = ldv<COH>(nrm + (size_t)r * Vh + h);
+    const float n = ldv<LD>(nrm + (size_t)r * Vh + h);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint4 v = ldv<COH>(p + sidx<NVEC>(k, Vh, r, h));
+      uint4 v = ldv<LD>(p + sidx<NVEC>(k, Vh, r, h));
       float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
       s[4 * k + 0] = cmk(a.x * n, a.y * n);
       s[4 * k + 1] = cmk(b.x * n, b.y * n);
@@ -247,19 +252,19 @@ struct SpinorIO<16> {
     }
   }
   // the stored values v / n without the per-site scale n, which is returned
-  template <bool COH = false>
+  template <int LD = LD_NC>
   __device__ static float load_unscaled(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
     const uint4* p = static_cast<const uint4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint4 v = ldv<COH>(p + sidx<NVEC>(k, Vh, r, h));
+      uint4 v = ldv<LD>(p + sidx<NVEC>(k, Vh, r, h));
       float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
       s[4 * k + 0] = cmk(a.x, a.y);
       s[4 * k + 1] = cmk(b.x, b.y);
       s[4 * k + 2] = cmk(c.x, c.y);
       s[4 * k + 3] = cmk(d.x, d.y);
     }
-    return ldv<COH>(nrm + (size_t)r * Vh + h);
+    return ldv<LD>(nrm + (size_t)r * Vh + h);
   }
   __device__ static void store(void* base, float* nrm, int Vh, int r, int h, const cx<float> s[12]) {
     float m = 0.f;
@@ -279,13 +284,13 @@ struct SpinorIO<16> {
     nrm[(size_t)r * Vh + h] = m;
   }
   // block 0 = chunk 0 and the first half of chunk 1; block 1 = the second half of chunk 1 and chunk 2
-  template <bool COH = false>
+  template <int LD = LD_NC>
   __device__ static void load_block(const void* base, const float* nrm, int Vh, int r, int h, int b,
                                     cx<float> s[6]) {
     const uint4* p = static_cast<const uint4*>(base);
-    const float n = ldv<COH>(nrm + (size_t)r * Vh + h);
-    const uint4 mid = ldv<COH>(p + sidx<NVEC>(1, Vh, r, h));
-    const uint4 end = ldv<COH>(p + sidx<NVEC>(b == 0 ? 0 : 2, Vh, r, h));
+    const float n = ldv<LD>(nrm + (size_t)r * Vh + h);
+    const uint4 mid = ldv<LD>(p + sidx<NVEC>(1, Vh, r, h));
+    const uint4 end = ldv<LD>(p + sidx<NVEC>(b == 0 ? 0 : 2, Vh, r, h));
     float2 e0 = h2f(end.x), e1 = h2f(end.y), e2 = h2f(end.z), e3 = h2f(end.w);
     if (b == 0) {
       float2 m0 = h2f(mid.x), m1 = h2f(mid.y);
@@ -413,19 +418,20 @@ __device__ __forceinline__ void hermitian6_accumulate(const R d[6], const cx<R> 
 template <>
 struct CloverIO<64> {
   static constexpr int NVEC = 36;  // double2 per site
+  template <int LD = LD_NC>
   __device__ static void apply(const void* c, int Vh, int h, int b, const cx<double> x[6], cx<double> y[6]) {
     const double2* q = static_cast<const double2*>(c) + (size_t)(b * 18) * Vh + h;
     double d[6];
     cx<double> L[15];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      double2 v = __ldg(q + (size_t)k * Vh);
+      double2 v = ldv<LD>(q + (size_t)k * Vh);
       d[2 * k] = v.x;
       d[2 * k + 1] = v.y;
     }
 #pragma unroll
     for (int k = 0; k < 15; k++) {
-      double2 v = __ldg(q + (size_t)(3 + k) * Vh);
+      double2 v = ldv<LD>(q + (size_t)(3 + k) * Vh);
       L[k] = cmk(v.x, v.y);
     }
     hermitian6_accumulate(d, L, x, y);
@@ -435,12 +441,13 @@ struct CloverIO<64> {
 template <>
 struct CloverIO<32> {
   static constexpr int NVEC = 18;  // float4 per site
+  template <int LD = LD_NC>
   __device__ static void apply(const void* c, int Vh, int h, int b, const cx<float> x[6], cx<float> y[6]) {
     const float4* q = static_cast<const float4*>(c) + (size_t)(b * 9) * Vh + h;
     float f[36];
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-      float4 v = __ldg(q + (size_t)k * Vh);
+      float4 v = ldv<LD>(q + (size_t)k * Vh);
       f[4 * k] = v.x;
       f[4 * k + 1] = v.y;
       f[4 * k + 2] = v.z;
@@ -461,13 +468,13 @@ template <>
 struct CloverIO<16> {
   static constexpr int NVEC = 9;  // uint4 per site
   // block B occupies halves [36B, 36B+36): uint4 4B .. 4B+4 (the middle uint4 is shared)
-  template <int B>
+  template <int B, int LD = LD_NC>
   __device__ static void apply_block(const void* c, int Vh, int h, const cx<float> x[6], cx<float> y[6]) {
     const uint4* q = static_cast<const uint4*>(c) + h;
     float f[40];
 #pragma unroll
     for (int k = 0; k < 5; k++) {
-      uint4 v = __ldg(q + (size_t)(4 * B + k) * Vh);
+      uint4 v = ldv<LD>(q + (size_t)(4 * B + k) * Vh);
       float2 a0 = h2f(v.x), a1 = h2f(v.y), a2 = h2f(v.z), a3 = h2f(v.w);
       f[8 * k + 0] = a0.x;
       f[8 * k + 1] = a0.y;
@@ -487,9 +494,10 @@ struct CloverIO<16> {
     for (int k = 0; k < 15; k++) L[k] = cmk(f[o + 6 + 2 * k], f[o + 7 + 2 * k]);
     hermitian6_accumulate(d, L, x, y);
   }
+  template <int LD = LD_NC>
   __device__ static void apply(const void* c, int Vh, int h, int b, const cx<float> x[6], cx<float> y[6]) {
-    if (b == 0) apply_block<0>(c, Vh, h, x, y);
-    else apply_block<1>(c, Vh, h, x, y);
+    if (b == 0) apply_block<0, LD>(c, Vh, h, x, y);
+    else apply_block<1, LD>(c, Vh, h, x, y);
   }
 };
 

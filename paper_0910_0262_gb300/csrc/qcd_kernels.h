@@ -24,13 +24,13 @@ struct PersistentCGArgs {
   CGControl* ctl;
   double *part_pap, *part_rr;  // one slot per block
   int slots;                   // slots in each; the grid never exceeds it
-  unsigned *bar_count, *bar_gen;
+  unsigned* bar_count;         // barrier arrivals, zeroed before the launch
   int* bar_err;                // set when a barrier wait gave up
   int max_iters;               // iterations this launch may run
 };
 cudaError_t launch_cg_persistent(int prec, int recon, const PersistentCGArgs& q, cudaStream_t st);
 // one grid barrier that a block never reaches (the wait must give up and set *err)
-cudaError_t launch_barrier_probe(unsigned* count, unsigned* gen, int* err, cudaStream_t st);
+cudaError_t launch_barrier_probe(unsigned* count, int* err, cudaStream_t st);
 
 // ---- layout (qcd_layout.cu)
 void launch_pack_gauge(const Geom& g, const double2* canon, void* g64, void* g32, int recon32, void* g16,
