@@ -213,6 +213,15 @@ qcd_status qcd_mhat_static(qcd_ctx* ctx, double* out, const double* in, int dagg
  */
 qcd_status qcd_selftest_barrier_timeout(qcd_ctx* ctx);
 
+/*
+ * Host-only self-test of the multiply-and-shift division by a lattice extent that the kernels use
+ * to turn a site index into coordinates (the same expression, evaluated on the host): checks every
+ * even extent 2..1024 against integer division on the numerators 0..65535, near each multiple of
+ * the extent up to 2^31 - 1, and on pseudo-random numerators.  Returns the number of mismatches
+ * (0 on success); needs no GPU and no context.
+ */
+long long qcd_selftest_fastdiv(void);
+
 /* Message describing the last failed call on this thread ("" if none). */
 const char* qcd_last_error(void);
 

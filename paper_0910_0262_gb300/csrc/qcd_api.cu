@@ -457,6 +457,9 @@ qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* strea
   c->g.XY = dims[0] * dims[1];
   c->g.XYZ = dims[0] * dims[1] * dims[2];
   c->g.t_bc = t_bc;
+  c->g.dX = make_fastdiv(dims[0]);
+  c->g.dY = make_fastdiv(dims[1]);
+  c->g.dZ = make_fastdiv(dims[2]);
   // partial sums of one reduction: nrhs x (blocks of the launch); the hopping kernel covers 32
   // (site, RHS) pairs per block, the fewest of all reducing kernels, so nrhs <= MAX_RHS needs
   // at most MAX_RHS * ceil(Vh * MAX_RHS / 32) slots
@@ -1244,6 +1247,33 @@ qcd_status qcd_selftest_barrier_timeout(qcd_ctx* c) {
   CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 4 * sizeof(unsigned), c->st));
   if (c->h_flags[2]) return fail(QCD_ERR_TIMEOUT, "grid barrier wait gave up as intended");
   return QCD_OK;
+}
+
+long long qcd_selftest_fastdiv(void) {
+  long long bad = 0;
+  unsigned long long state = 0x9E3779B97F4A7C15ULL;  // xorshift64 numerators
+  for (int d = 2; d <= 1024; d += 2) {
+    const FastDiv f = make_fastdiv(d);
+    auto check = [&](long long n) {
+      if (n < 0 || n > 0x7fffffffLL) return;
+      if (f.div((int)n) != (int)(n / d)) bad++;
+    };
+    for (long long n = 0; n < 65536; n++) check(n);
+    for (long long q = d; q <= 0x7fffffffLL; q = q * 3 + d) {
+      const long long m = q / d * d;
+      check(m - 1);
+      check(m);
+      check(m + d - 1);
+    }
+    check(0x7fffffffLL);
+    for (int k = 0; k < 4096; k++) {
+      state ^= state << 13;
+      state ^= state >> 7;
+      state ^= state << 17;
+      check((long long)(state & 0x7fffffffULL));
+    }
+  }
+  return bad;
 }
 
 qcd_status qcd_profile(qcd_ctx* c, int enable) {

@@ -112,9 +112,8 @@ __device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Rea
     int hh;
     bool valid;
     Site s;
-    DirLinks<R> L;
-    split_prologue<P, RECON, false>(A, sb, hh, valid, s, L);
-    v += split_unit<P, RECON, EPI, false, LDM>(A, hh, valid, s, L, 0, true, alpha, part, stage, true);
+    split_prologue(A, sb, hh, valid, s);
+    v += split_unit<P, RECON, EPI, LDM>(A, hh, valid, s, 0, true, alpha, part, stage, true);
   }
   return v;
 }

@@ -158,12 +158,7 @@ __global__ void __launch_bounds__(128) field_strength_kernel(Geom g, const doubl
   const int pl = (int)(tid / V), i = (int)(tid - (long long)pl * V);
   const int PM[6] = {0, 0, 0, 1, 1, 2}, PN[6] = {1, 2, 3, 2, 3, 3};
   int c[4];
-  c[0] = i % g.X;
-  int rest = i / g.X;
-  c[1] = rest % g.Y;
-  rest /= g.Y;
-  c[2] = rest % g.Z;
-  c[3] = rest / g.Z;
+  lattice_coords(g, i, c);
   const M3 F = field_strength(g, g64, c, PM[pl], PN[pl]);
   double2* q = Fbuf + (size_t)pl * 9 * V + i;
 #pragma unroll
@@ -180,12 +175,7 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const doub
   if (tid >= 2 * V) return;
   const int b = tid / V, i = tid - b * V;  // block b of lexicographic site i
   int c[4];
-  c[0] = i % g.X;
-  int rest = i / g.X;
-  c[1] = rest % g.Y;
-  rest /= g.Y;
-  c[2] = rest % g.Z;
-  c[3] = rest / g.Z;
+  lattice_coords(g, i, c);
   const int p = (c[0] + c[1] + c[2] + c[3]) & 1;
   const int h = i >> 1;
   auto Fe = [&](int pl, int e) {

@@ -140,16 +140,25 @@ struct DirLinks {
   R sf, sb;            // boundary factors of the two hops
 };
 
-template <int P, int RECON, int MU>
-__device__ __forceinline__ void load_dir(const DslashArgs& A, const Site& s, DirLinks<typename Real<P>::T>& L) {
-  using R = typename Real<P>::T;
-  const Geom& g = A.g;
+// neighbours and boundary factors along mu
+template <int MU, typename R>
+__device__ __forceinline__ void dir_index(const Geom& g, const Site& s, DirLinks<R>& L) {
   L.nbf = neighbor_fwd(g, s, MU) >> 1;
   L.nbb = neighbor_bwd(g, s, MU) >> 1;
-  GaugeIO<P, RECON>::load(A.gauge, g.Vh, A.p, MU, s.i >> 1, L.uf);
-  GaugeIO<P, RECON>::load(A.gauge, g.Vh, 1 - A.p, MU, L.nbb, L.ub);
   L.sf = (MU == 3 && s.t == g.T - 1) ? R(g.t_bc) : R(1);
   L.sb = (MU == 3 && s.t == 0) ? R(g.t_bc) : R(1);
+}
+
+template <int P, int RECON, int MU>
+__device__ __forceinline__ void dir_links(const DslashArgs& A, const Site& s, DirLinks<typename Real<P>::T>& L) {
+  GaugeIO<P, RECON>::load(A.gauge, A.g.Vh, A.p, MU, s.i >> 1, L.uf);
+  GaugeIO<P, RECON>::load(A.gauge, A.g.Vh, 1 - A.p, MU, L.nbb, L.ub);
+}
+
+template <int P, int RECON, int MU>
+__device__ __forceinline__ void load_dir(const DslashArgs& A, const Site& s, DirLinks<typename Real<P>::T>& L) {
+  dir_index<MU>(A.g, s, L);
+  dir_links<P, RECON, MU>(A, s, L);
 }
 
 // psi_r at half index nb; returns the factor still to be applied (the FP16 per-site scale, which
@@ -191,6 +200,14 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
     for (int k = 0; k < 6; k++) w[k] = f * w[k];
   }
   accumulate<MU, +1>(w, acc);
+}
+
+// The two hops along mu of one output site and RHS r, links loaded here.
+template <int P, int RECON, int MU, int COH>
+__device__ __forceinline__ void dir_unit(const DslashArgs& A, const Site& s, int r, cx<typename Real<P>::T> acc[12]) {
+  DirLinks<typename Real<P>::T> L;
+  load_dir<P, RECON, MU>(A, s, L);
+  hop_dir<P, MU, COH>(A, L, r, acc);
 }
 
 template <int P>
@@ -253,19 +270,18 @@ __device__ __forceinline__ void stage_spinor(uint4* dst, const void* base, const
 }
 
 // One (block of 32 output sites, RHS r) of the hopping operator on a 128-thread block: warp w
-// computes the two hops along mu = w for its lane's site (uniform per warp, no divergence), the
-// four partial sums meet in shared memory (part), warps 0 and 1 finish chiral block 0 and 1 (sum,
-// clover epilogue, gamma_5, norm or CG update) and the warps share the stores.  Links come from L
-// when KEEP_LINKS, else are loaded here.  COH is the load mode of the spinor fields (LD_NC, or a
-// coherent mode for a persistent kernel reading fields that other blocks wrote).  Returns the thread's share of |out|^2 (do_norm) or of
+// loads the two links along mu = w and computes the two hops for its lane's site (uniform per warp,
+// no divergence), the four partial sums meet in shared memory (part), warps 0 and 1 finish chiral
+// block 0 and 1 (sum, clover epilogue, gamma_5, norm or CG update) and the warps share the stores.
+// COH is the load mode of the spinor fields (LD_NC, or a coherent mode for a persistent kernel
+// reading fields that other blocks wrote).  Returns the thread's share of |out|^2 (do_norm) or of
 // |r|^2 (EPI_XPAY_CG, with cg_alpha applied when cg_active).  The epilogue's operands are staged in
 // stage (Stage<P, EPI>); the clover pair only when fetch_clover (it is kept from an earlier call on
 // the same sites otherwise).  All threads must call it; it synchronises the block and leaves part
 // and stage free for the next call.
-template <int P, int RECON, int EPI, bool KEEP_LINKS, int COH>
-__device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool valid, const Site& s,
-                                             DirLinks<typename Real<P>::T>& L, int r, bool cg_active,
-                                             double cg_alpha, cx<typename Real<P>::T> (*part)[12][32],
+template <int P, int RECON, int EPI, int COH>
+__device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool valid, const Site& s, int r,
+                                             bool cg_active, double cg_alpha, cx<typename Real<P>::T> (*part)[12][32],
                                              uint4* stage, bool fetch_clover) {
   using R = typename Real<P>::T;
   using ST = Stage<P, EPI>;
@@ -287,22 +303,10 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
     for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
     if (valid) {
       switch (w) {
-        case 0:
-          if (!KEEP_LINKS) load_dir<P, RECON, 0>(A, s, L);
-          hop_dir<P, 0, COH>(A, L, r, acc);
-          break;
-        case 1:
-          if (!KEEP_LINKS) load_dir<P, RECON, 1>(A, s, L);
-          hop_dir<P, 1, COH>(A, L, r, acc);
-          break;
-        case 2:
-          if (!KEEP_LINKS) load_dir<P, RECON, 2>(A, s, L);
-          hop_dir<P, 2, COH>(A, L, r, acc);
-          break;
-        default:
-          if (!KEEP_LINKS) load_dir<P, RECON, 3>(A, s, L);
-          hop_dir<P, 3, COH>(A, L, r, acc);
-          break;
+        case 0: dir_unit<P, RECON, 0, COH>(A, s, r, acc); break;
+        case 1: dir_unit<P, RECON, 1, COH>(A, s, r, acc); break;
+        case 2: dir_unit<P, RECON, 2, COH>(A, s, r, acc); break;
+        default: dir_unit<P, RECON, 3, COH>(A, s, r, acc); break;
       }
     }
 #pragma unroll
@@ -415,42 +419,25 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
   return nrm;
 }
 
-// Site and links of a lane in the block of 32 sites starting at 32 * sb.
-template <int P, int RECON, bool KEEP_LINKS>
-__device__ __forceinline__ void split_prologue(const DslashArgs& A, int sb, int& hh, bool& valid, Site& s,
-                                               DirLinks<typename Real<P>::T>& L) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  hh = sb * 32 + lane;
+// Site of a lane in the block of 32 sites starting at 32 * sb.
+__device__ __forceinline__ void split_prologue(const DslashArgs& A, int sb, int& hh, bool& valid, Site& s) {
+  hh = sb * 32 + (threadIdx.x & 31);
   valid = hh < A.g.Vh;
-  if (valid) {
-    s = site_of(A.g, A.p, hh);
-    if (KEEP_LINKS) {
-      switch (w) {
-        case 0: load_dir<P, RECON, 0>(A, s, L); break;
-        case 1: load_dir<P, RECON, 1>(A, s, L); break;
-        case 2: load_dir<P, RECON, 2>(A, s, L); break;
-        default: load_dir<P, RECON, 3>(A, s, L); break;
-      }
-    }
-  }
+  if (valid) s = site_of(A.g, A.p, hh);
 }
 
-// Hopping kernel: one block per 32 output sites, looping over the right-hand sides.  The links of
-// a site are loaded (and reconstructed) once and reused for every RHS in the multi-RHS
-// instantiations (MULTI); FP64 and the single-RHS instantiations reload them per RHS to keep the
-// register count low.
-template <int P, int RECON, int EPI, bool MULTI>
-__global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
+// Hopping kernel: one block per 32 output sites, looping over the right-hand sides (used for one
+// RHS, and for several in FP64).
+template <int P, int RECON, int EPI>
+__device__ __forceinline__ void dslash_split_body(const DslashArgs& A) {
   using R = typename Real<P>::T;
-  constexpr bool KEEP_LINKS = MULTI && P != 64;
   __shared__ cx<R> part[4][12][32];
   __shared__ uint4 stage[Stage<P, EPI>::U4];
   if (A.halt && *A.halt) return;
   int hh;
   bool valid;
   Site s;
-  DirLinks<R> L;
-  split_prologue<P, RECON, KEEP_LINKS>(A, blockIdx.x, hh, valid, s, L);
+  split_prologue(A, blockIdx.x, hh, valid, s);
   const bool reduce = A.do_norm || EPI == EPI_XPAY_CG;
   for (int r = 0; r < A.nrhs; r++) {
     bool act = false;
@@ -460,10 +447,147 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
       al = A.red.cg[r].alpha;
     }
     const double nrm =
-        split_unit<P, RECON, EPI, KEEP_LINKS, LD_NC>(A, hh, valid, s, L, r, act, al, part, stage, r == 0);
+        split_unit<P, RECON, EPI, LD_NC>(A, hh, valid, s, r, act, al, part, stage, r == 0);
     if (reduce) block_partial<128>(nrm, r, blockIdx.x, gridDim.x, A.red);
   }
   if (reduce) grid_finish<128>(A.nrhs, gridDim.x, gridDim.x, A.red);
+}
+
+template <int P, int RECON, int EPI>
+__global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
+  dslash_split_body<P, RECON, EPI>(A);
+}
+
+// Multi-RHS hopping kernel with one thread per (site, RHS).  A block of four warps covers 32 sites
+// (64 when nrhs = 2: two site groups of two warps); warp k of a site group takes RHS k, k + W, ...
+// (W warps per group), so the warps of a block share their sites' links and clover pair through L1
+// while each computes all eight hops and the epilogue of its own RHS, with no block barrier.
+// Sums are reduced per warp into the partial slot of (RHS, site group).
+template <int P, int RECON, int EPI>
+__global__ void __launch_bounds__(128) dslash_site_multi_kernel(DslashArgs A) {
+  using R = typename Real<P>::T;
+  constexpr int CP = CloverPrec<P>::CP;
+  constexpr int PR = P == 64 ? 64 : 32;
+  using RR = typename Real<PR>::T;
+  if (A.halt && *A.halt) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int G = A.nrhs == 2 ? 2 : 1, W = 4 / G;
+  const int grp = w / W, k = w - grp * W;
+  const int hh = (blockIdx.x * G + grp) * 32 + lane;
+  const bool valid = hh < A.g.Vh;
+  Site s;
+  if (valid) s = site_of(A.g, A.p, hh);
+  const bool reduce = A.do_norm || EPI == EPI_XPAY_CG;
+  const int Vh = A.g.Vh;
+  for (int r = k; r < A.nrhs; r += W) {
+    bool act = true;
+    double al = 0.0;
+    if (EPI == EPI_XPAY_CG) {
+      act = A.red.cg[r].active != 0;
+      al = A.red.cg[r].alpha;
+    }
+    double nrm = 0.0;
+    if (valid) {
+      cx<R> acc[12];
+#pragma unroll
+      for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
+      {
+        DirLinks<R> L;
+        load_dir<P, RECON, 0>(A, s, L);
+        hop_dir<P, 0, LD_NC>(A, L, r, acc);
+        load_dir<P, RECON, 1>(A, s, L);
+        hop_dir<P, 1, LD_NC>(A, L, r, acc);
+        load_dir<P, RECON, 2>(A, s, L);
+        hop_dir<P, 2, LD_NC>(A, L, r, acc);
+        load_dir<P, RECON, 3>(A, s, L);
+        hop_dir<P, 3, LD_NC>(A, L, r, acc);
+      }
+      cx<R> res[12];
+#pragma unroll
+      for (int b = 0; b < 2; b++) {
+        cx<R> v[6], o[6];
+#pragma unroll
+        for (int j = 0; j < 6; j++) v[j] = acc[6 * b + j];
+        if (EPI == EPI_NONE) {
+#pragma unroll
+          for (int j = 0; j < 6; j++) o[j] = v[j];
+        } else if (EPI == EPI_CLOVER_INV) {
+          CloverIO<CP>::apply(A.clover, Vh, hh, b, v, o);
+        } else {
+          cx<R> xs[6], cxs[6];
+          SpinorIO<P>::load_block(A.x, A.x_norm, Vh, r, hh, b, xs);
+          if (A.x_g5 && b == 1) {
+#pragma unroll
+            for (int j = 0; j < 6; j++) xs[j] = -xs[j];
+          }
+          CloverIO<CP>::apply(A.clover, Vh, hh, b, xs, cxs);
+          const R a = R(A.a);
+#pragma unroll
+          for (int j = 0; j < 6; j++) {
+            o[j].re = fma(a, v[j].re, cxs[j].re);
+            o[j].im = fma(a, v[j].im, cxs[j].im);
+          }
+        }
+        if (A.out_g5 && b == 1) {
+#pragma unroll
+          for (int j = 0; j < 6; j++) o[j] = -o[j];
+        }
+        if (EPI == EPI_XPAY_CG) {
+          if (act) {
+            const RR alr = RR(al);
+            cx<R> ps[6];
+            cx<RR> xs[6], rs[6];
+            SpinorIO<P>::load_block(A.cg_p, A.cg_p_norm, Vh, r, hh, b, ps);
+            SpinorIO<PR>::load_block(A.cg_x, nullptr, Vh, r, hh, b, xs);
+            SpinorIO<PR>::load_block(A.cg_r, nullptr, Vh, r, hh, b, rs);
+#pragma unroll
+            for (int j = 0; j < 6; j++) {
+              xs[j].re = fma(alr, RR(ps[j].re), xs[j].re);
+              xs[j].im = fma(alr, RR(ps[j].im), xs[j].im);
+              rs[j].re = fma(-alr, RR(o[j].re), rs[j].re);
+              rs[j].im = fma(-alr, RR(o[j].im), rs[j].im);
+              nrm += double(rs[j].re) * rs[j].re + double(rs[j].im) * rs[j].im;
+            }
+            SpinorIO<PR>::store_block(A.cg_x, nullptr, Vh, r, hh, b, xs);
+            SpinorIO<PR>::store_block(A.cg_r, nullptr, Vh, r, hh, b, rs);
+          }
+        } else {
+          if (A.do_norm) {
+#pragma unroll
+            for (int j = 0; j < 6; j++) nrm += double(o[j].re) * o[j].re + double(o[j].im) * o[j].im;
+          }
+#pragma unroll
+          for (int j = 0; j < 6; j++) res[6 * b + j] = o[j];
+        }
+      }
+      if (EPI != EPI_XPAY_CG) {
+        if (P == 16) {
+          cx<float> of[12];
+#pragma unroll
+          for (int c = 0; c < 12; c++) of[c] = cmk(float(res[c].re), float(res[c].im));
+          SpinorIO<16>::store(A.out, A.out_norm, Vh, r, hh, of);
+        } else {
+          SpinorIO<P>::store(A.out, A.out_norm, Vh, r, hh, res);
+        }
+      }
+    }
+    if (reduce) {
+      for (int off = 16; off >= 1; off >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, off);
+      if (lane == 0) {
+        const long long slot = (long long)r * (gridDim.x * G) + blockIdx.x * G + grp;
+        if (slot < A.red.capacity) A.red.partials[slot] = nrm;
+        else A.red.ctl->overflow = 1;
+      }
+    }
+  }
+  if (reduce) grid_finish<128>(A.nrhs, gridDim.x, gridDim.x * G, A.red);
+}
+
+// The single-RHS FP16 operator is bound by latency: it is held to 64 registers, so that 8 blocks
+// (32 warps) share an SM.
+template <int RECON, int EPI>
+__global__ void __launch_bounds__(128, 8) dslash_split_fp16_kernel(DslashArgs A) {
+  dslash_split_body<16, RECON, EPI>(A);
 }
 
 }  // namespace qcd

@@ -68,12 +68,7 @@ __device__ __forceinline__ M3 load_m3(const double2* buf, int plane, size_t V, i
 }
 
 __device__ __forceinline__ void lex_coords(const Geom& g, int i, int c[4]) {
-  c[0] = i % g.X;
-  int rest = i / g.X;
-  c[1] = rest % g.Y;
-  rest /= g.Y;
-  c[2] = rest % g.Z;
-  c[3] = rest / g.Z;
+  lattice_coords(g, i, c);
 }
 
 __device__ __forceinline__ int lex_index(const Geom& g, int x, int y, int z, int t) {

@@ -21,12 +21,50 @@
 
 namespace qcd {
 
+// Division by a lattice extent d >= 2, for 0 <= n < 2^31, as a multiply and a shift (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d)
+// and m = ceil(2^(31+l) / d) < 2^32, n / d = floor(n m / 2^(31+l)).  It is exact because
+// n (m d - 2^(31+l)) < 2^31 d <= 2^(31+l), so the excess of n m / 2^(31+l) over n / d stays below
+// 1 / d.  The host evaluates the same expression with a 64-bit product.
+struct FastDiv {
+  unsigned m;
+  int s;  // l - 1
+  __host__ __device__ __forceinline__ int div(int n) const {
+#ifdef __CUDA_ARCH__
+    return (int)(__umulhi((unsigned)n, m) >> s);
+#else
+    return (int)((((unsigned long long)(unsigned)n * m) >> 32) >> s);
+#endif
+  }
+};
+
+inline FastDiv make_fastdiv(int d) {
+  int l = 0;
+  while ((1LL << l) < d) l++;
+  FastDiv f;
+  f.s = l - 1;
+  f.m = (unsigned)(((1ULL << (31 + l)) + (unsigned long long)d - 1) / (unsigned long long)d);
+  return f;
+}
+
 struct Geom {
   int X, Y, Z, T;
-  int Vh;          // sites of one parity
-  int XY, XYZ;     // lexicographic strides
-  double t_bc;     // factor on U_t(x) at t = T-1 in the hopping term
+  int Vh;                // sites of one parity
+  int XY, XYZ;           // lexicographic strides
+  double t_bc;           // factor on U_t(x) at t = T-1 in the hopping term
+  FastDiv dX, dY, dZ;    // division by X, Y, Z
 };
+
+// (x, y, z, t) of the lexicographic index i = x + X (y + Y (z + Z t))
+__host__ __device__ __forceinline__ void lattice_coords(const Geom& g, int i, int c[4]) {
+  const int q1 = g.dX.div(i);
+  c[0] = i - q1 * g.X;
+  const int q2 = g.dY.div(q1);
+  c[1] = q1 - q2 * g.Y;
+  const int q3 = g.dZ.div(q2);
+  c[2] = q2 - q3 * g.Z;
+  c[3] = q3;
+}
 
 // ---------------------------------------------------------------- complex ----
 template <typename R>
@@ -83,14 +121,12 @@ struct Site {
 
 __device__ __forceinline__ Site site_of(const Geom& g, int p, int h) {
   Site s;
-  int i0 = 2 * h;
-  int rest = i0 / g.X;
-  int x0 = i0 - rest * g.X;
-  s.y = rest % g.Y;
-  rest /= g.Y;
-  s.z = rest % g.Z;
-  s.t = rest / g.Z;
-  s.x = x0 + ((p + s.y + s.z + s.t) & 1);
+  int c[4];
+  lattice_coords(g, 2 * h, c);
+  s.y = c[1];
+  s.z = c[2];
+  s.t = c[3];
+  s.x = c[0] + ((p + s.y + s.z + s.t) & 1);
   s.i = s.x + g.X * (s.y + g.Y * (s.z + g.Z * s.t));
   return s;
 }
@@ -251,20 +287,36 @@ struct SpinorIO<16> {
       s[4 * k + 3] = cmk(d.x * n, d.y * n);
     }
   }
-  // the stored values v / n without the per-site scale n, which is returned
+  // a site as stored (24 halves and the norm), so that loads can be issued well before the
+  // values are used
+  struct Raw {
+    uint4 v[3];
+    float n;
+  };
   template <int LD = LD_NC>
-  __device__ static float load_unscaled(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
+  __device__ static void load_raw(const void* base, const float* nrm, int Vh, int r, int h, Raw& q) {
     const uint4* p = static_cast<const uint4*>(base);
 #pragma unroll
+    for (int k = 0; k < 3; k++) q.v[k] = ldv<LD>(p + sidx<NVEC>(k, Vh, r, h));
+    q.n = ldv<LD>(nrm + (size_t)r * Vh + h);
+  }
+  // the stored values v / n without the per-site scale n, which is returned
+  __device__ static float unpack_unscaled(const Raw& q, cx<float> s[12]) {
+#pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint4 v = ldv<LD>(p + sidx<NVEC>(k, Vh, r, h));
-      float2 a = h2f(v.x), b = h2f(v.y), c = h2f(v.z), d = h2f(v.w);
+      float2 a = h2f(q.v[k].x), b = h2f(q.v[k].y), c = h2f(q.v[k].z), d = h2f(q.v[k].w);
       s[4 * k + 0] = cmk(a.x, a.y);
       s[4 * k + 1] = cmk(b.x, b.y);
       s[4 * k + 2] = cmk(c.x, c.y);
       s[4 * k + 3] = cmk(d.x, d.y);
     }
-    return ldv<LD>(nrm + (size_t)r * Vh + h);
+    return q.n;
+  }
+  template <int LD = LD_NC>
+  __device__ static float load_unscaled(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
+    Raw q;
+    load_raw<LD>(base, nrm, Vh, r, h, q);
+    return unpack_unscaled(q, s);
   }
   __device__ static void store(void* base, float* nrm, int Vh, int r, int h, const cx<float> s[12]) {
     float m = 0.f;

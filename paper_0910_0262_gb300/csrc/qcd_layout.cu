@@ -14,12 +14,12 @@ long long g_kernel_launches = 0;
 namespace {
 
 __device__ __forceinline__ void coords_of(const Geom& g, int i, int& x, int& y, int& z, int& t) {
-  x = i % g.X;
-  int rest = i / g.X;
-  y = rest % g.Y;
-  rest /= g.Y;
-  z = rest % g.Z;
-  t = rest / g.Z;
+  int c[4];
+  lattice_coords(g, i, c);
+  x = c[0];
+  y = c[1];
+  z = c[2];
+  t = c[3];
 }
 
 // canonical gauge U[i][mu][3][3] complex128 -> per-parity, per-direction SoA copies

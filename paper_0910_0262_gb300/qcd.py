@@ -70,6 +70,7 @@ _SIGNATURES = {
     "qcd_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(KernelStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "qcd_mhat_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "qcd_selftest_barrier_timeout": (ctypes.c_int, [_P]),
+    "qcd_selftest_fastdiv": (ctypes.c_longlong, []),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -155,6 +156,11 @@ def qcd_mhat_static(ctx, out_ptr, in_ptr, dagger=0):
 def qcd_selftest_barrier_timeout(ctx):
     """Returns the status of the barrier self-test (QCD_ERR_TIMEOUT = 8 when the wait gave up)."""
     return lib().qcd_selftest_barrier_timeout(ctx)
+
+
+def qcd_selftest_fastdiv():
+    """Mismatches of the kernels' division by a lattice extent against integer division (host only)."""
+    return lib().qcd_selftest_fastdiv()
 
 
 def qcd_last_error():

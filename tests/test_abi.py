@@ -63,3 +63,9 @@ def test_null_context_is_an_argument_error(libqcd):
     assert L.qcd_clover_build(None, 0.12, 1.0) == 1
     assert L.qcd_destroy(None) == 0
     assert "null" in qcd.qcd_last_error()
+
+
+def test_extent_division_matches_integer_division(libqcd):
+    """The kernels' multiply-and-shift division by X, Y, Z (host evaluation of the same expression)."""
+    libqcd.qcd_selftest_fastdiv.restype = ctypes.c_longlong
+    assert libqcd.qcd_selftest_fastdiv() == 0
