@@ -37,6 +37,11 @@ METRIC = "Dslash GFLOPS & HBM GB/s; time to 1e-8 CG solve, mixed vs FP64, 1 GB30
 # FP64 peak of GB300 derived from its unit counts and clock: 2 FP64 FMA / clock / SM x 152 SMs x 2.07 GHz
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 WORKLOAD = "c1_16^4"
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernel, with the summary
+# that holds the command; a kernel changed since its capture has no entry (traffic null)
+NCU_TRAFFIC = {
+    "cg_persistent_p32": (41.3e6, "profiles/cg_persistent_16x16x16x16.md"),
+}
 
 
 def parse():
@@ -299,14 +304,20 @@ def run_ours(args, world, rank, local):
     # roofline of the kernel with the largest device time per step
     dk = classes[dominant]
     if dominant == "dslash_p32" or dominant.startswith("cg_persistent_p32") or dominant.startswith("cg_persistent_p16"):
+        tr = NCU_TRAFFIC.get(dominant)
         result["roofline"] = {"kernel": dominant, "bound": "hbm", "achieved": dk["gbs"], "peak": hbm_peak,
-                              "unit": "GB/s", "frac": dk["gbs"] / hbm_peak, "traffic": None,
+                              "unit": "GB/s", "frac": dk["gbs"] / hbm_peak,
+                              "traffic": None if tr is None else tr[0],
+                              "algorithmic_bytes_per_launch": dk["bytes_per_launch"],
+                              "traffic_source": None if tr is None else tr[1],
                               "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
     else:
         fp64_peak = FP64_PEAK_TFLOPS * 1e3
+        tr = NCU_TRAFFIC.get(dominant)
         result["roofline"] = {"kernel": dominant, "bound": "alu", "achieved": dk["gflops"] / 1e3,
                               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": dk["gflops"] / fp64_peak,
-                              "traffic": None,
+                              "traffic": None if tr is None else tr[0],
+                              "traffic_source": None if tr is None else tr[1],
                               "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived; probe measured 1.19)"}
     result["roofline_dslash_fp32_in_solve"] = {"bound": "hbm", "achieved": d32["gbs"], "peak": hbm_peak,
                                                "unit": "GB/s", "frac": d32["gbs"] / hbm_peak,
@@ -479,9 +490,10 @@ def run_reference(args, world, rank):
             "e2e": {"value": v, "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-# CG iterations the 16^4 mixed solve takes (used to scale the oracle's per-iteration sample in the
-# reference arm, which has no GPU solve to count them)
-WORKLOAD_ITERS = 300
+# CG iterations the 16^4 solve to 1e-8 takes (58 for the FP64 and the mixed solve alike, as the
+# GPU runs of this workload report): scales the oracle's per-iteration sample in the reference arm,
+# which runs no GPU solve to count them
+WORKLOAD_ITERS = 58
 
 
 def run_dslash_only(args):
