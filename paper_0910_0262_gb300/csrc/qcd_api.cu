@@ -595,8 +595,9 @@ qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
   if ((s = ws_get(c, S_F_CL, force_clover_bytes(g), &work))) return s;
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->st));
   {
-    // 6 planes x 4 leaves x 3 products of 3x3 complex matrices per site, plus the two inversions
-    ProfScope ps(c, "clover_build", 0, 2.0 * g.Vh * (72 * 216.0 + 2 * 1000.0));
+    // 6 planes x 10 products of 3x3 complex matrices per site (two leaves share a product), plus
+    // the two inversions
+    ProfScope ps(c, "clover_build", 0, 2.0 * g.Vh * (60 * 216.0 + 2 * 1000.0));
     launch_clover_build(g, c->g64, kappa, csw, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, work,
                         c->flags, c->st);
   }

@@ -18,46 +18,49 @@ namespace qcd {
 
 namespace {
 
-// traceless part of (Q - Q^dag) / (8 i), with Q the four-leaf sum in the (mu, nu) plane
+// traceless part of (Q - Q^dag) / (8 i), with Q = L1 + L2 + L3 + L4 the four-leaf sum in the
+// (mu, nu) plane.  Only the anti-Hermitian part of Q is needed, and Q - Q^dag = M - M^dag with
+// M = (L1 - L4^dag) + (L2 - L3^dag), where L1 and L4^dag both start with U_mu(x) and L2 and L3^dag
+// both end with U_mu(x - mu):
+//   L1 - L4^dag = U_mu(x) [U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag - U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)]
+//   L2 - L3^dag = [U_nu(x) U_mu(x-mu+nu)^dag U_nu(x-mu)^dag - U_nu(x-nu)^dag U_mu(x-mu-nu)^dag U_nu(x-mu-nu)] U_mu(x-mu)
+// which takes 10 matrix products instead of the 12 of the four leaves.
 __device__ M3 field_strength(const Geom& g, const double2* g64, const int c[4], int mu, int nu) {
-  int xm[4] = {c[0], c[1], c[2], c[3]};
   auto at = [&](int dm, int dn, int dir) {
-    int q[4] = {xm[0], xm[1], xm[2], xm[3]};
+    int q[4] = {c[0], c[1], c[2], c[3]};
     q[mu] += dm;
     q[nu] += dn;
     return link_at(g, g64, q[0], q[1], q[2], q[3], dir);
   };
-  M3 Q;
-  // U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-  M3 l = mul_nd(mul_nd(mul(at(0, 0, mu), at(1, 0, nu)), at(0, 1, mu)), at(0, 0, nu));
-  Q = l;
-  // U_nu(x) U_mu(x-mu+nu)^dag U_nu(x-mu)^dag U_mu(x-mu)
-  l = mul(mul_nd(mul_nd(at(0, 0, nu), at(-1, 1, mu)), at(-1, 0, nu)), at(-1, 0, mu));
-#pragma unroll
-  for (int k = 0; k < 9; k++) Q.e[k] = Q.e[k] + l.e[k];
-  // U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
-  M3 t1 = at(-1, 0, mu), t2 = at(-1, -1, nu);
-  M3 a;  // t1^dag t2^dag = (t2 t1)^dag
+  M3 M;
   {
-    M3 b = mul(t2, t1);
+    // U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+    const M3 A = mul_nd(mul_nd(at(1, 0, nu), at(0, 1, mu)), at(0, 0, nu));
+    // U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) = (U_mu(x-nu) U_nu(x+mu-nu))^dag U_nu(x-nu)
+    const M3 B = mul_dn(mul(at(0, -1, mu), at(1, -1, nu)), at(0, -1, nu));
+    M3 D;
 #pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-      for (int j = 0; j < 3; j++) a.e[3 * i + j] = conj(b.e[3 * j + i]);
+    for (int k = 0; k < 9; k++) D.e[k] = A.e[k] - B.e[k];
+    M = mul(at(0, 0, mu), D);
   }
-  l = mul(mul(a, at(-1, -1, mu)), at(0, -1, nu));
+  {
+    // U_nu(x) U_mu(x-mu+nu)^dag U_nu(x-mu)^dag
+    const M3 A = mul_nd(mul_nd(at(0, 0, nu), at(-1, 1, mu)), at(-1, 0, nu));
+    // U_nu(x-nu)^dag U_mu(x-mu-nu)^dag U_nu(x-mu-nu) = (U_mu(x-mu-nu) U_nu(x-nu))^dag U_nu(x-mu-nu)
+    const M3 B = mul_dn(mul(at(-1, -1, mu), at(0, -1, nu)), at(-1, -1, nu));
+    M3 D;
 #pragma unroll
-  for (int k = 0; k < 9; k++) Q.e[k] = Q.e[k] + l.e[k];
-  // U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^dag
-  l = mul_nd(mul(mul_dn(at(0, -1, nu), at(0, -1, mu)), at(1, -1, nu)), at(0, 0, mu));
+    for (int k = 0; k < 9; k++) D.e[k] = A.e[k] - B.e[k];
+    const M3 M2 = mul(D, at(-1, 0, mu));
 #pragma unroll
-  for (int k = 0; k < 9; k++) Q.e[k] = Q.e[k] + l.e[k];
+    for (int k = 0; k < 9; k++) M.e[k] = M.e[k] + M2.e[k];
+  }
   M3 F;
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-      C d = Q.e[3 * i + j] - conj(Q.e[3 * j + i]);
+      C d = M.e[3 * i + j] - conj(M.e[3 * j + i]);
       F.e[3 * i + j] = cmk(d.im * 0.125, -d.re * 0.125);  // d / (8 i)
     }
   const double tr = (F.e[0].re + F.e[4].re + F.e[8].re) / 3.0;
@@ -81,28 +84,29 @@ __device__ bool invert6(const double d[6], const C L[15], double di[6], C Li[15]
     }
   }
   C l[6][6];
-  double ld[6];
+  double ild[6];  // 1 / L_jj: one division per pivot, multiplications elsewhere
   for (int j = 0; j < 6; j++) {
     double s = a[j][j].re;
     for (int k = 0; k < j; k++) s -= norm2(l[j][k]);
     if (!(s > 0.0)) return false;
-    ld[j] = sqrt(s);
-    l[j][j] = cmk(ld[j], 0.0);
+    const double ld = sqrt(s);
+    ild[j] = 1.0 / ld;
+    l[j][j] = cmk(ld, 0.0);
     for (int i = j + 1; i < 6; i++) {
       C v = a[i][j];
       for (int k = 0; k < j; k++) v = v - l[i][k] * conj(l[j][k]);
-      l[i][j] = cmk(v.re / ld[j], v.im / ld[j]);
+      l[i][j] = cmk(v.re * ild[j], v.im * ild[j]);
     }
   }
   // m = L^-1 (lower triangular)
   C m[6][6];
   for (int j = 0; j < 6; j++) {
     for (int i = 0; i < j; i++) m[i][j] = cmk(0.0, 0.0);
-    m[j][j] = cmk(1.0 / ld[j], 0.0);
+    m[j][j] = cmk(ild[j], 0.0);
     for (int i = j + 1; i < 6; i++) {
       C s = cmk(0.0, 0.0);
       for (int k = j; k < i; k++) s = s + l[i][k] * m[k][j];
-      m[i][j] = cmk(-s.re / ld[i], -s.im / ld[i]);
+      m[i][j] = cmk(-s.re * ild[i], -s.im * ild[i]);
     }
   }
   // A^-1 = m^dag m
@@ -220,70 +224,13 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const doub
   if (Ainv16) store_block16(Ainv16 + (size_t)p * 9 * g.Vh, g.Vh, h, b, di, Li);
 }
 
-__global__ void __launch_bounds__(128) clover_build_kernel(Geom g, const double2* __restrict__ g64, double kappa,
-                                                           double csw, double2* A64, double2* Ainv64, float4* A32,
-                                                           float4* Ainv32, uint4* A16, uint4* Ainv16,
-                                                           int* notposdef) {
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= 2 * g.Vh) return;
-  const int p = tid / g.Vh, h = tid - p * g.Vh;
-  const Site s = site_of(g, p, h);
-  const int c[4] = {s.x, s.y, s.z, s.t};
-  // F_{mu nu} for the six planes: xy xz xt yz yt zt
-  M3 F[6];
-  int k = 0;
-  for (int mu = 0; mu < 4; mu++)
-    for (int nu = mu + 1; nu < 4; nu++) F[k++] = field_strength(g, g64, c, mu, nu);
-  const M3 &Fxy = F[0], &Fxz = F[1], &Fxt = F[2], &Fyz = F[3], &Fyt = F[4], &Fzt = F[5];
-  const double kc = kappa * csw;
-  for (int b = 0; b < 2; b++) {
-    const double sg = b == 0 ? -1.0 : 1.0;
-    C B1[9], B2[9], B3[9];
-    for (int e = 0; e < 9; e++) {
-      B1[e] = Fyz.e[e] + sg * Fxt.e[e];
-      B2[e] = Fxz.e[e] - sg * Fyt.e[e];
-      B3[e] = Fxy.e[e] + sg * Fzt.e[e];
-    }
-    // H = [[B3, B1 - i B2], [B1 + i B2, -B3]], A_b = 1 - kc H
-    double d[6];
-    C L[15];
-    for (int i = 0; i < 6; i++) {
-      const int ii = i % 3;
-      d[i] = 1.0 - kc * (i < 3 ? B3[4 * ii].re : -B3[4 * ii].re);
-      for (int j = 0; j < i; j++) {
-        const int jj = j % 3;
-        C hv;
-        if (i < 3) hv = B3[3 * ii + jj];
-        else if (j < 3) hv = B1[3 * ii + jj] + times_i(B2[3 * ii + jj]);
-        else hv = -B3[3 * ii + jj];
-        L[tri(i, j)] = cmk(-kc * hv.re, -kc * hv.im);
-      }
-    }
-    double di[6];
-    C Li[15];
-    if (!invert6(d, L, di, Li)) {
-      *notposdef = 1;
-      for (int i = 0; i < 6; i++) di[i] = 0.0;
-      for (int i = 0; i < 15; i++) Li[i] = cmk(0.0, 0.0);
-    }
-    double2* A64p = A64 + (size_t)p * 36 * g.Vh;
-    double2* I64p = Ainv64 + (size_t)p * 36 * g.Vh;
-    store_block64(A64p, g.Vh, h, b, d, L);
-    store_block64(I64p, g.Vh, h, b, di, Li);
-    if (A32) store_block32(A32 + (size_t)p * 18 * g.Vh, g.Vh, h, b, d, L);
-    if (Ainv32) store_block32(Ainv32 + (size_t)p * 18 * g.Vh, g.Vh, h, b, di, Li);
-    if (A16) store_block16(A16 + (size_t)p * 9 * g.Vh, g.Vh, h, b, d, L);
-    if (Ainv16) store_block16(Ainv16 + (size_t)p * 9 * g.Vh, g.Vh, h, b, di, Li);
-  }
-}
-
 template <int P>
 __global__ void clover_apply_kernel(Geom g, const void* clov, const void* in, const float* in_norm, void* out,
                                     float* out_norm, int nrhs) {
   using R = typename Real<P>::T;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= g.Vh * nrhs) return;
-  const int r = tid % nrhs, h = tid / nrhs;
+  const int r = tid / g.Vh, h = tid - r * g.Vh;  // consecutive threads: consecutive sites of one RHS
   cx<R> s[12], o[12];
   SpinorIO<P>::load(in, in_norm, g.Vh, r, h, s);
   constexpr int CP = P;
@@ -298,23 +245,14 @@ void launch_clover_build(const Geom& g, const void* g64, double kappa, double cs
                          void* Ainv32, void* A16, void* Ainv16, void* work, int* notposdef, cudaStream_t st) {
   const int B = 128;
   const long long V = 2LL * g.Vh;
-  if (work) {
-    // F per (site, plane), then one chiral block per thread
-    g_kernel_launches += 2;
-    field_strength_kernel<<<(int)((6 * V + B - 1) / B), B, 0, st>>>(g, static_cast<const double2*>(g64),
-                                                                      static_cast<double2*>(work));
-    clover_assemble_kernel<<<(int)((2 * V + B - 1) / B), B, 0, st>>>(
-        g, static_cast<const double2*>(work), kappa, csw, static_cast<double2*>(A64), static_cast<double2*>(Ainv64),
-        static_cast<float4*>(A32), static_cast<float4*>(Ainv32), static_cast<uint4*>(A16),
-        static_cast<uint4*>(Ainv16), notposdef);
-    return;
-  }
-  g_kernel_launches += 1;
-  const int nb = (2 * g.Vh + B - 1) / B;
-  clover_build_kernel<<<nb, B, 0, st>>>(g, static_cast<const double2*>(g64), kappa, csw, static_cast<double2*>(A64),
-                                        static_cast<double2*>(Ainv64), static_cast<float4*>(A32),
-                                        static_cast<float4*>(Ainv32), static_cast<uint4*>(A16),
-                                        static_cast<uint4*>(Ainv16), notposdef);
+  // F per (site, plane), then one chiral block per thread
+  g_kernel_launches += 2;
+  field_strength_kernel<<<(int)((6 * V + B - 1) / B), B, 0, st>>>(g, static_cast<const double2*>(g64),
+                                                                    static_cast<double2*>(work));
+  clover_assemble_kernel<<<(int)((2 * V + B - 1) / B), B, 0, st>>>(
+      g, static_cast<const double2*>(work), kappa, csw, static_cast<double2*>(A64), static_cast<double2*>(Ainv64),
+      static_cast<float4*>(A32), static_cast<float4*>(Ainv32), static_cast<uint4*>(A16), static_cast<uint4*>(Ainv16),
+      notposdef);
 }
 
 void launch_clover_apply(int prec, const Geom& g, const void* clover, const void* in, const float* in_norm, void* out,

@@ -70,26 +70,37 @@ __device__ __forceinline__ void project(const cx<R> s[12], cx<R> h[6]) {
   }
 }
 
-// Expand the multiplied half spinor back to four spins and accumulate.
-template <int MU, int SGN, typename R>
+// Expand the multiplied half spinor back to four spins and accumulate (FIRST: the first term of
+// the sum, stored instead of added to a zero accumulator, which would cost an add per component).
+template <int MU, int SGN, bool FIRST = false, typename R>
 __device__ __forceinline__ void accumulate(const cx<R> h[6], cx<R> acc[12]) {
 #pragma unroll
   for (int a = 0; a < 3; a++) {
     const cx<R> h0 = h[a], h1 = h[3 + a];
-    acc[a] = acc[a] + h0;
-    acc[3 + a] = acc[3 + a] + h1;
+    cx<R> lo, hi;  // the terms of spin rows 2 and 3
     if (MU == 0) {
-      acc[6 + a] = acc[6 + a] + (SGN < 0 ? times_i(h1) : times_mi(h1));
-      acc[9 + a] = acc[9 + a] + (SGN < 0 ? times_i(h0) : times_mi(h0));
+      lo = SGN < 0 ? times_i(h1) : times_mi(h1);
+      hi = SGN < 0 ? times_i(h0) : times_mi(h0);
     } else if (MU == 1) {
-      acc[6 + a] = SGN < 0 ? acc[6 + a] - h1 : acc[6 + a] + h1;
-      acc[9 + a] = SGN < 0 ? acc[9 + a] + h0 : acc[9 + a] - h0;
+      lo = SGN < 0 ? -h1 : h1;
+      hi = SGN < 0 ? h0 : -h0;
     } else if (MU == 2) {
-      acc[6 + a] = acc[6 + a] + (SGN < 0 ? times_i(h0) : times_mi(h0));
-      acc[9 + a] = acc[9 + a] + (SGN < 0 ? times_mi(h1) : times_i(h1));
+      lo = SGN < 0 ? times_i(h0) : times_mi(h0);
+      hi = SGN < 0 ? times_mi(h1) : times_i(h1);
     } else {
-      acc[6 + a] = SGN < 0 ? acc[6 + a] - h0 : acc[6 + a] + h0;
-      acc[9 + a] = SGN < 0 ? acc[9 + a] - h1 : acc[9 + a] + h1;
+      lo = SGN < 0 ? -h0 : h0;
+      hi = SGN < 0 ? -h1 : h1;
+    }
+    if (FIRST) {
+      acc[a] = h0;
+      acc[3 + a] = h1;
+      acc[6 + a] = lo;
+      acc[9 + a] = hi;
+    } else {
+      acc[a] = acc[a] + h0;
+      acc[3 + a] = acc[3 + a] + h1;
+      acc[6 + a] = acc[6 + a] + lo;
+      acc[9 + a] = acc[9 + a] + hi;
     }
   }
 }
@@ -174,8 +185,8 @@ __device__ __forceinline__ typename Real<P>::T load_neighbor(const DslashArgs& A
   return R(1);
 }
 
-// acc += (1 - g_mu) U_mu(x) psi_r(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi_r(x-mu)
-template <int P, int MU, int COH = LD_NC>
+// acc += (1 - g_mu) U_mu(x) psi_r(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi_r(x-mu)  (FIRST: acc =)
+template <int P, int MU, int COH = LD_NC, bool FIRST = false>
 __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<typename Real<P>::T>& L, int r,
                                         cx<typename Real<P>::T> acc[12]) {
   using R = typename Real<P>::T;
@@ -189,7 +200,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
 #pragma unroll
     for (int k = 0; k < 6; k++) w[k] = f * w[k];
   }
-  accumulate<MU, -1>(w, acc);
+  accumulate<MU, -1, FIRST>(w, acc);
   f = load_neighbor<P, COH>(A, r, L.nbb, sp);
   if (A.in_g5) apply_g5(sp);
   project<MU, +1>(sp, h);
@@ -202,12 +213,12 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
   accumulate<MU, +1>(w, acc);
 }
 
-// The two hops along mu of one output site and RHS r, links loaded here.
+// acc = the two hops along mu of one output site and RHS r, links loaded here.
 template <int P, int RECON, int MU, int COH>
 __device__ __forceinline__ void dir_unit(const DslashArgs& A, const Site& s, int r, cx<typename Real<P>::T> acc[12]) {
   DirLinks<typename Real<P>::T> L;
   load_dir<P, RECON, MU>(A, s, L);
-  hop_dir<P, MU, COH>(A, L, r, acc);
+  hop_dir<P, MU, COH, true>(A, L, r, acc);
 }
 
 template <int P>
@@ -299,8 +310,6 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
   }
   {
     cx<R> acc[12];
-#pragma unroll
-    for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
     if (valid) {
       switch (w) {
         case 0: dir_unit<P, RECON, 0, COH>(A, s, r, acc); break;
@@ -308,6 +317,9 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
         case 2: dir_unit<P, RECON, 2, COH>(A, s, r, acc); break;
         default: dir_unit<P, RECON, 3, COH>(A, s, r, acc); break;
       }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
     }
 #pragma unroll
     for (int c = 0; c < 12; c++) part[w][c][lane] = acc[c];
@@ -489,12 +501,10 @@ __global__ void __launch_bounds__(128) dslash_site_multi_kernel(DslashArgs A) {
     double nrm = 0.0;
     if (valid) {
       cx<R> acc[12];
-#pragma unroll
-      for (int c = 0; c < 12; c++) acc[c] = cmk(R(0), R(0));
       {
         DirLinks<R> L;
         load_dir<P, RECON, 0>(A, s, L);
-        hop_dir<P, 0, LD_NC>(A, L, r, acc);
+        hop_dir<P, 0, LD_NC, true>(A, L, r, acc);
         load_dir<P, RECON, 1>(A, s, L);
         hop_dir<P, 1, LD_NC>(A, L, r, acc);
         load_dir<P, RECON, 2>(A, s, L);

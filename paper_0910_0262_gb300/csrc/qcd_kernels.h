@@ -44,7 +44,7 @@ void launch_check_finite(const double* data, size_t n, int* flag, cudaStream_t s
 // ---- clover (qcd_clover.cu)
 // A (both parities) and A^-1 (both parities) in FP64, FP32 and FP16; flag set if a block is not positive definite.
 // work: 6 * 9 * V double2 for the field strengths (two kernels: F per site and plane, then one chiral
-// block per thread); null: a single kernel with one site per thread.
+// block per thread).
 void launch_clover_build(const Geom& g, const void* g64, double kappa, double csw, void* A64, void* Ainv64,
                          void* A32, void* Ainv32, void* A16, void* Ainv16, void* work, int* notposdef,
                          cudaStream_t st);
