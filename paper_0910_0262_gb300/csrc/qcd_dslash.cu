@@ -30,25 +30,34 @@ void launch_split_fp16(int epi, const DslashArgs& a, cudaStream_t st) {
 }
 
 template <int P, int RECON>
-void launch_site_multi(int epi, const DslashArgs& a, cudaStream_t st) {
-  const int G = a.nrhs == 2 ? 2 : 1;
+void launch_site(int epi, const DslashArgs& a, cudaStream_t st) {
+  const int G = a.nrhs == 1 ? 4 : (a.nrhs == 2 ? 2 : 1);
   const int nb = (a.g.Vh + 32 * G - 1) / (32 * G);
   switch (epi) {
-    case EPI_NONE: dslash_site_multi_kernel<P, RECON, EPI_NONE><<<nb, 128, 0, st>>>(a); break;
-    case EPI_CLOVER_INV: dslash_site_multi_kernel<P, RECON, EPI_CLOVER_INV><<<nb, 128, 0, st>>>(a); break;
-    case EPI_XPAY_CG: dslash_site_multi_kernel<P, RECON, EPI_XPAY_CG><<<nb, 128, 0, st>>>(a); break;
-    default: dslash_site_multi_kernel<P, RECON, EPI_XPAY><<<nb, 128, 0, st>>>(a); break;
+    case EPI_NONE: dslash_site_kernel<P, RECON, EPI_NONE><<<nb, 128, 0, st>>>(a); break;
+    case EPI_CLOVER_INV: dslash_site_kernel<P, RECON, EPI_CLOVER_INV><<<nb, 128, 0, st>>>(a); break;
+    case EPI_XPAY_CG: dslash_site_kernel<P, RECON, EPI_XPAY_CG><<<nb, 128, 0, st>>>(a); break;
+    default: dslash_site_kernel<P, RECON, EPI_XPAY><<<nb, 128, 0, st>>>(a); break;
   }
 }
 
-// one RHS: the direction-split kernel (four threads per site); several RHS in FP32/FP16: one thread
-// per (site, RHS); FP64 (bound by the FP64 pipe): the split kernel for any number of RHS
+// Half volume from which one RHS runs one thread per site: below it the four threads per site of
+// the direction-split kernel are needed to fill the GPU (16^4: 32768 sites per parity would give
+// 256 blocks), above it the site kernel's lower instruction count and absence of block barriers win
+// (32^3 x 64: FP16 147 -> 116 us, FP32 170 -> 164 us per hopping launch).
+#ifndef QCD_SITE_KERNEL_MIN_VH
+#define QCD_SITE_KERNEL_MIN_VH (1 << 17)
+#endif
+const int SITE_KERNEL_MIN_VH = QCD_SITE_KERNEL_MIN_VH;
+
+// FP32/FP16: one thread per (site, RHS) for several RHS or large lattices, else the direction-split
+// kernel; FP64 (bound by the FP64 pipe): the split kernel for any number of RHS
 template <int P, int RECON>
 void launch_prec(int epi, const DslashArgs& a, cudaStream_t st) {
   if constexpr (P == 64) {
     launch_split<P, RECON>(epi, a, st);
   } else {
-    if (a.nrhs > 1) launch_site_multi<P, RECON>(epi, a, st);
+    if (a.nrhs > 1 || a.g.Vh >= SITE_KERNEL_MIN_VH) launch_site<P, RECON>(epi, a, st);
     else if constexpr (P == 16) launch_split_fp16<RECON>(epi, a, st);
     else launch_split<P, RECON>(epi, a, st);
   }

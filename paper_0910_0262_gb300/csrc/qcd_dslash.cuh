@@ -470,20 +470,21 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
   dslash_split_body<P, RECON, EPI>(A);
 }
 
-// Multi-RHS hopping kernel with one thread per (site, RHS).  A block of four warps covers 32 sites
-// (64 when nrhs = 2: two site groups of two warps); warp k of a site group takes RHS k, k + W, ...
-// (W warps per group), so the warps of a block share their sites' links and clover pair through L1
-// while each computes all eight hops and the epilogue of its own RHS, with no block barrier.
-// Sums are reduced per warp into the partial slot of (RHS, site group).
+// Hopping kernel with one thread per (site, RHS).  A block of four warps covers 32 sites (64 when
+// nrhs = 2: two site groups of two warps; 128 when nrhs = 1: four groups of one warp); warp k of a
+// site group takes RHS k, k + W, ... (W warps per group), so the warps of a block share their
+// sites' links and clover pair through L1 while each computes all eight hops and the epilogue of
+// its own RHS, with no block barrier.  Sums are reduced per warp into the partial slot of (RHS,
+// site group).
 template <int P, int RECON, int EPI>
-__global__ void __launch_bounds__(128) dslash_site_multi_kernel(DslashArgs A) {
+__global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
   using R = typename Real<P>::T;
   constexpr int CP = CloverPrec<P>::CP;
   constexpr int PR = P == 64 ? 64 : 32;
   using RR = typename Real<PR>::T;
   if (A.halt && *A.halt) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int G = A.nrhs == 2 ? 2 : 1, W = 4 / G;
+  const int G = A.nrhs == 1 ? 4 : (A.nrhs == 2 ? 2 : 1), W = 4 / G;
   const int grp = w / W, k = w - grp * W;
   const int hh = (blockIdx.x * G + grp) * 32 + lane;
   const bool valid = hh < A.g.Vh;

@@ -10,6 +10,7 @@
     2 Re<phi, X> - |Mhat X|^2, so that FP64 rounding of S does not swamp the O(eps) change).
 32^3 x 64 (eps 0.15, seed 4, 8 RHS):
   * the FP64 Mhat at sampled even sites against the single-site oracle;
+  * Mhat and Mhat^dag in FP32 and FP16, for 1 and 8 RHS, at sampled even sites likewise;
   * one batched mixed-precision solve of all 8 RHS with FP16 inner iterations: every RHS
     reaches a true residual <= 1e-8 (recomputed with the FP64 operator checked above).
 """
@@ -178,6 +179,35 @@ def test_c3_fp64_operator_at_sampled_sites(c3):
         dend += np.sum(np.abs(wantd) ** 2)
     assert np.sqrt(num / den) <= 1e-13
     assert np.sqrt(numd / dend) <= 1e-13
+
+
+@pytest.mark.parametrize("prec,tol", [(32, 1e-6), (16, 5e-3)])
+@pytest.mark.parametrize("nrhs", [1, 8])
+def test_c3_inner_precision_operator_at_sampled_sites(c3, prec, tol, nrhs):
+    """Mhat and Mhat^dag in FP32 / FP16 on the 32^3 x 64 lattice (one thread per (site, RHS)
+    kernel, for 1 and for 8 RHS) against the single-site FP64 oracle, RHS 0, 3 and 7."""
+    from paper_0910_0262_gb300 import qcd as Q
+    w, U, b, op = c3
+    dims = w["dims"]
+    src = to_dev(b[:nrhs])
+    out = to_np(op.dslash(src, Q.QCD_OP_MHAT, precision=prec))
+    outd = to_np(op.dslash(src, Q.QCD_OP_MHAT, dagger=True, precision=prec))
+    rng = np.random.default_rng(7)
+    Vh = b.shape[1]
+    hs = list(rng.integers(0, Vh, 6)) + [0, Vh - 1]
+    for r in [r for r in (0, 3, 7) if r < nrhs]:
+        num = den = numd = dend = 0.0
+        for h in hs:
+            i = next(i for i in (2 * int(h), 2 * int(h) + 1) if sum(local.coords(dims, i)) % 2 == 0)
+            c = local.coords(dims, i)
+            want = local.mhat_site(U, b[r], dims, c, KAPPA, CSW, TBC)
+            wantd = local.mhat_site(U, b[r], dims, c, KAPPA, CSW, TBC, dagger_op=True)
+            num += np.sum(np.abs(out[r, int(h)] - want) ** 2)
+            den += np.sum(np.abs(want) ** 2)
+            numd += np.sum(np.abs(outd[r, int(h)] - wantd) ** 2)
+            dend += np.sum(np.abs(wantd) ** 2)
+        assert np.sqrt(num / den) <= tol, (prec, nrhs, r, np.sqrt(num / den))
+        assert np.sqrt(numd / dend) <= tol, (prec, nrhs, r, np.sqrt(numd / dend))
 
 
 def test_c3_batched_fp16_solve(c3):

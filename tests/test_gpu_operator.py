@@ -3,8 +3,9 @@
 Every op of qcd_dslash (D_eo, D_oe and their adjoints, Mhat, Mhat^dag,
 Mhat^dag Mhat, A_ee, A_oo^-1) in FP64, FP32 and FP16, with 18- and 12-real link
 storage, on lattices whose half volume leaves a ragged last thread block
-(432 and 96 sites per parity; blocks of 128) and with 3 right-hand sides (a
-batch of 2 plus a batch of 1).
+(432 and 96 sites per parity: the 32-site blocks of the single-RHS kernels end
+ragged at 432, the 64-site blocks of the 2-RHS kernel at 96), with 3
+right-hand sides (a batch of 2 plus a batch of 1) and with 13 (8 + 4 + 1).
 
 Tolerances (relative L2 per field): FP64 1e-13 and FP32 1e-6 (the targets of
 the method's statement); FP16 with per-site norms is stated, gated at 5e-3.
@@ -84,3 +85,20 @@ def test_fp64_is_linear_and_gamma5_hermitian_on_gpu(lattice):
     lhs = np.vdot(b, Ma)
     rhs = np.vdot(Mdb, a)
     assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+BATCH_OPS = [o for o in OPS if o[0] in ("DSLASH_EO", "MHAT", "MDAGM", "CLOVER_INV")]
+
+
+@pytest.mark.parametrize("prec,recon", [(64, 18), (32, 12), (32, 18), (16, 12)])
+@pytest.mark.parametrize("name,op,dagger", BATCH_OPS, ids=[f"{o[0]}{'_dag' if o[2] else ''}" for o in BATCH_OPS])
+def test_operator_parity_rhs_batches(lattice, prec, recon, name, op, dagger):
+    """13 right-hand sides: batches of 8, 4 and 1 (the multi-RHS kernel with two RHS per warp, with
+    one, and the single-RHS kernel), each RHS against the oracle."""
+    dims, U, ref, ctxs, fields = lattice
+    rng = np.random.default_rng(17)
+    many = rand_eo(13, fields.shape[1], rng)
+    out = to_np(ctxs[recon].dslash(to_dev(many), op, dagger=bool(dagger), precision=prec))
+    for r in range(13):
+        err = rel_l2(out[r], expected(ref, op, dagger, many[r]))
+        assert err <= TOL[prec], f"{name} dag={dagger} p{prec} r{recon} rhs {r}: rel L2 {err:.3e}"

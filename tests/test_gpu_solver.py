@@ -1,5 +1,5 @@
 """CG on Mhat^dag Mhat x = b on the GPU: FP64, mixed FP32 and mixed FP16 (with FP64
-reliable updates), several right-hand sides.  Every solution must have a true
+reliable updates), several right-hand sides (batches of 1, 2, 4 and 8).  Every solution must have a true
 relative residual <= 1e-8 recomputed by the FP64 oracle's operator."""
 
 import numpy as np
@@ -19,7 +19,7 @@ def problem():
     require_gpu()
     from paper_0910_0262_gb300.qcd import CloverWilson
     dims = (6, 6, 4, 8)
-    U, b = synth.make_problem(dims, 0.2, 11, nrhs=3)
+    U, b = synth.make_problem(dims, 0.2, 11, nrhs=12)
     ref = evenodd.SchurOperator(U, KAPPA, CSW, -1.0)
     c = CloverWilson(dims, -1.0)
     c.load_gauge(to_dev(U), recon12=True)
@@ -32,8 +32,9 @@ def true_residual(ref, x, b):
 
 
 @pytest.mark.parametrize("inner", [64, 32, 16])
-@pytest.mark.parametrize("nrhs", [1, 3])
+@pytest.mark.parametrize("nrhs", [1, 3, 12])
 def test_cg_true_residual(problem, inner, nrhs):
+    """nrhs = 3 runs batches of 2 and 1, nrhs = 12 batches of 8 and 4 (the multi-RHS kernels)."""
     dims, U, b, ref, c = problem
     bb = b[:nrhs]
     x, stats, ok = c.cg_solve(to_dev(bb), tol=1e-8, inner_prec=inner, max_iter=5000)
