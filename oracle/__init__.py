@@ -23,6 +23,12 @@ project:
 * ``cg``       -- textbook conjugate gradient on Mhat^dagger Mhat.
 * ``force``    -- dS/dU for S = phi^dagger (Mhat^dagger Mhat)^-1 phi by brute
   force insertion into every path (each hopping term, each clover leaf).
+* ``cloverdet`` -- the clover determinant term S_det = -2 log det A_oo of the
+  even-odd preconditioned action (numpy.linalg.slogdet per site) and its
+  derivative by the same insertion; the full-lattice source preparation and
+  odd-site reconstruction of the even-odd solve.
+* ``local``    -- single-site evaluations of the operator for sampled checks of
+  large lattices.
 
 Every function is pinned by tests that do not reuse its own formula: the
 free-field plane-wave closed form, gamma5-hermiticity and the explicit adjoint,
@@ -32,4 +38,4 @@ own sign and normalisation conventions is unpinned (no MILC code or output is
 available); the conventions are stated where they are defined.
 """
 
-from . import lattice, dirac, evenodd, cg, force, local  # noqa: F401
+from . import lattice, dirac, evenodd, cg, force, cloverdet, local  # noqa: F401

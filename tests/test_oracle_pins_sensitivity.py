@@ -7,8 +7,9 @@ corresponding pin from the other oracle tests must then fail.
 import numpy as np
 import pytest
 
-from oracle import dirac, force, evenodd
+from oracle import dirac, force, evenodd, cloverdet
 import test_oracle_operator as t_op
+import test_oracle_cloverdet as t_cd
 import test_oracle_clover as t_cl
 import test_oracle_force as t_fo
 
@@ -97,3 +98,25 @@ def test_schur_sign_is_caught(monkeypatch):
     monkeypatch.setattr(evenodd.SchurOperator, "Mhat", mhat_plus)
     import test_oracle_solve as t_so
     assert _fails(t_so.test_schur_complement_matches_dense_full_solve, (2, 2, 2, 2), 0.5, 1)
+
+
+def test_determinant_coefficient_without_traceless_part_is_caught(monkeypatch):
+    orig = cloverdet.coefficients
+
+    def coeffs_with_trace(op):
+        C = orig(op)
+        odd = np.broadcast_to((np.indices(op.U.shape[:4]).sum(axis=0) % 2 == 1)[..., None, None], C.shape[1:])
+        return C + 0.01j * np.where(odd, np.eye(3), 0.0)[None]
+    monkeypatch.setattr(cloverdet, "coefficients", coeffs_with_trace)
+    assert _fails(t_cd.test_force_against_finite_differences)
+
+
+def test_determinant_of_even_sites_is_caught(monkeypatch):
+    monkeypatch.setattr(cloverdet, "action", lambda op: -2.0 * cloverdet.logdet(op)[0])
+    assert _fails(t_cd.test_small_csw_second_order_closed_form)
+
+
+def test_reconstruction_sign_is_caught(monkeypatch):
+    monkeypatch.setattr(cloverdet, "reconstruct_odd",
+                        lambda op, x_e, b_o: evenodd.SchurOperator.site(op.A_oo_inv, b_o - op.kappa * op.D_oe(x_e)))
+    assert _fails(t_cd.test_full_solve_with_both_parities_matches_dense, (2, 2, 2, 2), 24)
