@@ -11,7 +11,10 @@ value = device time per step (CUDA events on the library's stream, L2 flushed
 between steps).  The JSON line also carries the plain FP64 GPU solve time, the
 Dslash GFLOPS / GB/s of the kernels inside the solve, the roofline of the
 dominant kernel, an end-to-end number with host buffers, and the FP64 numpy
-oracle timed on a bounded sample on the host cores.
+oracle timed on a bounded sample on the host cores.  Beside the step it
+measures the hopping-kernel bandwidth of Mhat^dag Mhat on 32^3 x 64 and
+48^3 x 96 (FP32 / FP16, 1 and 8 / 4 RHS) and the batched FP16 8-RHS solve
+against 8 sequential FP64 solves on 32^3 x 64.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -324,6 +327,8 @@ def run_ours(args, world, rank, local):
                                                "note": "16^4 working set is L2-resident inside a solve"}
     if not args.no_hbm or not args.no_batched:
         result.update(large_volume(dev, hbm_peak, not args.no_hbm, not args.no_batched))
+    if not args.no_hbm:
+        result["dslash_largest_volume"] = largest_volume(dev, hbm_peak)
     if not args.no_e2e:
         result["e2e"] = run_e2e(op, U_np, b_np, w, stream, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -332,12 +337,41 @@ def run_ours(args, world, rank, local):
     return result
 
 
-def large_volume(dev, hbm_peak, do_hbm, do_batched, reps=5):
+def dslash_bandwidth(op, b, hbm_peak, rhs_list, warmup=5, reps=20):
+    """Mhat^dag Mhat (4 hopping launches with fused clover epilogues) in FP32 and FP16 for each RHS
+    count: after `warmup` applications, `reps` applications each timed by the library's per-launch
+    CUDA events (device time of the 4 launches); the median application gives the per-launch time,
+    and the algorithmic bytes and flops the library counts per launch give GB/s and GFLOP/s."""
+    import torch
+    from paper_0910_0262_gb300 import qcd as Q
+    out = {}
+    for prec in (32, 16):
+        for nrhs in rhs_list:
+            v = b[:nrhs].contiguous()
+            for _ in range(warmup):
+                op.dslash(v, Q.QCD_OP_MDAGM, precision=prec)
+            samples = []
+            for _ in range(reps):
+                op.profile(True)
+                op.dslash(v, Q.QCD_OP_MDAGM, precision=prec)
+                rows = [p for p in op.profile_read() if p["name"].startswith(f"dslash_p{prec}")]
+                op.profile(False)
+                samples.append((sum(p["total_ms"] for p in rows), sum(p["bytes"] for p in rows),
+                                sum(p["flops"] for p in rows), sum(p["launches"] for p in rows)))
+            ms = float(np.median([t[0] for t in samples]))
+            by, fl, n = samples[0][1], samples[0][2], samples[0][3]
+            gbs = by / (ms * 1e-3) / 1e9
+            out[f"fp{prec}_rhs{nrhs}"] = {"launches": n, "avg_us": 1e3 * ms / n, "gbs": gbs, "frac_hbm": gbs / hbm_peak,
+                                          "gflops": fl / (ms * 1e-3) / 1e9, "bytes_per_launch": by / n,
+                                          "timing": f"median of {reps} applications after {warmup} warm-up"}
+    return out
+
+
+def large_volume(dev, hbm_peak, do_hbm, do_batched):
     """32^3 x 64 lattice (eps 0.15, seed 4, 8 RHS; working set far above the 129 MB L2).
 
-    dslash_large_volume: Mhat^dag Mhat (4 hopping launches with fused clover epilogues) in FP32 and
-    FP16 with 12-real links, 1 and 8 RHS: per-launch CUDA-event times on the library's stream,
-    algorithmic bytes per launch / duration against the measured HBM bandwidth.
+    dslash_large_volume: Mhat^dag Mhat in FP32 and FP16 with 12-real links, 1 and 8 RHS
+    (dslash_bandwidth), against the measured HBM bandwidth.
     batched_solve: one batched mixed solve of the 8 RHS (FP16 inner, FP64 reliable updates) against
     8 sequential plain FP64 solves, both to a true residual of 1e-8.
     """
@@ -354,28 +388,9 @@ def large_volume(dev, hbm_peak, do_hbm, do_batched, reps=5):
     b = torch.from_numpy(b_np).to(dev)
     res = {}
     if do_hbm:
-        out = {}
-        for prec in (32, 16):
-            for nrhs in (1, 8):
-                v = b[:nrhs].contiguous()
-                op.dslash(v, Q.QCD_OP_MDAGM, precision=prec)
-                torch.cuda.synchronize(dev)
-                op.profile(True)
-                for _ in range(reps):
-                    op.dslash(v, Q.QCD_OP_MDAGM, precision=prec)
-                prof = op.profile_read()
-                op.profile(False)
-                rows = [p for p in prof if p["name"].startswith(f"dslash_p{prec}")]
-                ms = sum(p["total_ms"] for p in rows)
-                by = sum(p["bytes"] for p in rows)
-                fl = sum(p["flops"] for p in rows)
-                n = sum(p["launches"] for p in rows)
-                gbs = by / (ms * 1e-3) / 1e9
-                out[f"fp{prec}_rhs{nrhs}"] = {"launches": n, "avg_us": 1e3 * ms / n, "gbs": gbs,
-                                              "frac_hbm": gbs / hbm_peak, "gflops": fl / (ms * 1e-3) / 1e9,
-                                              "bytes_per_launch": by / n}
         res["dslash_large_volume"] = {"dims": list(dims), "op": "Mhat^dag Mhat (4 hopping launches with fused "
-                                      "clover epilogues)", "peak_gbs": hbm_peak, "results": out}
+                                      "clover epilogues)", "peak_gbs": hbm_peak,
+                                      "results": dslash_bandwidth(op, b, hbm_peak, (1, 8))}
     if do_batched:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         kw = dict(tol=1e-8, reliable_every=50, reliable_delta=0.1)
@@ -398,6 +413,26 @@ def large_volume(dev, hbm_peak, do_hbm, do_batched, reps=5):
             "sequential_iters": [s[1][0]["iters"] for s in seq],
             "sequential_true_rel_resid": max(s[1][0]["true_rel_resid"] for s in seq),
             "converged": bool(okb and all(s[2] for s in seq))}
+    op.close()
+    return res
+
+
+def largest_volume(dev, hbm_peak):
+    """48^3 x 96 lattice (eps 0.15, seed 5, 4 RHS; 10.6 M sites): the hopping-kernel bandwidth of
+    Mhat^dag Mhat in FP32 and FP16 for 1 and 4 RHS (dslash_bandwidth)."""
+    import torch
+    from paper_0910_0262_gb300 import synth
+    from paper_0910_0262_gb300 import qcd as Q
+    w = synth.WORKLOADS["c4_48^3x96"]
+    dims = w["dims"]
+    U_np, b_np = synth.make_problem(dims, w["eps"], w["seed"], w["nrhs"])
+    op = Q.CloverWilson(dims, -1.0, stream=torch.cuda.current_stream(dev))
+    op.load_gauge(torch.from_numpy(U_np).to(dev), recon12=True)
+    del U_np
+    op.clover_build(0.12, 1.0)
+    b = torch.from_numpy(b_np).to(dev)
+    res = {"dims": list(dims), "op": "Mhat^dag Mhat (4 hopping launches with fused clover epilogues)",
+           "peak_gbs": hbm_peak, "results": dslash_bandwidth(op, b, hbm_peak, (1, 4))}
     op.close()
     return res
 

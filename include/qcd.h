@@ -94,6 +94,7 @@ typedef struct {
 /* qcd_fermion_force flags */
 #define QCD_FORCE_INPUT_IS_SOLUTION 1 /* phi_or_x holds X = (Mhat^dag Mhat)^-1 phi: no solve */
 #define QCD_FORCE_GRADIENT 2          /* write G = dS/dRe U + i dS/dIm U instead of the Lie-algebra force */
+#define QCD_FORCE_CLOVER_DET 4        /* add the force of S_det = -2 sum_{x odd} log det A(x) */
 
 /*
  * Create a context for a lattice of extents dims = {X, Y, Z, T}; all must be
@@ -162,6 +163,35 @@ qcd_status qcd_cg_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, cons
  */
 qcd_status qcd_fermion_force(qcd_ctx* ctx, double* F, const double* phi_or_x, int nrhs, int flags,
                              const qcd_solver_params* params, qcd_solver_stats* stats);
+/*
+ * With QCD_FORCE_CLOVER_DET the force (or gradient) of the clover determinant term of the even-odd
+ * preconditioned two-flavour action is added: det M = det A_oo det Mhat, so the action carries
+ * S_det = -2 log det A_oo = -2 sum_{x odd} log det A(x) besides the pseudofermion term (the form of
+ * the clover_dynamical application the paper ports, Sec. 1).  Its derivative enters through the
+ * clover leaves like the pseudofermion's clover term.  With this flag nrhs may be 0 (phi_or_x may
+ * then be NULL): F is the determinant term alone.
+ */
+
+/*
+ * log det of the clover term from the Cholesky factors of the last qcd_clover_build, summed over
+ * the sites of each parity (both 6x6 chiral blocks): out[0] = sum_{x even} log det A(x),
+ * out[1] = sum_{x odd} log det A(x); S_det = -2 out[1].  out: host array of 2.  Synchronises.
+ * Returns QCD_ERR_STATE without a clover term.
+ */
+qcd_status qcd_clover_logdet(qcd_ctx* ctx, double out[2]);
+
+/*
+ * The full-lattice system M (x_e, x_o) = (b_e, b_o), M = [[A_ee, -kappa D_eo], [-kappa D_oe, A_oo]]
+ * (even sites first), reduces to the even-site system Mhat x_e = b_e + kappa D_eo A_oo^-1 b_o and
+ * the odd half x_o = A_oo^-1 (b_o + kappa D_oe x_e).  Both steps in FP64 on device complex128 fields
+ * [nrhs][V/2][4][3]; b_o may be NULL (zero).  Outputs must not overlap inputs.
+ * qcd_prepare_source: bhat_e = b_e + kappa D_eo A_oo^-1 b_o.
+ * qcd_reconstruct_odd: x_o = A_oo^-1 (b_o + kappa D_oe x_e).
+ * (Mhat x_e = bhat_e is solved as Mhat^dag Mhat x_e = Mhat^dag bhat_e with qcd_dslash and
+ * qcd_cg_solve.)  Return QCD_ERR_STATE without a clover term.
+ */
+qcd_status qcd_prepare_source(qcd_ctx* ctx, double* bhat_e, const double* b_e, const double* b_o, int nrhs);
+qcd_status qcd_reconstruct_odd(qcd_ctx* ctx, double* x_o, const double* x_e, const double* b_o, int nrhs);
 
 /*
  * Per-kernel timing with CUDA events on the context's stream.  enable = 1 resets

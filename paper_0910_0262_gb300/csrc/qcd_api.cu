@@ -123,6 +123,7 @@ struct qcd_ctx {
   void* Ainv32 = nullptr;
   void* A16 = nullptr;
   void* Ainv16 = nullptr;
+  double* logdet = nullptr;  // [parity][block][Vh] log det of each clover block
   bool have_clover = false;
   double kappa = 0, csw = 0;
   // device status words: [0] clover not positive definite, [1] non-finite input
@@ -517,7 +518,7 @@ qcd_status qcd_destroy(qcd_ctx* c) {
   cudaSetDevice(c->device);
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
-  void* dev[] = {c->g64, c->g32, c->g16, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, c->flags,
+  void* dev[] = {c->g64, c->g32, c->g16, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, c->logdet, c->flags,
                  c->pc_part, c->pc_bar,
                  c->partials, c->counter, c->results, c->cg, c->ctl};
   for (void* p : dev)
@@ -590,6 +591,7 @@ qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
     CUDA_TRY(cudaMalloc(&c->Ainv32, (size_t)2 * 18 * g.Vh * sizeof(float4)));
     CUDA_TRY(cudaMalloc(&c->A16, (size_t)2 * 9 * g.Vh * sizeof(uint4)));
     CUDA_TRY(cudaMalloc(&c->Ainv16, (size_t)2 * 9 * g.Vh * sizeof(uint4)));
+    CUDA_TRY(cudaMalloc(&c->logdet, (size_t)2 * 2 * g.Vh * sizeof(double)));
   }
   void* work;
   if ((s = ws_get(c, S_F_CL, force_clover_bytes(g), &work))) return s;
@@ -599,7 +601,7 @@ qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
     // the two inversions
     ProfScope ps(c, "clover_build", 0, 2.0 * g.Vh * (60 * 216.0 + 2 * 1000.0));
     launch_clover_build(g, c->g64, kappa, csw, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, work,
-                        c->flags, c->st);
+                        c->logdet, c->flags, c->st);
   }
   CUDA_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   if ((s = sync_and_check(c, "clover_build"))) return s;
@@ -1170,11 +1172,29 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
                              const qcd_solver_params* prm, qcd_solver_stats* stats) {
   qcd_status s = check_ctx(c);
   if (s) return s;
-  if (!F || !phi_or_x) return fail(QCD_ERR_ARG, "null pointer");
-  if (nrhs < 1) return fail(QCD_ERR_ARG, "nrhs must be >= 1");
-  if (flags & ~(QCD_FORCE_INPUT_IS_SOLUTION | QCD_FORCE_GRADIENT)) return fail(QCD_ERR_ARG, "unknown force flags");
+  const bool det = (flags & QCD_FORCE_CLOVER_DET) != 0;
+  if (!F || (!phi_or_x && nrhs > 0)) return fail(QCD_ERR_ARG, "null pointer");
+  if (nrhs < (det ? 0 : 1)) return fail(QCD_ERR_ARG, "nrhs must be >= 1 (>= 0 with QCD_FORCE_CLOVER_DET)");
+  if (flags & ~(QCD_FORCE_INPUT_IS_SOLUTION | QCD_FORCE_GRADIENT | QCD_FORCE_CLOVER_DET))
+    return fail(QCD_ERR_ARG, "unknown force flags");
   if (!c->have_clover) return fail(QCD_ERR_STATE, "fermion_force before clover_build");
   const Geom& g = c->g;
+  if (nrhs == 0) {
+    // the determinant term alone: its coefficients into a zeroed buffer, then the leaves
+    void* clf;
+    if ((s = ws_get(c, S_F_CL, force_clover_bytes(g), &clf))) return s;
+    CUDA_TRY(cudaMemsetAsync(clf, 0, force_clover_bytes(g), c->st));
+    const double V = 2.0 * g.Vh;
+    {
+      ProfScope ps(c, "force_det_coeff", g.Vh * (72 * 16.0) + V * 6 * 144.0 * 2, 0.0);
+      launch_force_det_coeff(g, c->kappa, c->csw, static_cast<const double2*>(clover_ptr(c, 64, true, 1)),
+                             static_cast<double2*>(clf), c->st);
+    }
+    ProfScope ps(c, "force_links", 4 * V * 504.0, 4 * V * force_link_flops(0, true));
+    launch_force_links(g, c->kappa, 0, c->g64, nullptr, nullptr, nullptr, nullptr, static_cast<const double2*>(clf),
+                       reinterpret_cast<double2*>(F), (flags & QCD_FORCE_GRADIENT) != 0, true, false, c->st);
+    return sync_and_check(c, "fermion_force");
+  }
   const size_t fs = (size_t)g.Vh * 12;
   // X (canonical, FP64) for all RHS
   const double2* X = reinterpret_cast<const double2*>(phi_or_x);
@@ -1226,6 +1246,11 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
     launch_force_coeff(g, c->kappa, c->csw, nb, Xe + off, Xo + off, Ye + off, Yo + off, static_cast<double2*>(clf),
                        k > 0, c->st);
   }
+  if (det) {
+    ProfScope ps(c, "force_det_coeff", g.Vh * (72 * 16.0) + V * 6 * 144.0 * 2, 0.0);
+    launch_force_det_coeff(g, c->kappa, c->csw, static_cast<const double2*>(clover_ptr(c, 64, true, 1)),
+                           static_cast<double2*>(clf), c->st);
+  }
   // per link: the hopping part of every batch, the clover part once (F is linear in G)
   for (size_t k = 0; k < batches.size(); k++) {
     const size_t off = batches[k].first;
@@ -1247,6 +1272,102 @@ qcd_status qcd_selftest_barrier_timeout(qcd_ctx* c) {
   if ((s = sync_and_check(c, "barrier self-test"))) return s;
   CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 4 * sizeof(unsigned), c->st));
   if (c->h_flags[2]) return fail(QCD_ERR_TIMEOUT, "grid barrier wait gave up as intended");
+  return QCD_OK;
+}
+
+qcd_status qcd_clover_logdet(qcd_ctx* c, double out[2]) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!out) return fail(QCD_ERR_ARG, "null pointer");
+  if (!c->have_clover) return fail(QCD_ERR_STATE, "clover_logdet before clover_build");
+  launch_parity_sum(c->g, c->logdet, reduce_args(c, FIN_STORE), c->st);
+  CUDA_TRY(cudaMemcpyAsync(c->h_results, c->results, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if ((s = sync_and_check(c, "clover_logdet"))) return s;
+  out[0] = c->h_results[0];
+  out[1] = c->h_results[1];
+  return QCD_OK;
+}
+
+// shared checks of the two full-lattice helpers
+static qcd_status eo_check(qcd_ctx* c, const void* out, const void* in1, const void* in2, int nrhs) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!out || !in1) return fail(QCD_ERR_ARG, "null field pointer");
+  if (nrhs < 1) return fail(QCD_ERR_ARG, "nrhs must be >= 1");
+  if (!c->have_clover) return fail(QCD_ERR_STATE, "needs clover_build");
+  const size_t bytes = (size_t)c->g.Vh * 12 * sizeof(double2) * nrhs;
+  for (const void* in : {in1, in2})
+    if (in && (const char*)out < (const char*)in + bytes && (const char*)in < (const char*)out + bytes)
+      return fail(QCD_ERR_ARG, "output overlaps an input");
+  return QCD_OK;
+}
+
+qcd_status qcd_prepare_source(qcd_ctx* c, double* bhat_e, const double* b_e, const double* b_o, int nrhs) {
+  qcd_status s = eo_check(c, bhat_e, b_e, b_o, nrhs);
+  if (s) return s;
+  const Geom& g = c->g;
+  const size_t n = (size_t)g.Vh * 12;
+  for (int done = 0; done < nrhs;) {
+    const int nb = batch_of(nrhs - done);
+    const double2* ce = reinterpret_cast<const double2*>(b_e) + done * n;
+    double2* cout = reinterpret_cast<double2*>(bhat_e) + done * n;
+    if (!b_o) {
+      CUDA_TRY(cudaMemcpyAsync(cout, ce, n * nb * sizeof(double2), cudaMemcpyDeviceToDevice, c->st));
+    } else {
+      void *u, *t;
+      const size_t fb = spinor_bytes(g, 64, nb);
+      if ((s = ws_get(c, S_IN, fb, &u)) || (s = ws_get(c, S_T, fb, &t))) return s;
+      // t = A_oo^-1 b_o, u = D_eo t (native), bhat_e = kappa u + b_e (canonical)
+      launch_spinor_to_native(64, g, reinterpret_cast<const double2*>(b_o) + done * n, u, nullptr, nb, c->st);
+      launch_clover_apply(64, g, clover_ptr(c, 64, true, 1), u, nullptr, t, nullptr, nb, c->st);
+      DslashArgs a = base_args(c, 64, 0, nb);
+      a.in = t;
+      a.out = u;
+      run_dslash(c, 64, EPI_NONE, a);
+      launch_spinor_to_canon(64, g, u, nullptr, cout, nb, c->st);
+      launch_axpby(n * nb, 1.0, ce, c->kappa, cout, c->st);
+    }
+    done += nb;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QCD_ERR_CUDA, "prepare_source launch: %s", cudaGetErrorString(e));
+  return QCD_OK;
+}
+
+qcd_status qcd_reconstruct_odd(qcd_ctx* c, double* x_o, const double* x_e, const double* b_o, int nrhs) {
+  qcd_status s = eo_check(c, x_o, x_e, b_o, nrhs);
+  if (s) return s;
+  const Geom& g = c->g;
+  const size_t n = (size_t)g.Vh * 12;
+  for (int done = 0; done < nrhs;) {
+    const int nb = batch_of(nrhs - done);
+    void *u, *t;
+    const size_t fb = spinor_bytes(g, 64, nb);
+    if ((s = ws_get(c, S_IN, fb, &u)) || (s = ws_get(c, S_T, fb, &t))) return s;
+    // t = A_oo^-1 D_oe x_e (one fused launch), then x_o = kappa t + A_oo^-1 b_o
+    launch_spinor_to_native(64, g, reinterpret_cast<const double2*>(x_e) + done * n, u, nullptr, nb, c->st);
+    DslashArgs a = base_args(c, 64, 1, nb);
+    a.in = u;
+    a.out = t;
+    a.clover = clover_ptr(c, 64, true, 1);
+    run_dslash(c, 64, EPI_CLOVER_INV, a);
+    double2* cout = reinterpret_cast<double2*>(x_o) + done * n;
+    launch_spinor_to_canon(64, g, t, nullptr, cout, nb, c->st);
+    if (b_o) {
+      launch_spinor_to_native(64, g, reinterpret_cast<const double2*>(b_o) + done * n, u, nullptr, nb, c->st);
+      launch_clover_apply(64, g, clover_ptr(c, 64, true, 1), u, nullptr, t, nullptr, nb, c->st);
+      // x_o = kappa x_o + (A_oo^-1 b_o): the native result goes through the canonical staging
+      void* stage;
+      if ((s = ws_get(c, S_CANON, n * nb * sizeof(double2), &stage))) return s;
+      launch_spinor_to_canon(64, g, t, nullptr, static_cast<double2*>(stage), nb, c->st);
+      launch_axpby(n * nb, 1.0, static_cast<const double2*>(stage), c->kappa, cout, c->st);
+    } else {
+      launch_axpby(n * nb, 0.0, cout, c->kappa, cout, c->st);
+    }
+    done += nb;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QCD_ERR_CUDA, "reconstruct_odd launch: %s", cudaGetErrorString(e));
   return QCD_OK;
 }
 

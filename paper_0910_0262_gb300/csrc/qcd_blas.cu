@@ -110,6 +110,23 @@ __global__ void __launch_bounds__(BB) redot_kernel(Geom g, int nrhs, const doubl
   grid_finish<BB>(nrhs, (long long)gridDim.x * gridDim.y, gridDim.x, red);
 }
 
+// per parity (blockIdx.y), the sum of the 2 * Vh doubles v[p][0 .. 2 Vh) (two chiral blocks per site)
+__global__ void __launch_bounds__(BB) parity_sum_kernel(Geom g, const double* v, ReduceArgs red) {
+  const int p = blockIdx.y;
+  const int j = blockIdx.x * BB + threadIdx.x;
+  const double x = j < 2 * g.Vh ? v[(size_t)p * 2 * g.Vh + j] : 0.0;
+  block_partial<BB>(x, p, blockIdx.x, gridDim.x, red);
+  grid_finish<BB>(2, (long long)gridDim.x * gridDim.y, gridDim.x, red);
+}
+
+// y = a x + b y over n complex numbers
+__global__ void __launch_bounds__(BB) axpby_kernel(size_t n, double a, const double2* x, double b, double2* y) {
+  const size_t j = (size_t)blockIdx.x * BB + threadIdx.x;
+  if (j >= n) return;
+  const double2 u = x[j], w = y[j];
+  y[j] = make_double2(fma(a, u.x, b * w.x), fma(a, u.y, b * w.y));
+}
+
 dim3 grid2(const Geom& g, int nrhs) { return dim3((g.Vh + BB - 1) / BB, nrhs); }
 
 }  // namespace
@@ -139,6 +156,16 @@ void launch_true_residual(int prec_r, const Geom& g, int nrhs, const double2* b,
 void launch_norm2(const Geom& g, int nrhs, const double2* v, const ReduceArgs& red, cudaStream_t st) {
   g_kernel_launches += 1;
   norm2_kernel<<<grid2(g, nrhs), BB, 0, st>>>(g, nrhs, v, red);
+}
+
+void launch_parity_sum(const Geom& g, const double* v, const ReduceArgs& red, cudaStream_t st) {
+  g_kernel_launches += 1;
+  parity_sum_kernel<<<dim3((2 * g.Vh + BB - 1) / BB, 2), BB, 0, st>>>(g, v, red);
+}
+
+void launch_axpby(size_t n, double a, const double2* x, double b, double2* y, cudaStream_t st) {
+  g_kernel_launches += 1;
+  axpby_kernel<<<(unsigned)((n + BB - 1) / BB), BB, 0, st>>>(n, a, x, b, y);
 }
 
 void launch_redot(const Geom& g, int nrhs, const double2* a, const double2* b, const ReduceArgs& red,

@@ -73,8 +73,8 @@ __device__ M3 field_strength(const Geom& g, const double2* g64, const int c[4], 
 __device__ __forceinline__ int tri(int i, int j) { return i * (i - 1) / 2 + j; }
 
 // Cholesky-based inverse of a Hermitian positive definite 6x6 matrix given as
-// (diag d, strictly-lower L).  Returns false on a non-positive pivot.
-__device__ bool invert6(const double d[6], const C L[15], double di[6], C Li[15]) {
+// (diag d, strictly-lower L), and log det = sum_j log L_jj^2.  Returns false on a non-positive pivot.
+__device__ bool invert6(const double d[6], const C L[15], double di[6], C Li[15], double* logdet) {
   C a[6][6];
   for (int i = 0; i < 6; i++) {
     a[i][i] = cmk(d[i], 0.0);
@@ -85,10 +85,12 @@ __device__ bool invert6(const double d[6], const C L[15], double di[6], C Li[15]
   }
   C l[6][6];
   double ild[6];  // 1 / L_jj: one division per pivot, multiplications elsewhere
+  double ldet = 0.0;
   for (int j = 0; j < 6; j++) {
     double s = a[j][j].re;
     for (int k = 0; k < j; k++) s -= norm2(l[j][k]);
     if (!(s > 0.0)) return false;
+    ldet += log(s);
     const double ld = sqrt(s);
     ild[j] = 1.0 / ld;
     l[j][j] = cmk(ld, 0.0);
@@ -118,6 +120,7 @@ __device__ bool invert6(const double d[6], const C L[15], double di[6], C Li[15]
       else Li[tri(i, j)] = s;
     }
   }
+  *logdet = ldet;
   return true;
 }
 
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(128) field_strength_kernel(Geom g, const doubl
 __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const double2* __restrict__ Fbuf, double kappa,
                                                               double csw, double2* A64, double2* Ainv64, float4* A32,
                                                               float4* Ainv32, uint4* A16, uint4* Ainv16,
-                                                              int* notposdef) {
+                                                              double* logdet, int* notposdef) {
   const int V = 2 * g.Vh;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= 2 * V) return;
@@ -211,11 +214,14 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const doub
   }
   double di[6];
   C Li[15];
-  if (!invert6(d, L, di, Li)) {
+  double ld = 0.0;
+  if (!invert6(d, L, di, Li, &ld)) {
     *notposdef = 1;
+    ld = 0.0;
     for (int k = 0; k < 6; k++) di[k] = 0.0;
     for (int k = 0; k < 15; k++) Li[k] = cmk(0.0, 0.0);
   }
+  logdet[((size_t)p * 2 + b) * g.Vh + h] = ld;
   store_block64(A64 + (size_t)p * 36 * g.Vh, g.Vh, h, b, d, L);
   store_block64(Ainv64 + (size_t)p * 36 * g.Vh, g.Vh, h, b, di, Li);
   if (A32) store_block32(A32 + (size_t)p * 18 * g.Vh, g.Vh, h, b, d, L);
@@ -242,7 +248,8 @@ __global__ void clover_apply_kernel(Geom g, const void* clov, const void* in, co
 }  // namespace
 
 void launch_clover_build(const Geom& g, const void* g64, double kappa, double csw, void* A64, void* Ainv64, void* A32,
-                         void* Ainv32, void* A16, void* Ainv16, void* work, int* notposdef, cudaStream_t st) {
+                         void* Ainv32, void* A16, void* Ainv16, void* work, double* logdet, int* notposdef,
+                         cudaStream_t st) {
   const int B = 128;
   const long long V = 2LL * g.Vh;
   // F per (site, plane), then one chiral block per thread
@@ -252,7 +259,7 @@ void launch_clover_build(const Geom& g, const void* g64, double kappa, double cs
   clover_assemble_kernel<<<(int)((2 * V + B - 1) / B), B, 0, st>>>(
       g, static_cast<const double2*>(work), kappa, csw, static_cast<double2*>(A64), static_cast<double2*>(Ainv64),
       static_cast<float4*>(A32), static_cast<float4*>(Ainv32), static_cast<uint4*>(A16), static_cast<uint4*>(Ainv16),
-      notposdef);
+      logdet, notposdef);
 }
 
 void launch_clover_apply(int prec, const Geom& g, const void* clover, const void* in, const float* in_norm, void* out,

@@ -20,6 +20,7 @@
 //     plaquette sum to the staple s1 s2 s3 with the corner's C inserted at each
 //     corner:  c0 s1 s2 s3 + s1 c1 s2 s3 + s1 s2 c2 s3 + s1 s2 s3 c3.
 //     The result is either G or F = -1/2 P_TA(U G^dag).
+//  3. det_coeff (optional): the clover determinant term's coefficients, added to C before 2.
 #include "qcd_dslash.cuh"
 #include "qcd_force.h"
 #include "qcd_su3.cuh"
@@ -162,9 +163,7 @@ template <int MU, int SGN>
 __device__ __forceinline__ void spin_project_full(const C v[12], C out[12]) {
   C h[6];
   project<MU, SGN>(v, h);
-#pragma unroll
-  for (int k = 0; k < 12; k++) out[k] = cmk(0.0, 0.0);
-  accumulate<MU, SGN>(h, out);
+  accumulate<MU, SGN, true>(h, out);
 }
 
 template <int MU>
@@ -175,6 +174,75 @@ __device__ __forceinline__ void hop_terms(const C Xy[12], const C Yy[12], const 
   outer_acc(v, Yy, scale, A);        // G += A^dag
   spin_project_full<MU, +1>(Xy, v);  // (1 + g) X(y)
   outer_acc(v, Yn, scale, B);        // G += B
+}
+
+// 3. the clover determinant term S_det = -2 sum_{x odd} log det A(x) of the even-odd preconditioned
+// action: dS_det = -2 sum tr(A^-1 dA), and with dA = -kappa c_sw sum sigma_{mu nu} (x) dF_{mu nu} and
+// F the traceless part of (Q - Q^dag)/(8i), its leaf coefficient at an odd site is
+//   C_{mu nu} = -i (kappa c_sw / 4)(B + B^dag),  B the traceless part of
+//   B_ac = sum_t sigma_{mu nu}[t][s] (A^-1)_{(s a),(t c)}  (s = the one spin sigma couples to t),
+// the same form as the pseudofermion's clover coefficient; it is added to Cbuf.  One thread per odd
+// site reads the two 6x6 blocks of A_oo^-1 (diagonal, then strictly-lower entries).
+__global__ void __launch_bounds__(FB) det_coeff_kernel(Geom g, double kappa, double csw, const double2* Ainv_odd,
+                                                       double2* Cbuf) {
+  const int h = blockIdx.x * FB + threadIdx.x;
+  if (h >= g.Vh) return;
+  const int V = 2 * g.Vh;
+  const Site st = site_of(g, 1, h);
+  double d[2][6];
+  C L[2][15];
+#pragma unroll
+  for (int b = 0; b < 2; b++) {
+    const double2* q = Ainv_odd + (size_t)(b * 18) * g.Vh + h;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const double2 v = __ldg(q + (size_t)k * g.Vh);
+      d[b][2 * k] = v.x;
+      d[b][2 * k + 1] = v.y;
+    }
+#pragma unroll
+    for (int k = 0; k < 15; k++) {
+      const double2 v = __ldg(q + (size_t)(3 + k) * g.Vh);
+      L[b][k] = cmk(v.x, v.y);
+    }
+  }
+  // (A^-1)_{(s a),(t c)} for spins s, t of one chiral block
+  auto el = [&](int s, int a, int t, int c) -> C {
+    const int b = s >> 1, i6 = 3 * (s & 1) + a, j6 = 3 * (t & 1) + c;
+    if (i6 == j6) return cmk(d[b][i6], 0.0);
+    if (i6 > j6) return L[b][i6 * (i6 - 1) / 2 + j6];
+    return conj(L[b][j6 * (j6 - 1) / 2 + i6]);
+  };
+  // sigma_{mu nu}[t][PERM[t]] = coefficient COEF[t] (0: 1, 1: -1, 2: i, 3: -i); planes xy xz xt yz yt zt
+  constexpr int PERM[6][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {1, 0, 3, 2}, {1, 0, 3, 2}, {1, 0, 3, 2}, {0, 1, 2, 3}};
+  constexpr int COEF[6][4] = {{0, 1, 0, 1}, {3, 2, 3, 2}, {1, 1, 0, 0}, {0, 0, 0, 0}, {3, 2, 2, 3}, {1, 0, 0, 1}};
+  const double f = kappa * csw / 4.0;
+#pragma unroll
+  for (int pl = 0; pl < 6; pl++) {
+    M3 B;
+#pragma unroll
+    for (int k = 0; k < 9; k++) B.e[k] = cmk(0.0, 0.0);
+#pragma unroll
+    for (int t = 0; t < 4; t++)
+#pragma unroll
+      for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int c = 0; c < 3; c++) B.e[3 * a + c] = B.e[3 * a + c] + coef_mul(COEF[pl][t], el(PERM[pl][t], a, t, c));
+    const double tr = (B.e[0].re + B.e[4].re + B.e[8].re) / 3.0;
+    const double ti = (B.e[0].im + B.e[4].im + B.e[8].im) / 3.0;
+    B.e[0] = B.e[0] - cmk(tr, ti);
+    B.e[4] = B.e[4] - cmk(tr, ti);
+    B.e[8] = B.e[8] - cmk(tr, ti);
+    M3 Cm = load_m3(Cbuf, pl, V, st.i);
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const C h2 = B.e[3 * a + c] + conj(B.e[3 * c + a]);
+        Cm.e[3 * a + c] = Cm.e[3 * a + c] + cmk(f * h2.im, -f * h2.re);  // -i f h2
+      }
+    store_m3(Cbuf, pl, V, st.i, Cm);
+  }
 }
 
 // c0 s1 s2 s3 + s1 c1 s2 s3 + s1 s2 c2 s3 + s1 s2 s3 c3
@@ -311,6 +379,12 @@ void launch_force_links(const Geom& g, double kappa, int nrhs, const void* g64, 
   link_force_kernel<<<(int)((4LL * V + FB - 1) / FB), FB, 0, st>>>(g, kappa, nrhs, static_cast<const double2*>(g64),
                                                                     Xe, Xo, Ye, Yo, Cbuf, out, gradient ? 1 : 0,
                                                                     with_clover ? 1 : 0, accumulate ? 1 : 0);
+}
+
+void launch_force_det_coeff(const Geom& g, double kappa, double csw, const double2* Ainv_odd, double2* Cbuf,
+                            cudaStream_t st) {
+  g_kernel_launches += 1;
+  det_coeff_kernel<<<(g.Vh + FB - 1) / FB, FB, 0, st>>>(g, kappa, csw, Ainv_odd, Cbuf);
 }
 
 double force_link_flops(int nrhs, bool with_clover) { return (with_clover ? 6.0 * 1800.0 : 0.0) + 744.0 * nrhs + 274.0; }

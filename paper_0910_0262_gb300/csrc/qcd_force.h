@@ -24,6 +24,10 @@ void launch_force_coeff(const Geom& g, double kappa, double csw, int nrhs, const
 void launch_force_links(const Geom& g, double kappa, int nrhs, const void* g64, const double2* Xe, const double2* Xo,
                         const double2* Ye, const double2* Yo, const double2* Cbuf, double2* out, bool gradient,
                         bool with_clover, bool accumulate, cudaStream_t st);
+// 3. add to Cbuf the coefficients of the clover determinant term S_det = -2 sum_{x odd} log det A(x)
+// (at odd sites), from the FP64 A_oo^-1 blocks ([36][Vh] double2 of the odd parity).
+void launch_force_det_coeff(const Geom& g, double kappa, double csw, const double2* Ainv_odd, double2* Cbuf,
+                            cudaStream_t st);
 // conventional FP64 flop counts: per link of kernel 2, per site of kernel 1
 double force_link_flops(int nrhs, bool with_clover);
 double force_coeff_flops(int nrhs);

@@ -44,10 +44,10 @@ void launch_check_finite(const double* data, size_t n, int* flag, cudaStream_t s
 // ---- clover (qcd_clover.cu)
 // A (both parities) and A^-1 (both parities) in FP64, FP32 and FP16; flag set if a block is not positive definite.
 // work: 6 * 9 * V double2 for the field strengths (two kernels: F per site and plane, then one chiral
-// block per thread).
+// block per thread); logdet: [parity][block][Vh] log det of each 6x6 block.
 void launch_clover_build(const Geom& g, const void* g64, double kappa, double csw, void* A64, void* Ainv64,
-                         void* A32, void* Ainv32, void* A16, void* Ainv16, void* work, int* notposdef,
-                         cudaStream_t st);
+                         void* A32, void* Ainv32, void* A16, void* Ainv16, void* work, double* logdet,
+                         int* notposdef, cudaStream_t st);
 // out = C in for a site-local clover field C of parity-matched fields
 void launch_clover_apply(int prec, const Geom& g, const void* clover, const void* in, const float* in_norm,
                          void* out, float* out_norm, int nrhs, cudaStream_t st);
@@ -68,6 +68,10 @@ void launch_true_residual(int prec_r, const Geom& g, int nrhs, const double2* b,
                           float* r_lon, const ReduceArgs& red, cudaStream_t st);
 // |v|^2 (FP64 native) -> reduction
 void launch_norm2(const Geom& g, int nrhs, const double2* v, const ReduceArgs& red, cudaStream_t st);
+// result[p] = sum of v[p][0 .. 2 Vh) for p = 0, 1 (FIN_STORE)
+void launch_parity_sum(const Geom& g, const double* v, const ReduceArgs& red, cudaStream_t st);
+// y = a x + b y over n complex numbers
+void launch_axpby(size_t n, double a, const double2* x, double b, double2* y, cudaStream_t st);
 // Re <a, b> (FP64 native) -> reduction
 void launch_redot(const Geom& g, int nrhs, const double2* a, const double2* b, const ReduceArgs& red,
                   cudaStream_t st);

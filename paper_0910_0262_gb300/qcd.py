@@ -27,6 +27,7 @@ QCD_GAUGE_RECON12 = 1
 QCD_OP_DSLASH_EO, QCD_OP_DSLASH_OE, QCD_OP_MHAT, QCD_OP_MDAGM, QCD_OP_CLOVER, QCD_OP_CLOVER_INV = range(6)
 QCD_FORCE_INPUT_IS_SOLUTION = 1
 QCD_FORCE_GRADIENT = 2
+QCD_FORCE_CLOVER_DET = 4
 
 
 class SolverParams(ctypes.Structure):
@@ -71,6 +72,9 @@ _SIGNATURES = {
     "qcd_mhat_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "qcd_selftest_barrier_timeout": (ctypes.c_int, [_P]),
     "qcd_selftest_fastdiv": (ctypes.c_longlong, []),
+    "qcd_clover_logdet": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "qcd_prepare_source": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "qcd_reconstruct_odd": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -134,6 +138,21 @@ def qcd_fermion_force(ctx, F_ptr, in_ptr, nrhs, flags, params, stats):
     if s not in (QCD_OK, 6):
         _check(s)
     return s
+
+
+def qcd_clover_logdet(ctx):
+    """(sum over even sites, sum over odd sites) of log det A(x)."""
+    out = (ctypes.c_double * 2)()
+    _check(lib().qcd_clover_logdet(ctx, out))
+    return out[0], out[1]
+
+
+def qcd_prepare_source(ctx, bhat_ptr, be_ptr, bo_ptr, nrhs):
+    return _check(lib().qcd_prepare_source(ctx, bhat_ptr, be_ptr, bo_ptr, int(nrhs)))
+
+
+def qcd_reconstruct_odd(ctx, xo_ptr, xe_ptr, bo_ptr, nrhs):
+    return _check(lib().qcd_reconstruct_odd(ctx, xo_ptr, xe_ptr, bo_ptr, int(nrhs)))
 
 
 def qcd_profile(ctx, enable):
@@ -236,16 +255,37 @@ class CloverWilson:
         s = qcd_cg_solve(self.ctx, _ptr(x), _ptr(b), n, prm, st)
         return x, [st[i].as_dict() for i in range(n)], s == QCD_OK
 
-    def fermion_force(self, phi_or_x, input_is_solution=False, gradient=False, **kw):
-        """Force (or Wirtinger gradient) [T, Z, Y, X, 4, 3, 3] summed over the RHS of phi_or_x."""
-        n = self._spinor(phi_or_x)
+    def fermion_force(self, phi_or_x, input_is_solution=False, gradient=False, clover_det=False, **kw):
+        """Force (or Wirtinger gradient) [T, Z, Y, X, 4, 3, 3] summed over the RHS of phi_or_x; with
+        clover_det the force of S_det = -2 log det A_oo is added (phi_or_x may then be None: that
+        term alone)."""
+        n = 0 if phi_or_x is None else self._spinor(phi_or_x)
         X, Y, Z, T = self.dims
-        F = torch.empty((T, Z, Y, X, 4, 3, 3), dtype=torch.complex128, device=phi_or_x.device)
-        flags = (QCD_FORCE_INPUT_IS_SOLUTION if input_is_solution else 0) | (QCD_FORCE_GRADIENT if gradient else 0)
-        prm = None if input_is_solution else solver_params(**kw)
-        st = (SolverStats * n)()
-        qcd_fermion_force(self.ctx, _ptr(F), _ptr(phi_or_x), n, flags, prm, st)
+        F = torch.empty((T, Z, Y, X, 4, 3, 3), dtype=torch.complex128, device=self.device)
+        flags = ((QCD_FORCE_INPUT_IS_SOLUTION if input_is_solution else 0) | (QCD_FORCE_GRADIENT if gradient else 0)
+                 | (QCD_FORCE_CLOVER_DET if clover_det else 0))
+        prm = None if (input_is_solution or n == 0) else solver_params(**kw)
+        st = (SolverStats * max(n, 1))()
+        qcd_fermion_force(self.ctx, _ptr(F), None if n == 0 else _ptr(phi_or_x), n, flags, prm, st)
         return F, [st[i].as_dict() for i in range(n)]
+
+    def clover_logdet(self):
+        """(sum_{x even}, sum_{x odd}) of log det A(x); the determinant term is S_det = -2 * [1]."""
+        return qcd_clover_logdet(self.ctx)
+
+    def prepare_source(self, b_e, b_o=None):
+        """b_e + kappa D_eo A_oo^-1 b_o: the even source of the full-lattice system."""
+        n = self._spinor(b_e)
+        out = torch.empty_like(b_e)
+        qcd_prepare_source(self.ctx, _ptr(out), _ptr(b_e), None if b_o is None else _ptr(b_o), n)
+        return out
+
+    def reconstruct_odd(self, x_e, b_o=None):
+        """x_o = A_oo^-1 (b_o + kappa D_oe x_e): the odd half of the full-lattice solution."""
+        n = self._spinor(x_e)
+        out = torch.empty_like(x_e)
+        qcd_reconstruct_odd(self.ctx, _ptr(out), _ptr(x_e), None if b_o is None else _ptr(b_o), n)
+        return out
 
     def profile(self, enable=True):
         qcd_profile(self.ctx, enable)
