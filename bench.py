@@ -325,6 +325,7 @@ def run_ours(args, world, rank, local):
     result["roofline_dslash_fp32_in_solve"] = {"bound": "hbm", "achieved": d32["gbs"], "peak": hbm_peak,
                                                "unit": "GB/s", "frac": d32["gbs"] / hbm_peak,
                                                "note": "16^4 working set is L2-resident inside a solve"}
+    result["clover_det_and_full_solve"] = clover_det_section(op, x, b, stream)
     if not args.no_hbm or not args.no_batched:
         result.update(large_volume(dev, hbm_peak, not args.no_hbm, not args.no_batched))
     if not args.no_hbm:
@@ -335,6 +336,39 @@ def run_ours(args, world, rank, local):
         result["cpu_baseline"] = cpu_baseline(w, iters)
     op.close()
     return result
+
+
+def clover_det_section(op, x, b, stream, warmup=3, reps=10):
+    """On the step's lattice: device times (CUDA events on the library's stream, median of `reps`
+    after `warmup`) of the clover determinant term -- log det A per parity, its force alone, the
+    pseudofermion force with and without it -- and of the full-lattice helpers (source preparation,
+    odd-site reconstruction), with the determinant term's value."""
+    import torch
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    le, lo = op.clover_logdet()
+    res = {"logdet_even": le, "logdet_odd": lo, "S_det": -2.0 * lo,
+           "logdet_ms": timed(op.clover_logdet),
+           "det_force_alone_ms": timed(lambda: op.fermion_force(None, clover_det=True)),
+           "pf_force_ms": timed(lambda: op.fermion_force(x, input_is_solution=True)),
+           "pf_plus_det_force_ms": timed(lambda: op.fermion_force(x, input_is_solution=True, clover_det=True)),
+           "prepare_source_ms": timed(lambda: op.prepare_source(b, b)),
+           "reconstruct_odd_ms": timed(lambda: op.reconstruct_odd(x, b)),
+           "timing": f"median of {reps} after {warmup} warm-up, CUDA events (calls that synchronise included)"}
+    res["det_term_marginal_ms"] = res["pf_plus_det_force_ms"] - res["pf_force_ms"]
+    return res
 
 
 def dslash_bandwidth(op, b, hbm_peak, rhs_list, warmup=5, reps=20):
