@@ -27,6 +27,8 @@ project:
   even-odd preconditioned action (numpy.linalg.slogdet per site) and its
   derivative by the same insertion; the full-lattice source preparation and
   odd-site reconstruction of the even-odd solve.
+* ``md``       -- Wilson gauge action and force, momenta, the link update exp(eps P) U
+  (scipy.linalg.expm) with reunitarisation, leapfrog, and the two-flavour R-algorithm step.
 * ``local``    -- single-site evaluations of the operator for sampled checks of
   large lattices.
 
@@ -38,4 +40,4 @@ own sign and normalisation conventions is unpinned (no MILC code or output is
 available); the conventions are stated where they are defined.
 """
 
-from . import lattice, dirac, evenodd, cg, force, cloverdet, local  # noqa: F401
+from . import lattice, dirac, evenodd, cg, force, cloverdet, md, local  # noqa: F401

@@ -7,8 +7,9 @@ corresponding pin from the other oracle tests must then fail.
 import numpy as np
 import pytest
 
-from oracle import dirac, force, evenodd, cloverdet
+from oracle import dirac, force, evenodd, cloverdet, md
 import test_oracle_operator as t_op
+import test_oracle_md as t_md
 import test_oracle_cloverdet as t_cd
 import test_oracle_clover as t_cl
 import test_oracle_force as t_fo
@@ -120,3 +121,20 @@ def test_reconstruction_sign_is_caught(monkeypatch):
     monkeypatch.setattr(cloverdet, "reconstruct_odd",
                         lambda op, x_e, b_o: evenodd.SchurOperator.site(op.A_oo_inv, b_o - op.kappa * op.D_oe(x_e)))
     assert _fails(t_cd.test_full_solve_with_both_parities_matches_dense, (2, 2, 2, 2), 24)
+
+
+def test_gauge_force_factor_is_caught(monkeypatch):
+    orig = md.gauge_force
+    monkeypatch.setattr(md, "gauge_force", lambda U, beta: 0.5 * orig(U, beta))
+    assert _fails(t_md.test_leapfrog_energy_error_is_second_order_and_reversible)
+
+
+def test_noise_drawn_before_the_half_step_is_caught(monkeypatch):
+    def r_step_early(U, P, eta, eps, beta, kappa, csw, with_det=True):
+        op = evenodd.SchurOperator(U, kappa, csw)
+        phis = [op.Mhat_dag(e) for e in eta]
+        Uh = md.update_links(U, P, eps / 2.0)
+        P = P - eps * md.total_force(Uh, beta, kappa, csw, phis, with_det)
+        return md.update_links(Uh, P, eps / 2.0), P
+    monkeypatch.setattr(md, "r_step", r_step_early)
+    assert _fails(t_md.test_r_step_is_reversible_for_fixed_noise)
