@@ -95,6 +95,7 @@ typedef struct {
 #define QCD_FORCE_INPUT_IS_SOLUTION 1 /* phi_or_x holds X = (Mhat^dag Mhat)^-1 phi: no solve */
 #define QCD_FORCE_GRADIENT 2          /* write G = dS/dRe U + i dS/dIm U instead of the Lie-algebra force */
 #define QCD_FORCE_CLOVER_DET 4        /* add the force of S_det = -2 sum_{x odd} log det A(x) */
+#define QCD_FORCE_ACCUMULATE 8        /* qcd_gauge_force: add to F instead of overwriting it */
 
 /*
  * Create a context for a lattice of extents dims = {X, Y, Z, T}; all must be
@@ -192,6 +193,39 @@ qcd_status qcd_clover_logdet(qcd_ctx* ctx, double out[2]);
  */
 qcd_status qcd_prepare_source(qcd_ctx* ctx, double* bhat_e, const double* b_e, const double* b_o, int nrhs);
 qcd_status qcd_reconstruct_odd(qcd_ctx* ctx, double* x_o, const double* x_e, const double* b_o, int nrhs);
+
+/*
+ * Molecular dynamics of the hybrid R algorithm the paper's application runs (Sec. 1, su3_rmd), with
+ * the standard conventions: Wilson gauge action S_g = beta sum_x sum_{mu<nu} (1 - Re tr P_{mu nu}/3);
+ * momenta P_mu(x) traceless anti-Hermitian (device complex128 [t][z][y][x][mu][3][3], like the
+ * links), kinetic energy K = -sum tr P^2; equations of motion dU/dtau = P U, dP/dtau = -F with F
+ * the Lie-algebra force of qcd_fermion_force's convention.
+ *
+ * qcd_gauge_force: F (or with QCD_FORCE_GRADIENT G) of S_g for the loaded links; with
+ *   QCD_FORCE_ACCUMULATE added to F.
+ * qcd_plaquette: *mean = < Re tr P_{mu nu}(x) / 3 > over sites and the six planes of the loaded links
+ *   (S_g = 6 V beta (1 - mean)).  Synchronises.
+ * qcd_kinetic_energy: *K = -sum tr P^2 = sum |P_ij|^2.  Synchronises.
+ * qcd_update_links: U <- exp(eps P) U on every link (the exponential by scaling and squaring of a
+ *   Taylor series, to rounding), then reunitarised (rows 0, 1 Gram-Schmidt, row 2 = conj(row 0 x
+ *   row 1)).  Touches only U: the context's packed links are not reloaded.
+ * qcd_r_step: one two-flavour R-algorithm step on U and P in place, for nrhs pseudofermion noise
+ *   fields eta (device [nrhs][V/2][4][3], complex Gaussian drawn by the caller):
+ *     U' = exp(eps/2 P) U;  phi = Mhat(U')^dag eta;  P -= eps (F_g + F_f(phi) [+ F_det]);
+ *     U = exp(eps/2 P) U'
+ *   (the noisy pseudofermion is drawn at the half step: the R algorithm's time shift
+ *   eps (1 - N_f/2)/2 vanishes for the two flavours Mhat^dag Mhat describes).  kappa and c_sw are
+ *   those of the last qcd_clover_build; flags: QCD_FORCE_CLOVER_DET adds the determinant term.
+ *   params/stats as in qcd_fermion_force.  On return the context holds U's packed links and clover
+ *   term.  Synchronises.
+ * All return QCD_ERR_STATE without loaded links (qcd_r_step: without a clover term).
+ */
+qcd_status qcd_gauge_force(qcd_ctx* ctx, double* F, double beta, int flags);
+qcd_status qcd_plaquette(qcd_ctx* ctx, double* mean);
+qcd_status qcd_kinetic_energy(qcd_ctx* ctx, const double* P, double* K);
+qcd_status qcd_update_links(qcd_ctx* ctx, double* U, const double* P, double eps);
+qcd_status qcd_r_step(qcd_ctx* ctx, double* U, double* P, const double* eta, int nrhs, double eps, double beta,
+                      int flags, const qcd_solver_params* params, qcd_solver_stats* stats);
 
 /*
  * Per-kernel timing with CUDA events on the context's stream.  enable = 1 resets

@@ -51,6 +51,7 @@ enum Slot {
   S_X_LO, S_R_LO, S_P, S_AP, S_TL, S_YL,                 // inner solver fields
   S_X_LO_N, S_R_LO_N, S_P_N, S_AP_N, S_TL_N, S_YL_N,
   S_F_X, S_F_Y, S_F_CL,                                  // force work fields
+  S_MD_F, S_MD_PHI,                                      // R-algorithm step
   S_COUNT
 };
 
@@ -1369,6 +1370,104 @@ qcd_status qcd_reconstruct_odd(qcd_ctx* c, double* x_o, const double* x_e, const
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(QCD_ERR_CUDA, "reconstruct_odd launch: %s", cudaGetErrorString(e));
   return QCD_OK;
+}
+
+qcd_status qcd_gauge_force(qcd_ctx* c, double* F, double beta, int flags) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!F) return fail(QCD_ERR_ARG, "null pointer");
+  if (flags & ~(QCD_FORCE_GRADIENT | QCD_FORCE_ACCUMULATE)) return fail(QCD_ERR_ARG, "unknown gauge force flags");
+  if (!c->have_gauge) return fail(QCD_ERR_STATE, "gauge_force before load_gauge");
+  {
+    const double V = 2.0 * c->g.Vh;
+    ProfScope ps(c, "gauge_force", 4 * V * (18 * 144.0 + 144.0 * ((flags & QCD_FORCE_ACCUMULATE) ? 2 : 1)),
+                 4 * V * 13 * 198.0);
+    launch_gauge_force(c->g, beta, c->g64, reinterpret_cast<double2*>(F), (flags & QCD_FORCE_GRADIENT) != 0,
+                       (flags & QCD_FORCE_ACCUMULATE) != 0, c->st);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QCD_ERR_CUDA, "gauge_force launch: %s", cudaGetErrorString(e));
+  return QCD_OK;
+}
+
+qcd_status qcd_plaquette(qcd_ctx* c, double* mean) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!mean) return fail(QCD_ERR_ARG, "null pointer");
+  if (!c->have_gauge) return fail(QCD_ERR_STATE, "plaquette before load_gauge");
+  launch_plaquette(c->g, c->g64, reduce_args(c, FIN_STORE), c->st);
+  CUDA_TRY(cudaMemcpyAsync(c->h_results, c->results, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if ((s = sync_and_check(c, "plaquette"))) return s;
+  *mean = c->h_results[0] / (6.0 * 2.0 * c->g.Vh);
+  return QCD_OK;
+}
+
+qcd_status qcd_kinetic_energy(qcd_ctx* c, const double* P, double* K) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!P || !K) return fail(QCD_ERR_ARG, "null pointer");
+  launch_flat_norm2((size_t)c->g.Vh * 2 * 4 * 9, reinterpret_cast<const double2*>(P), reduce_args(c, FIN_STORE),
+                    c->st);
+  CUDA_TRY(cudaMemcpyAsync(c->h_results, c->results, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if ((s = sync_and_check(c, "kinetic_energy"))) return s;
+  *K = c->h_results[0];
+  return QCD_OK;
+}
+
+qcd_status qcd_update_links(qcd_ctx* c, double* U, const double* P, double eps) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!U || !P) return fail(QCD_ERR_ARG, "null pointer");
+  const size_t nlinks = (size_t)c->g.Vh * 2 * 4;
+  if ((const char*)U < (const char*)P + nlinks * 9 * sizeof(double2) &&
+      (const char*)P < (const char*)U + nlinks * 9 * sizeof(double2))
+    return fail(QCD_ERR_ARG, "U and P overlap");
+  {
+    ProfScope ps(c, "link_update", nlinks * 3 * 144.0, nlinks * 16 * 198.0);
+    launch_link_update(nlinks, eps, reinterpret_cast<const double2*>(P), reinterpret_cast<double2*>(U), c->st);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QCD_ERR_CUDA, "update_links launch: %s", cudaGetErrorString(e));
+  return QCD_OK;
+}
+
+qcd_status qcd_r_step(qcd_ctx* c, double* U, double* P, const double* eta, int nrhs, double eps, double beta,
+                      int flags, const qcd_solver_params* prm, qcd_solver_stats* stats) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!U || !P || (!eta && nrhs > 0)) return fail(QCD_ERR_ARG, "null pointer");
+  if (nrhs < 0) return fail(QCD_ERR_ARG, "nrhs must be >= 0");
+  if (flags & ~QCD_FORCE_CLOVER_DET) return fail(QCD_ERR_ARG, "unknown r_step flags");
+  if (!c->have_clover) return fail(QCD_ERR_STATE, "r_step needs a clover term (kappa, c_sw)");
+  if (nrhs > 0 && (s = check_params(prm))) return s;
+  const Geom& g = c->g;
+  const double kappa = c->kappa, csw = c->csw;
+  const int gflags = c->recon == 12 ? QCD_GAUGE_RECON12 : 0;
+  const size_t nlinks = (size_t)g.Vh * 2 * 4;
+  void *fv, *phiv = nullptr;
+  if ((s = ws_get(c, S_MD_F, nlinks * 9 * sizeof(double2), &fv))) return s;
+  if (nrhs > 0 && (s = ws_get(c, S_MD_PHI, (size_t)g.Vh * 12 * sizeof(double2) * nrhs, &phiv))) return s;
+  double* F = static_cast<double*>(fv);
+  // half step of the links, then the fields at U'
+  if ((s = qcd_update_links(c, U, P, 0.5 * eps))) return s;
+  if ((s = qcd_load_gauge(c, U, 1, gflags)) || (s = qcd_clover_build(c, kappa, csw))) return s;
+  const int fflags = QCD_FORCE_CLOVER_DET & flags;
+  if (nrhs > 0) {
+    if ((s = qcd_dslash(c, static_cast<double*>(phiv), eta, QCD_OP_MHAT, 1, 64, nrhs))) return s;
+    s = qcd_fermion_force(c, F, static_cast<const double*>(phiv), nrhs, fflags, prm, stats);
+  } else if (fflags) {
+    s = qcd_fermion_force(c, F, nullptr, 0, fflags, nullptr, nullptr);
+  } else {
+    CUDA_TRY(cudaMemsetAsync(F, 0, nlinks * 9 * sizeof(double2), c->st));
+  }
+  if (s && s != QCD_ERR_NOT_CONVERGED) return s;
+  const qcd_status solve_status = s;
+  if ((s = qcd_gauge_force(c, F, beta, QCD_FORCE_ACCUMULATE))) return s;
+  // P -= eps F, then the second half step
+  launch_axpby(nlinks * 9, -eps, reinterpret_cast<const double2*>(F), 1.0, reinterpret_cast<double2*>(P), c->st);
+  if ((s = qcd_update_links(c, U, P, 0.5 * eps))) return s;
+  if ((s = qcd_load_gauge(c, U, 1, gflags)) || (s = qcd_clover_build(c, kappa, csw))) return s;
+  return solve_status;
 }
 
 long long qcd_selftest_fastdiv(void) {

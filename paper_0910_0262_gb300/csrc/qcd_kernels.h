@@ -68,6 +68,18 @@ void launch_true_residual(int prec_r, const Geom& g, int nrhs, const double2* b,
                           float* r_lon, const ReduceArgs& red, cudaStream_t st);
 // |v|^2 (FP64 native) -> reduction
 void launch_norm2(const Geom& g, int nrhs, const double2* v, const ReduceArgs& red, cudaStream_t st);
+// ---- molecular dynamics (qcd_md.cu); canonical link fields [V][4][3][3] complex128
+// Wilson gauge force (or gradient) of beta sum (1 - Re tr P / 3) from the FP64 packed links, written
+// to or added to out
+void launch_gauge_force(const Geom& g, double beta, const void* g64, double2* out, bool gradient, bool accumulate,
+                        cudaStream_t st);
+// result[0] = sum over sites and planes of Re tr P_{mu nu}(x) / 3 (FIN_STORE)
+void launch_plaquette(const Geom& g, const void* g64, const ReduceArgs& red, cudaStream_t st);
+// result[0] = sum of |v_j|^2 over n complex numbers (FIN_STORE)
+void launch_flat_norm2(size_t n, const double2* v, const ReduceArgs& red, cudaStream_t st);
+// U <- reunitarised exp(eps P) U for nlinks canonical links
+void launch_link_update(size_t nlinks, double eps, const double2* P, double2* U, cudaStream_t st);
+
 // result[p] = sum of v[p][0 .. 2 Vh) for p = 0, 1 (FIN_STORE)
 void launch_parity_sum(const Geom& g, const double* v, const ReduceArgs& red, cudaStream_t st);
 // y = a x + b y over n complex numbers

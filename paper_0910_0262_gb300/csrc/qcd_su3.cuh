@@ -25,6 +25,15 @@ __device__ __forceinline__ M3 mul(const M3& a, const M3& b) {
     }
   return c;
 }
+// acc + a conj(b) (four FMAs)
+__device__ __forceinline__ C cfma_nc(C a, C b, C acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(a.im, b.re, acc.im);
+  acc.im = fma(-a.re, b.im, acc.im);
+  return acc;
+}
+
 // a * b^dag
 __device__ __forceinline__ M3 mul_nd(const M3& a, const M3& b) {
   M3 c;
@@ -32,9 +41,9 @@ __device__ __forceinline__ M3 mul_nd(const M3& a, const M3& b) {
   for (int i = 0; i < 3; i++)
 #pragma unroll
     for (int j = 0; j < 3; j++) {
-      C s = cmk(0.0, 0.0);
-#pragma unroll
-      for (int k = 0; k < 3; k++) s = s + a.e[3 * i + k] * conj(b.e[3 * j + k]);
+      C s = a.e[3 * i] * conj(b.e[3 * j]);
+      s = cfma_nc(a.e[3 * i + 1], b.e[3 * j + 1], s);
+      s = cfma_nc(a.e[3 * i + 2], b.e[3 * j + 2], s);
       c.e[3 * i + j] = s;
     }
   return c;

@@ -28,6 +28,7 @@ QCD_OP_DSLASH_EO, QCD_OP_DSLASH_OE, QCD_OP_MHAT, QCD_OP_MDAGM, QCD_OP_CLOVER, QC
 QCD_FORCE_INPUT_IS_SOLUTION = 1
 QCD_FORCE_GRADIENT = 2
 QCD_FORCE_CLOVER_DET = 4
+QCD_FORCE_ACCUMULATE = 8
 
 
 class SolverParams(ctypes.Structure):
@@ -75,6 +76,12 @@ _SIGNATURES = {
     "qcd_clover_logdet": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "qcd_prepare_source": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
     "qcd_reconstruct_odd": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
+    "qcd_gauge_force": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.c_int]),
+    "qcd_plaquette": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "qcd_kinetic_energy": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
+    "qcd_update_links": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
+    "qcd_r_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -153,6 +160,34 @@ def qcd_prepare_source(ctx, bhat_ptr, be_ptr, bo_ptr, nrhs):
 
 def qcd_reconstruct_odd(ctx, xo_ptr, xe_ptr, bo_ptr, nrhs):
     return _check(lib().qcd_reconstruct_odd(ctx, xo_ptr, xe_ptr, bo_ptr, int(nrhs)))
+
+
+def qcd_gauge_force(ctx, F_ptr, beta, flags=0):
+    return _check(lib().qcd_gauge_force(ctx, F_ptr, float(beta), int(flags)))
+
+
+def qcd_plaquette(ctx):
+    out = ctypes.c_double()
+    _check(lib().qcd_plaquette(ctx, ctypes.byref(out)))
+    return out.value
+
+
+def qcd_kinetic_energy(ctx, P_ptr):
+    out = ctypes.c_double()
+    _check(lib().qcd_kinetic_energy(ctx, P_ptr, ctypes.byref(out)))
+    return out.value
+
+
+def qcd_update_links(ctx, U_ptr, P_ptr, eps):
+    return _check(lib().qcd_update_links(ctx, U_ptr, P_ptr, float(eps)))
+
+
+def qcd_r_step(ctx, U_ptr, P_ptr, eta_ptr, nrhs, eps, beta, flags, params, stats):
+    s = lib().qcd_r_step(ctx, U_ptr, P_ptr, eta_ptr, int(nrhs), float(eps), float(beta), int(flags),
+                         ctypes.byref(params) if params is not None else None, stats)
+    if s not in (QCD_OK, 6):
+        _check(s)
+    return s
 
 
 def qcd_profile(ctx, enable):
@@ -286,6 +321,45 @@ class CloverWilson:
         out = torch.empty_like(x_e)
         qcd_reconstruct_odd(self.ctx, _ptr(out), _ptr(x_e), None if b_o is None else _ptr(b_o), n)
         return out
+
+    def _links(self, t):
+        if t.dtype != torch.complex128 or not t.is_cuda or not t.is_contiguous() or t.numel() != self.V * 36:
+            raise ValueError("link-shaped fields must be contiguous complex128 CUDA tensors of V*4*9 elements")
+
+    def gauge_force(self, beta, gradient=False, out=None):
+        """Wilson gauge force (or gradient) of the loaded links; added to `out` when given."""
+        X, Y, Z, T = self.dims
+        F = out if out is not None else torch.empty((T, Z, Y, X, 4, 3, 3), dtype=torch.complex128,
+                                                     device=self.device)
+        self._links(F)
+        flags = (QCD_FORCE_GRADIENT if gradient else 0) | (QCD_FORCE_ACCUMULATE if out is not None else 0)
+        qcd_gauge_force(self.ctx, _ptr(F), beta, flags)
+        return F
+
+    def plaquette(self):
+        """Mean of Re tr P_{mu nu}(x) / 3 over sites and planes of the loaded links."""
+        return qcd_plaquette(self.ctx)
+
+    def kinetic_energy(self, P):
+        self._links(P)
+        return qcd_kinetic_energy(self.ctx, _ptr(P))
+
+    def update_links(self, U, P, eps):
+        """U <- exp(eps P) U (reunitarised), in place."""
+        self._links(U)
+        self._links(P)
+        qcd_update_links(self.ctx, _ptr(U), _ptr(P), eps)
+        return U
+
+    def r_step(self, U, P, eta, eps, beta, clover_det=True, **kw):
+        """One two-flavour R-algorithm step on U and P in place (noise eta [n, V/2, 4, 3] or None)."""
+        self._links(U)
+        self._links(P)
+        n = 0 if eta is None else self._spinor(eta)
+        st = (SolverStats * max(n, 1))()
+        s = qcd_r_step(self.ctx, _ptr(U), _ptr(P), None if eta is None else _ptr(eta), n, eps, beta,
+                       QCD_FORCE_CLOVER_DET if clover_det else 0, solver_params(**kw) if n else None, st)
+        return [st[i].as_dict() for i in range(n)], s == QCD_OK
 
     def profile(self, enable=True):
         qcd_profile(self.ctx, enable)

@@ -1,0 +1,143 @@
+"""GPU parity of the molecular-dynamics pieces against the oracle (``oracle.md``).
+
+* Wilson gauge gradient and force, element by element (FP64, relative L2 1e-13);
+* mean plaquette and kinetic energy (1e-13);
+* the link update exp(eps P) U with reunitarisation, also with eps |P| large enough to need the
+  scaling-and-squaring path (1e-13);
+* one two-flavour R-algorithm step with two pseudofermions and the determinant term (links and
+  momenta within 1e-9: both sides solve to 1e-12), and its reversibility for fixed noise;
+* leapfrog composed from the GPU calls (gauge + pseudofermion + determinant forces, link update):
+  the energy error H = K + S_g + S_f + S_det, every term measured on the GPU, falls as eps^2.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import evenodd, force, md
+from paper_0910_0262_gb300 import synth
+from gpu_util import require_gpu, to_dev, to_np, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+KAPPA, CSW, BETA = 0.12, 1.0, 5.6
+
+
+def random_momenta(shape, rng, scale=1.0):
+    p = scale * rng.standard_normal(tuple(shape) + (8,))
+    return np.einsum('...a,aij->...ij', 1j * p, synth.T_GEN)
+
+
+@pytest.fixture(scope="module", params=[(6, 6, 4, 6), (4, 2, 6, 4)], ids=["6x6x4x6", "4x2x6x4"])
+def links(request):
+    require_gpu()
+    from paper_0910_0262_gb300.qcd import CloverWilson
+    dims = request.param
+    U, _ = synth.make_problem(dims, 0.4, 61)
+    c = CloverWilson(dims, -1.0)
+    c.load_gauge(to_dev(U))
+    yield dims, U, c
+    c.close()
+
+
+def test_gauge_force_and_gradient(links):
+    dims, U, c = links
+    G = to_np(c.gauge_force(BETA, gradient=True))
+    G_ref = md.gauge_gradient(U, BETA)
+    assert rel_l2(G, G_ref) <= 1e-13
+    F = to_np(c.gauge_force(BETA))
+    assert rel_l2(F, force.lie_force(U, G_ref)) <= 1e-13
+    F2 = to_np(c.gauge_force(BETA, out=to_dev(F)))
+    assert rel_l2(F2, 2 * F) <= 1e-15
+
+
+def test_plaquette_and_kinetic_energy(links):
+    dims, U, c = links
+    assert abs(c.plaquette() - md.mean_plaquette(U)) <= 1e-14
+    P = random_momenta(U.shape[:5], np.random.default_rng(2))
+    K = c.kinetic_energy(to_dev(P))
+    assert abs(K - md.kinetic_energy(P)) <= 1e-13 * md.kinetic_energy(P)
+
+
+@pytest.mark.parametrize("eps,scale", [(0.1, 1.0), (2.0, 3.0)])
+def test_link_update(links, eps, scale):
+    dims, U, c = links
+    P = random_momenta(U.shape[:5], np.random.default_rng(3), scale)
+    Ut = to_dev(U)
+    c.update_links(Ut, to_dev(P), eps)
+    assert rel_l2(to_np(Ut), md.update_links(U, P, eps)) <= 1e-13
+
+
+def _r_setup(dims, seed):
+    from paper_0910_0262_gb300.qcd import CloverWilson
+    U, eta = synth.make_problem(dims, 0.3, seed, nrhs=2)
+    P = random_momenta(U.shape[:5], np.random.default_rng(seed))
+    c = CloverWilson(dims, -1.0)
+    c.load_gauge(to_dev(U))
+    c.clover_build(KAPPA, CSW)
+    return U, P, eta, c
+
+
+def test_r_step_matches_oracle_and_is_reversible():
+    require_gpu()
+    dims = (2, 2, 2, 4)
+    U, P, eta, c = _r_setup(dims, 62)
+    Ut, Pt = to_dev(U), to_dev(P)
+    stats, ok = c.r_step(Ut, Pt, to_dev(eta), 0.05, BETA, clover_det=True, tol=1e-12, inner_prec=64)
+    assert ok and len(stats) == 2
+    U1, P1 = md.r_step(U, P, eta, 0.05, BETA, KAPPA, CSW, with_det=True)
+    assert rel_l2(to_np(Ut), U1) <= 1e-9
+    assert rel_l2(to_np(Pt), P1) <= 1e-9
+    assert abs(c.plaquette() - md.mean_plaquette(U1)) <= 1e-9
+    Pt.neg_()
+    c.r_step(Ut, Pt, to_dev(eta), 0.05, BETA, clover_det=True, tol=1e-12, inner_prec=64)
+    assert rel_l2(to_np(Ut), U) <= 1e-9 and rel_l2(-to_np(Pt), P) <= 1e-9
+    c.close()
+
+
+def test_gpu_leapfrog_energy_error_is_second_order():
+    require_gpu()
+    from paper_0910_0262_gb300 import qcd as Q
+    from paper_0910_0262_gb300.qcd import CloverWilson
+    dims = (4, 4, 4, 4)
+    U0, eta = synth.make_problem(dims, 0.3, 63, nrhs=1)
+    P0 = random_momenta(U0.shape[:5], np.random.default_rng(63))
+    c = CloverWilson(dims, -1.0)
+    c.load_gauge(to_dev(U0))
+    c.clover_build(KAPPA, CSW)
+    phi = c.dslash(to_dev(eta), Q.QCD_OP_MHAT, dagger=True)  # fixed pseudofermion
+    kw = dict(tol=1e-13, inner_prec=64)
+
+    def load(U):
+        c.load_gauge(U)
+        c.clover_build(KAPPA, CSW)
+
+    def total_force(U):
+        load(U)
+        F, _ = c.fermion_force(phi, clover_det=True, **kw)
+        return c.gauge_force(BETA, out=F)
+
+    def H(U, P):
+        load(U)
+        _, st, ok = c.cg_solve(phi, **kw)
+        S_f = st[0]["b_dot_x"]
+        S_det = -2.0 * c.clover_logdet()[1]
+        S_g = 6 * np.prod(dims) * BETA * (1.0 - c.plaquette())
+        return c.kinetic_energy(P) + S_g + S_f + S_det
+
+    U, P = to_dev(U0), to_dev(P0)
+    H0 = H(U, P)
+    dH = []
+    for n in (4, 8):
+        eps = 0.1 / n
+        U, P = to_dev(U0), to_dev(P0)
+        F = total_force(U)
+        for _ in range(n):
+            P -= 0.5 * eps * F
+            c.update_links(U, P, eps)
+            F = total_force(U)
+            P -= 0.5 * eps * F
+        dH.append(abs(H(U, P) - H0))
+    c.close()
+    assert dH[0] > 1e-7
+    assert 3.0 < dH[0] / dH[1] < 5.5, dH
