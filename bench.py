@@ -326,6 +326,7 @@ def run_ours(args, world, rank, local):
                                                "unit": "GB/s", "frac": d32["gbs"] / hbm_peak,
                                                "note": "16^4 working set is L2-resident inside a solve"}
     result["clover_det_and_full_solve"] = clover_det_section(op, x, b, stream)
+    result["r_algorithm_step"] = r_step_section(op, U, w, stream)
     if not args.no_hbm or not args.no_batched:
         result.update(large_volume(dev, hbm_peak, not args.no_hbm, not args.no_batched))
     if not args.no_hbm:
@@ -336,6 +337,49 @@ def run_ours(args, world, rank, local):
         result["cpu_baseline"] = cpu_baseline(w, iters)
     op.close()
     return result
+
+
+def r_step_section(op, U, w, stream, warmup=2, reps=5, eps=0.02, beta=5.6):
+    """One two-flavour R-algorithm step on the step's lattice (one pseudofermion, determinant term,
+    mixed FP32 solve to 1e-8): device time (CUDA events, median of `reps`) and its kernel classes
+    from one profiled step; momenta and noise drawn on the host with numpy (seeded)."""
+    import torch
+    from paper_0910_0262_gb300 import synth
+    rng = np.random.default_rng(71)
+    Ut = U.clone()
+    p = rng.standard_normal(tuple(Ut.shape[:5]) + (8,))
+    P = torch.from_numpy(np.einsum('...a,aij->...ij', 1j * p, synth.T_GEN)).to(Ut.device)
+    eta = torch.from_numpy(synth.gaussian_sources(w["dims"], 1, rng)).to(Ut.device)
+    kw = dict(tol=1e-8, inner_prec=32, reliable_every=50, reliable_delta=0.1)
+    ts, iters = [], []
+    for k in range(warmup + reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if k == warmup:
+            op.profile(True)
+        e0.record(stream)
+        st, ok = op.r_step(Ut, P, eta, eps, beta, clover_det=True, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k == warmup:
+            prof = op.profile_read()
+            op.profile(False)
+        if not ok:
+            raise RuntimeError("R step solve did not converge")
+        if k >= warmup:
+            ts.append(e0.elapsed_time(e1))
+            iters.append(st[0]["iters"])
+    classes = {}
+    for q in prof:
+        key = q["name"].split("_r")[0] if q["name"].startswith("dslash") else q["name"]
+        c = classes.setdefault(key, {"launches": 0, "ms": 0.0})
+        c["launches"] += q["launches"]
+        c["ms"] += q["total_ms"]
+    op.load_gauge(U, recon12=True)
+    op.clover_build(w["kappa"], w["csw"])
+    return {"ms": float(np.median(ts)), "eps": eps, "beta": beta, "pseudofermions": 1, "clover_det": True,
+            "solve": "mixed fp32, tol 1e-8", "cg_iters": iters, "plaquette_after": op.plaquette(),
+            "kernel_ms_one_step": {k: round(v["ms"], 4) for k, v in sorted(classes.items(), key=lambda kv: -kv[1]["ms"])},
+            "timing": f"median of {reps} steps after {warmup}, CUDA events"}
 
 
 def clover_det_section(op, x, b, stream, warmup=3, reps=10):

@@ -29,6 +29,7 @@ project:
   odd-site reconstruction of the even-odd solve.
 * ``md``       -- Wilson gauge action and force, momenta, the link update exp(eps P) U
   (scipy.linalg.expm) with reunitarisation, leapfrog, and the two-flavour R-algorithm step.
+* ``measure``  -- Polyakov loop and the stochastic psi-bar psi estimate (the plaquette is in ``md``).
 * ``local``    -- single-site evaluations of the operator for sampled checks of
   large lattices.
 
@@ -40,4 +41,4 @@ own sign and normalisation conventions is unpinned (no MILC code or output is
 available); the conventions are stated where they are defined.
 """
 
-from . import lattice, dirac, evenodd, cg, force, cloverdet, md, local  # noqa: F401
+from . import lattice, dirac, evenodd, cg, force, cloverdet, md, measure, local  # noqa: F401
