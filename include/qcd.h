@@ -228,6 +228,20 @@ qcd_status qcd_r_step(qcd_ctx* ctx, double* U, double* P, const double* eta, int
                       int flags, const qcd_solver_params* params, qcd_solver_stats* stats);
 
 /*
+ * Measurements per trajectory.
+ * qcd_polyakov: out[0] + i out[1] = < tr prod_{t=0}^{T-1} U_t(xvec, t) / 3 > over the spatial sites of
+ *   the loaded links (plain links: the antiperiodic sign belongs to the fermions).  Synchronises.
+ * qcd_pbp: the stochastic psi-bar psi estimate out[r] = Re eta_r^dag M^-1 eta_r / (2V) for nrhs noise
+ *   vectors eta_r = (eta_e, eta_o) (device [nrhs][V/2][4][3] each, complex Gaussian with unit
+ *   variance per real drawn by the caller, so that it estimates Re Tr M^-1 / V): M^-1 eta through
+ *   qcd_prepare_source, the CG of qcd_cg_solve on Mhat^dag Mhat x_e = Mhat^dag bhat_e (params,
+ *   stats as there) and qcd_reconstruct_odd.  out: host array of nrhs.  Synchronises.
+ */
+qcd_status qcd_polyakov(qcd_ctx* ctx, double out[2]);
+qcd_status qcd_pbp(qcd_ctx* ctx, const double* eta_e, const double* eta_o, int nrhs, double* out,
+                   const qcd_solver_params* params, qcd_solver_stats* stats);
+
+/*
  * Per-kernel timing with CUDA events on the context's stream.  enable = 1 resets
  * the counters and starts recording an event pair around every launch of the
  * tracked kernels (hopping kernels by epilogue, BLAS updates); 0 stops.

@@ -52,6 +52,7 @@ enum Slot {
   S_X_LO_N, S_R_LO_N, S_P_N, S_AP_N, S_TL_N, S_YL_N,
   S_F_X, S_F_Y, S_F_CL,                                  // force work fields
   S_MD_F, S_MD_PHI,                                      // R-algorithm step
+  S_PBP,                                                 // psi-bar psi estimate
   S_COUNT
 };
 
@@ -1467,6 +1468,60 @@ qcd_status qcd_r_step(qcd_ctx* c, double* U, double* P, const double* eta, int n
   launch_axpby(nlinks * 9, -eps, reinterpret_cast<const double2*>(F), 1.0, reinterpret_cast<double2*>(P), c->st);
   if ((s = qcd_update_links(c, U, P, 0.5 * eps))) return s;
   if ((s = qcd_load_gauge(c, U, 1, gflags)) || (s = qcd_clover_build(c, kappa, csw))) return s;
+  return solve_status;
+}
+
+qcd_status qcd_polyakov(qcd_ctx* c, double out[2]) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!out) return fail(QCD_ERR_ARG, "null pointer");
+  if (!c->have_gauge) return fail(QCD_ERR_STATE, "polyakov before load_gauge");
+  launch_polyakov(c->g, c->g64, reduce_args(c, FIN_STORE), c->st);
+  CUDA_TRY(cudaMemcpyAsync(c->h_results, c->results, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  if ((s = sync_and_check(c, "polyakov"))) return s;
+  out[0] = c->h_results[0] / c->g.XYZ;
+  out[1] = c->h_results[1] / c->g.XYZ;
+  return QCD_OK;
+}
+
+qcd_status qcd_pbp(qcd_ctx* c, const double* eta_e, const double* eta_o, int nrhs, double* out,
+                   const qcd_solver_params* prm, qcd_solver_stats* stats) {
+  qcd_status s = check_ctx(c);
+  if (s) return s;
+  if (!eta_e || !eta_o || !out) return fail(QCD_ERR_ARG, "null pointer");
+  if (nrhs < 1 || nrhs > MAX_RHS) return fail(QCD_ERR_ARG, "nrhs must be in 1..%d", MAX_RHS);
+  if (!c->have_clover) return fail(QCD_ERR_STATE, "pbp needs a clover term");
+  if ((s = check_params(prm))) return s;
+  const Geom& g = c->g;
+  const size_t n = (size_t)g.Vh * 12, fb = n * nrhs * sizeof(double2);
+  void* w;
+  if ((s = ws_get(c, S_PBP, 4 * fb, &w))) return s;
+  double2* bh = static_cast<double2*>(w);
+  double2* rhs = bh + n * nrhs;
+  double2* xe = rhs + n * nrhs;
+  double2* xo = xe + n * nrhs;
+  if ((s = qcd_prepare_source(c, reinterpret_cast<double*>(bh), eta_e, eta_o, nrhs))) return s;
+  if ((s = qcd_dslash(c, reinterpret_cast<double*>(rhs), reinterpret_cast<const double*>(bh), QCD_OP_MHAT, 1, 64,
+                      nrhs)))
+    return s;
+  CUDA_TRY(cudaMemsetAsync(xe, 0, fb, c->st));
+  qcd_solver_params p2 = *prm;
+  p2.use_x0 = 0;
+  const qcd_status solve_status = qcd_cg_solve(c, reinterpret_cast<double*>(xe), reinterpret_cast<const double*>(rhs),
+                                               nrhs, &p2, stats);
+  if (solve_status && solve_status != QCD_ERR_NOT_CONVERGED) return solve_status;
+  if ((s = qcd_reconstruct_odd(c, reinterpret_cast<double*>(xo), reinterpret_cast<const double*>(xe), eta_o, nrhs)))
+    return s;
+  // Re <eta_e, x_e> + Re <eta_o, x_o> per RHS
+  std::vector<double> acc(nrhs, 0.0);
+  for (int half = 0; half < 2; half++) {
+    launch_flat_redot(n, nrhs, reinterpret_cast<const double2*>(half ? eta_o : eta_e), half ? xo : xe,
+                      reduce_args(c, FIN_STORE), c->st);
+    CUDA_TRY(cudaMemcpyAsync(c->h_results, c->results, nrhs * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if ((s = sync_and_check(c, "pbp"))) return s;
+    for (int r = 0; r < nrhs; r++) acc[r] += c->h_results[r];
+  }
+  for (int r = 0; r < nrhs; r++) out[r] = acc[r] / (2.0 * 2.0 * g.Vh);
   return solve_status;
 }
 

@@ -77,6 +77,11 @@ void launch_gauge_force(const Geom& g, double beta, const void* g64, double2* ou
 void launch_plaquette(const Geom& g, const void* g64, const ReduceArgs& red, cudaStream_t st);
 // result[0] = sum of |v_j|^2 over n complex numbers (FIN_STORE)
 void launch_flat_norm2(size_t n, const double2* v, const ReduceArgs& red, cudaStream_t st);
+// result[0] + i result[1] = sum over spatial sites of tr prod_t U_t / 3 (FIN_STORE)
+void launch_polyakov(const Geom& g, const void* g64, const ReduceArgs& red, cudaStream_t st);
+// result[r] = Re sum_j conj(a_j) b_j over the n complex numbers of RHS r (FIN_STORE)
+void launch_flat_redot(size_t n, int nrhs, const double2* a, const double2* b, const ReduceArgs& red,
+                       cudaStream_t st);
 // U <- reunitarised exp(eps P) U for nlinks canonical links
 void launch_link_update(size_t nlinks, double eps, const double2* P, double2* U, cudaStream_t st);
 

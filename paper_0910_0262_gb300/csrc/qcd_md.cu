@@ -1,6 +1,7 @@
 // Molecular-dynamics kernels of the hybrid R algorithm (the update the paper's application runs,
 // Sec. 1, su3_rmd): Wilson gauge force, plaquette sum, momentum norm and the link update
-// U <- exp(eps P) U with reunitarisation.  All FP64.
+// U <- exp(eps P) U with reunitarisation; and the per-trajectory measurements (Polyakov loop, the
+// dot products of the psi-bar psi estimate).  All FP64.
 //
 //   S_g = beta sum_x sum_{mu<nu} (1 - Re tr P_{mu nu}(x) / 3)
 //   P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
@@ -139,6 +140,40 @@ __global__ void __launch_bounds__(MB) flat_norm2_kernel(size_t n, const double2*
   grid_finish<MB>(1, gridDim.x, gridDim.x, red);
 }
 
+// Polyakov loop: per spatial site, tr prod_t U_t(x, t) / 3; real and imaginary parts summed as RHS
+// 0 and 1 of the reduction
+__global__ void __launch_bounds__(MB) polyakov_kernel(Geom g, const double2* g64, ReduceArgs red) {
+  const int XYZ = g.XYZ;
+  const int j = blockIdx.x * MB + threadIdx.x;
+  C tr = cmk(0.0, 0.0);
+  if (j < XYZ) {
+    const int q1 = g.dX.div(j);
+    const int x = j - q1 * g.X;
+    const int z = g.dY.div(q1);
+    const int y = q1 - z * g.Y;
+    M3 p = link_at(g, g64, x, y, z, 0, 3);
+    for (int t = 1; t < g.T; t++) p = mul(p, link_at(g, g64, x, y, z, t, 3));
+    tr = p.e[0] + p.e[4] + p.e[8];
+  }
+  block_partial<MB>(tr.re / 3.0, 0, blockIdx.x, gridDim.x, red);
+  block_partial<MB>(tr.im / 3.0, 1, blockIdx.x, gridDim.x, red);
+  grid_finish<MB>(2, gridDim.x, gridDim.x, red);
+}
+
+// per RHS r (blockIdx.y): Re sum_j conj(a_j) b_j over n complex numbers at offset r * n
+__global__ void __launch_bounds__(MB) flat_redot_kernel(size_t n, int nrhs, const double2* a, const double2* b,
+                                                        ReduceArgs red) {
+  const size_t j = (size_t)blockIdx.x * MB + threadIdx.x;
+  const int r = blockIdx.y;
+  double s = 0.0;
+  if (j < n) {
+    const double2 u = a[(size_t)r * n + j], v = b[(size_t)r * n + j];
+    s = u.x * v.x + u.y * v.y;
+  }
+  block_partial<MB>(s, r, blockIdx.x, gridDim.x, red);
+  grid_finish<MB>(nrhs, (long long)gridDim.x * gridDim.y, gridDim.x, red);
+}
+
 // exp(M) for a 3x3 complex M: scaling by 2^-s until the Frobenius norm is <= 1/4, Taylor series to
 // order 14 in Horner form (the first omitted term is below 1e-20 of the identity), then s squarings
 // (Moler and Van Loan, "Nineteen dubious ways to compute the exponential of a matrix", 2003)
@@ -226,6 +261,17 @@ void launch_plaquette(const Geom& g, const void* g64, const ReduceArgs& red, cud
 void launch_flat_norm2(size_t n, const double2* v, const ReduceArgs& red, cudaStream_t st) {
   g_kernel_launches += 1;
   flat_norm2_kernel<<<(unsigned)((n + MB - 1) / MB), MB, 0, st>>>(n, v, red);
+}
+
+void launch_polyakov(const Geom& g, const void* g64, const ReduceArgs& red, cudaStream_t st) {
+  g_kernel_launches += 1;
+  polyakov_kernel<<<(g.XYZ + MB - 1) / MB, MB, 0, st>>>(g, static_cast<const double2*>(g64), red);
+}
+
+void launch_flat_redot(size_t n, int nrhs, const double2* a, const double2* b, const ReduceArgs& red,
+                       cudaStream_t st) {
+  g_kernel_launches += 1;
+  flat_redot_kernel<<<dim3((unsigned)((n + MB - 1) / MB), nrhs), MB, 0, st>>>(n, nrhs, a, b, red);
 }
 
 void launch_link_update(size_t nlinks, double eps, const double2* P, double2* U, cudaStream_t st) {

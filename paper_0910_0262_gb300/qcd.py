@@ -82,6 +82,9 @@ _SIGNATURES = {
     "qcd_update_links": (ctypes.c_int, [_P, _P, _P, ctypes.c_double]),
     "qcd_r_step": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+    "qcd_polyakov": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
+    "qcd_pbp": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -188,6 +191,20 @@ def qcd_r_step(ctx, U_ptr, P_ptr, eta_ptr, nrhs, eps, beta, flags, params, stats
     if s not in (QCD_OK, 6):
         _check(s)
     return s
+
+
+def qcd_polyakov(ctx):
+    out = (ctypes.c_double * 2)()
+    _check(lib().qcd_polyakov(ctx, out))
+    return complex(out[0], out[1])
+
+
+def qcd_pbp(ctx, eta_e_ptr, eta_o_ptr, nrhs, params, stats):
+    out = (ctypes.c_double * nrhs)()
+    s = lib().qcd_pbp(ctx, eta_e_ptr, eta_o_ptr, int(nrhs), out, ctypes.byref(params), stats)
+    if s not in (QCD_OK, 6):
+        _check(s)
+    return [out[i] for i in range(nrhs)], s
 
 
 def qcd_profile(ctx, enable):
@@ -360,6 +377,19 @@ class CloverWilson:
         s = qcd_r_step(self.ctx, _ptr(U), _ptr(P), None if eta is None else _ptr(eta), n, eps, beta,
                        QCD_FORCE_CLOVER_DET if clover_det else 0, solver_params(**kw) if n else None, st)
         return [st[i].as_dict() for i in range(n)], s == QCD_OK
+
+    def polyakov(self):
+        """Complex mean over spatial sites of tr prod_t U_t / 3 for the loaded links."""
+        return qcd_polyakov(self.ctx)
+
+    def pbp(self, eta_e, eta_o, **kw):
+        """Stochastic psi-bar psi estimates Re eta^dag M^-1 eta / (2V), one per noise vector."""
+        n = self._spinor(eta_e)
+        if self._spinor(eta_o) != n:
+            raise ValueError("eta_e and eta_o must hold the same number of fields")
+        st = (SolverStats * n)()
+        vals, s = qcd_pbp(self.ctx, _ptr(eta_e), _ptr(eta_o), n, solver_params(**kw), st)
+        return vals, [st[i].as_dict() for i in range(n)], s == QCD_OK
 
     def profile(self, enable=True):
         qcd_profile(self.ctx, enable)

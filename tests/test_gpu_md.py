@@ -6,6 +6,7 @@
   scaling-and-squaring path (1e-13);
 * one two-flavour R-algorithm step with two pseudofermions and the determinant term (links and
   momenta within 1e-9: both sides solve to 1e-12), and its reversibility for fixed noise;
+* Polyakov loop and the psi-bar psi estimate for fixed noise (1e-13; 1e-9 with solves to 1e-12);
 * leapfrog composed from the GPU calls (gauge + pseudofermion + determinant forces, link update):
   the energy error H = K + S_g + S_f + S_det, every term measured on the GPU, falls as eps^2.
 """
@@ -14,7 +15,7 @@ import numpy as np
 import pytest
 import torch
 
-from oracle import evenodd, force, md
+from oracle import evenodd, force, md, measure
 from paper_0910_0262_gb300 import synth
 from gpu_util import require_gpu, to_dev, to_np, rel_l2
 
@@ -141,3 +142,28 @@ def test_gpu_leapfrog_energy_error_is_second_order():
     c.close()
     assert dH[0] > 1e-7
     assert 3.0 < dH[0] / dH[1] < 5.5, dH
+
+
+def test_polyakov_loop(links):
+    dims, U, c = links
+    L = c.polyakov()
+    want = measure.polyakov_loop(U)
+    assert abs(L - want) <= 1e-13 * max(1.0, abs(want))
+
+
+def test_pbp_estimate_for_fixed_noise():
+    require_gpu()
+    from paper_0910_0262_gb300.qcd import CloverWilson
+    dims = (4, 2, 6, 4)
+    U, eta = synth.make_problem(dims, 0.3, 64, nrhs=6)
+    c = CloverWilson(dims, -1.0)
+    c.load_gauge(to_dev(U))
+    c.clover_build(KAPPA, CSW)
+    ee, eo = eta[:3], eta[3:]
+    vals, stats, ok = c.pbp(to_dev(ee), to_dev(eo), tol=1e-12, inner_prec=32)
+    assert ok
+    op = evenodd.SchurOperator(U, KAPPA, CSW)
+    for r in range(3):
+        want = measure.pbp(op, ee[r], eo[r])
+        assert abs(vals[r] - want) <= 1e-9 * abs(want), (r, vals[r], want)
+    c.close()
