@@ -1424,7 +1424,7 @@ qcd_status qcd_update_links(qcd_ctx* c, double* U, const double* P, double eps) 
       (const char*)P < (const char*)U + nlinks * 9 * sizeof(double2))
     return fail(QCD_ERR_ARG, "U and P overlap");
   {
-    ProfScope ps(c, "link_update", nlinks * 3 * 144.0, nlinks * 16 * 198.0);
+    ProfScope ps(c, "link_update", nlinks * 3 * 144.0, nlinks * 10 * 198.0);
     launch_link_update(nlinks, eps, reinterpret_cast<const double2*>(P), reinterpret_cast<double2*>(U), c->st);
   }
   cudaError_t e = cudaGetLastError();

@@ -174,9 +174,10 @@ __global__ void __launch_bounds__(MB) flat_redot_kernel(size_t n, int nrhs, cons
   grid_finish<MB>(nrhs, (long long)gridDim.x * gridDim.y, gridDim.x, red);
 }
 
-// exp(M) for a 3x3 complex M: scaling by 2^-s until the Frobenius norm is <= 1/4, Taylor series to
-// order 14 in Horner form (the first omitted term is below 1e-20 of the identity), then s squarings
-// (Moler and Van Loan, "Nineteen dubious ways to compute the exponential of a matrix", 2003)
+// exp(M) for a 3x3 complex M: scaling by 2^-s until the Frobenius norm r is <= 1/4, the Taylor
+// series to the lowest order n with r^(n+1)/(n+1)! <= 1e-17 (at most 12 at r = 1/4; about 8 for the
+// eps |P| of a molecular-dynamics step) in Horner form, then s squarings (Moler and Van Loan,
+// "Nineteen dubious ways to compute the exponential of a matrix", 2003)
 __device__ M3 expm3(M3 m) {
   double nrm = 0.0;
 #pragma unroll
@@ -190,12 +191,17 @@ __device__ M3 expm3(M3 m) {
   const double sc = ldexp(1.0, -s);
 #pragma unroll
   for (int k = 0; k < 9; k++) m.e[k] = cmk(sc * m.e[k].re, sc * m.e[k].im);
-  // E = I + m (I + m/2 (I + m/3 (... (I + m/14))))
+  int order = 0;
+  for (double t = 1.0; order < 20; order++) {
+    t *= nrm / (order + 1);  // r^(order+1) / (order+1)!
+    if (t <= 1e-17) break;
+  }
+  // E = I + m (I + m/2 (I + m/3 (... (I + m/order))))
   M3 e;
 #pragma unroll
   for (int k = 0; k < 9; k++) e.e[k] = cmk(0.0, 0.0);
   e.e[0] = e.e[4] = e.e[8] = cmk(1.0, 0.0);
-  for (int n = 14; n >= 1; n--) {
+  for (int n = order; n >= 1; n--) {
     M3 t = mul(m, e);
     const double f = 1.0 / n;
 #pragma unroll
