@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-hbm", action="store_true", help="skip the large-volume Dslash bandwidth measurement")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 32^3x64 8-RHS batched-mixed vs sequential-FP64 solve comparison")
+    ap.add_argument("--no-md", action="store_true",
+                    help="skip the clover-determinant, full-solve and R-algorithm sections")
     ap.add_argument("--only", default=None, choices=[None, "dslash"],
                     help="dslash: only apply Mhat^dag Mhat (FP32 and FP64) a few times, for profiler captures")
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides for --only dslash")
@@ -325,8 +327,9 @@ def run_ours(args, world, rank, local):
     result["roofline_dslash_fp32_in_solve"] = {"bound": "hbm", "achieved": d32["gbs"], "peak": hbm_peak,
                                                "unit": "GB/s", "frac": d32["gbs"] / hbm_peak,
                                                "note": "16^4 working set is L2-resident inside a solve"}
-    result["clover_det_and_full_solve"] = clover_det_section(op, x, b, stream)
-    result["r_algorithm_step"] = r_step_section(op, U, w, stream)
+    if not args.no_md:
+        result["clover_det_and_full_solve"] = clover_det_section(op, x, b, stream)
+        result["r_algorithm_step"] = r_step_section(op, U, w, stream)
     if not args.no_hbm or not args.no_batched:
         result.update(large_volume(dev, hbm_peak, not args.no_hbm, not args.no_batched))
     if not args.no_hbm:

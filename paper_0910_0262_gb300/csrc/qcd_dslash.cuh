@@ -10,6 +10,8 @@
 // DMA engine streams (Sec. 3); here it is a coalesced structure-of-arrays gather.
 #pragma once
 
+#include <type_traits>
+
 #include "qcd_internal.cuh"
 
 namespace qcd {
@@ -470,28 +472,97 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
   dslash_split_body<P, RECON, EPI>(A);
 }
 
+// y = C x for chiral block b of a clover pair decoded to FP32 in shared memory (value m of block b of
+// the site in lane at scl[(36 b + m) * 32 + lane]: 6 diagonal reals, then 15 strictly-lower complex)
+template <typename R>
+__device__ __forceinline__ void clover_apply_smem(const float* scl, int lane, int b, const cx<R> x[6], cx<R> y[6]) {
+  R d[6];
+  cx<R> L[15];
+#pragma unroll
+  for (int i = 0; i < 6; i++) d[i] = scl[(36 * b + i) * 32 + lane];
+#pragma unroll
+  for (int k = 0; k < 15; k++) L[k] = cmk(R(scl[(36 * b + 6 + 2 * k) * 32 + lane]), R(scl[(36 * b + 7 + 2 * k) * 32 + lane]));
+  hermitian6_accumulate(d, L, x, y);
+}
+
 // Hopping kernel with one thread per (site, RHS).  A block of four warps covers 32 sites (64 when
 // nrhs = 2: two site groups of two warps; 128 when nrhs = 1: four groups of one warp); warp k of a
-// site group takes RHS k, k + W, ... (W warps per group), so the warps of a block share their
-// sites' links and clover pair through L1 while each computes all eight hops and the epilogue of
-// its own RHS, with no block barrier.  Sums are reduced per warp into the partial slot of (RHS,
-// site group).
-template <int P, int RECON, int EPI>
-__global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
+// site group takes RHS k, k + W, ... (W warps per group) and computes all eight hops and the
+// epilogue of its RHS, with no block barrier.  The links and the clover pair of the block's sites
+// are the same for every RHS: with STAGED (nrhs >= 3, one site group) the block decodes them once
+// (12-real links reconstructed, FP16 converted) into shared memory; otherwise every warp reads them
+// through L1.  Sums are reduced per warp into the partial slot of (RHS, site group).
+template <int P, int RECON, int EPI, bool STAGED>
+__device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
   using R = typename Real<P>::T;
   constexpr int CP = CloverPrec<P>::CP;
   constexpr int PR = P == 64 ? 64 : 32;
   using RR = typename Real<PR>::T;
+  __shared__ cx<R> sl[STAGED ? 8 * 9 * 32 : 1];                      // [link 2 mu + bwd][element][site]
+  __shared__ float scl[(STAGED && EPI != EPI_NONE) ? 72 * 32 : 1];  // [clover value][site]
   if (A.halt && *A.halt) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int G = A.nrhs == 1 ? 4 : (A.nrhs == 2 ? 2 : 1), W = 4 / G;
+  const int G = STAGED ? 1 : (A.nrhs == 1 ? 4 : (A.nrhs == 2 ? 2 : 1)), W = 4 / G;
   const int grp = w / W, k = w - grp * W;
   const int hh = (blockIdx.x * G + grp) * 32 + lane;
   const bool valid = hh < A.g.Vh;
+  const int Vh = A.g.Vh;
+  if (STAGED) {
+    for (int it = threadIdx.x; it < 8 * 32; it += 128) {
+      const int j = it >> 5, l = it & 31, hs = blockIdx.x * 32 + l, mu = j >> 1;
+      if (hs < Vh) {
+        const Site ss = site_of(A.g, A.p, hs);
+        cx<R> u[9];
+        if ((j & 1) == 0) GaugeIO<P, RECON>::load(A.gauge, Vh, A.p, mu, ss.i >> 1, u);
+        else GaugeIO<P, RECON>::load(A.gauge, Vh, 1 - A.p, mu, neighbor_bwd(A.g, ss, mu) >> 1, u);
+#pragma unroll
+        for (int e = 0; e < 9; e++) sl[(j * 9 + e) * 32 + l] = u[e];
+      }
+    }
+    if (EPI != EPI_NONE) {
+      const int hs0 = blockIdx.x * 32;
+      if (CP == 32) {
+        const float4* q = static_cast<const float4*>(A.clover);
+        for (int it = threadIdx.x; it < 18 * 32; it += 128) {
+          const int v = it >> 5, l = it & 31;  // float4 v = 9 b + k of the pair
+          if (hs0 + l < Vh) {
+            const float4 f = __ldg(q + (size_t)v * Vh + hs0 + l);
+            const int m = 36 * (v / 9) + 4 * (v % 9);
+            scl[(m + 0) * 32 + l] = f.x;
+            scl[(m + 1) * 32 + l] = f.y;
+            scl[(m + 2) * 32 + l] = f.z;
+            scl[(m + 3) * 32 + l] = f.w;
+          }
+        }
+      } else {
+        const uint4* q = static_cast<const uint4*>(A.clover);
+        for (int it = threadIdx.x; it < 9 * 32; it += 128) {
+          const int v = it >> 5, l = it & 31;  // halves 8 v .. 8 v + 7 of the site's 72
+          if (hs0 + l < Vh) {
+            const uint4 f = __ldg(q + (size_t)v * Vh + hs0 + l);
+            const float2 a = h2f(f.x), b = h2f(f.y), c = h2f(f.z), d = h2f(f.w);
+            const int m = 8 * v;
+            scl[(m + 0) * 32 + l] = a.x;
+            scl[(m + 1) * 32 + l] = a.y;
+            scl[(m + 2) * 32 + l] = b.x;
+            scl[(m + 3) * 32 + l] = b.y;
+            scl[(m + 4) * 32 + l] = c.x;
+            scl[(m + 5) * 32 + l] = c.y;
+            scl[(m + 6) * 32 + l] = d.x;
+            scl[(m + 7) * 32 + l] = d.y;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
   Site s;
   if (valid) s = site_of(A.g, A.p, hh);
   const bool reduce = A.do_norm || EPI == EPI_XPAY_CG;
-  const int Vh = A.g.Vh;
+  auto apply_cl = [&](int b, const cx<R> x[6], cx<R> y[6]) {
+    if (STAGED) clover_apply_smem(scl, lane, b, x, y);
+    else CloverIO<CP>::apply(A.clover, Vh, hh, b, x, y);
+  };
   for (int r = k; r < A.nrhs; r += W) {
     bool act = true;
     double al = 0.0;
@@ -504,13 +575,26 @@ __global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
       cx<R> acc[12];
       {
         DirLinks<R> L;
-        load_dir<P, RECON, 0>(A, s, L);
+        auto links = [&](auto mu_c) {
+          constexpr int MU = decltype(mu_c)::value;
+          if (STAGED) {
+            dir_index<MU>(A.g, s, L);
+#pragma unroll
+            for (int e = 0; e < 9; e++) {
+              L.uf[e] = sl[((2 * MU) * 9 + e) * 32 + lane];
+              L.ub[e] = sl[((2 * MU + 1) * 9 + e) * 32 + lane];
+            }
+          } else {
+            load_dir<P, RECON, MU>(A, s, L);
+          }
+        };
+        links(std::integral_constant<int, 0>());
         hop_dir<P, 0, LD_NC, true>(A, L, r, acc);
-        load_dir<P, RECON, 1>(A, s, L);
+        links(std::integral_constant<int, 1>());
         hop_dir<P, 1, LD_NC>(A, L, r, acc);
-        load_dir<P, RECON, 2>(A, s, L);
+        links(std::integral_constant<int, 2>());
         hop_dir<P, 2, LD_NC>(A, L, r, acc);
-        load_dir<P, RECON, 3>(A, s, L);
+        links(std::integral_constant<int, 3>());
         hop_dir<P, 3, LD_NC>(A, L, r, acc);
       }
       cx<R> res[12];
@@ -523,7 +607,7 @@ __global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
 #pragma unroll
           for (int j = 0; j < 6; j++) o[j] = v[j];
         } else if (EPI == EPI_CLOVER_INV) {
-          CloverIO<CP>::apply(A.clover, Vh, hh, b, v, o);
+          apply_cl(b, v, o);
         } else {
           cx<R> xs[6], cxs[6];
           SpinorIO<P>::load_block(A.x, A.x_norm, Vh, r, hh, b, xs);
@@ -531,7 +615,7 @@ __global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
 #pragma unroll
             for (int j = 0; j < 6; j++) xs[j] = -xs[j];
           }
-          CloverIO<CP>::apply(A.clover, Vh, hh, b, xs, cxs);
+          apply_cl(b, xs, cxs);
           const R a = R(A.a);
 #pragma unroll
           for (int j = 0; j < 6; j++) {
@@ -592,6 +676,18 @@ __global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
     }
   }
   if (reduce) grid_finish<128>(A.nrhs, gridDim.x, gridDim.x * G, A.red);
+}
+
+template <int P, int RECON, int EPI, bool STAGED>
+__global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
+  dslash_site_body<P, RECON, EPI, STAGED>(A);
+}
+
+// FP16 with 1 or 2 RHS (no staging): held to 102 registers, 5 blocks per SM (the compiler's own
+// choice of 124-128 leaves 4)
+template <int RECON, int EPI>
+__global__ void __launch_bounds__(128, 5) dslash_site_fp16_kernel(DslashArgs A) {
+  dslash_site_body<16, RECON, EPI, false>(A);
 }
 
 // The single-RHS FP16 operator is bound by latency: it is held to 64 registers, so that 8 blocks
