@@ -31,12 +31,12 @@ void launch_split_fp16(int epi, const DslashArgs& a, cudaStream_t st) {
 
 template <int P, int RECON, bool STAGED>
 void launch_site_k(int epi, const DslashArgs& a, int nb, cudaStream_t st) {
-  if constexpr (P == 16 && !STAGED) {
+  if constexpr (P == 16) {
     switch (epi) {
-      case EPI_NONE: dslash_site_fp16_kernel<RECON, EPI_NONE><<<nb, 128, 0, st>>>(a); break;
-      case EPI_CLOVER_INV: dslash_site_fp16_kernel<RECON, EPI_CLOVER_INV><<<nb, 128, 0, st>>>(a); break;
-      case EPI_XPAY_CG: dslash_site_fp16_kernel<RECON, EPI_XPAY_CG><<<nb, 128, 0, st>>>(a); break;
-      default: dslash_site_fp16_kernel<RECON, EPI_XPAY><<<nb, 128, 0, st>>>(a); break;
+      case EPI_NONE: dslash_site_fp16_kernel<RECON, EPI_NONE, STAGED><<<nb, 128, 0, st>>>(a); break;
+      case EPI_CLOVER_INV: dslash_site_fp16_kernel<RECON, EPI_CLOVER_INV, STAGED><<<nb, 128, 0, st>>>(a); break;
+      case EPI_XPAY_CG: dslash_site_fp16_kernel<RECON, EPI_XPAY_CG, STAGED><<<nb, 128, 0, st>>>(a); break;
+      default: dslash_site_fp16_kernel<RECON, EPI_XPAY, STAGED><<<nb, 128, 0, st>>>(a); break;
     }
     return;
   }
@@ -54,7 +54,7 @@ void launch_site(int epi, const DslashArgs& a, cudaStream_t st) {
   const int nb = (a.g.Vh + 32 * G - 1) / (32 * G);
   // staging pays once its cost is spread over enough RHS: FP32 from 4 RHS (32^3 x 64, 8 RHS: 857 ->
   // 702 us; 48^3 x 96, 4 RHS: 2628 -> 2362 us), FP16 (cheaper links and clover to decode) from 8
-  // (8 RHS: 721 -> 691 us; 4 RHS: 1978 -> 2195 us)
+  // (48^3 x 96, 4 RHS: 1816 us unstaged, 2025 staged; 32^3 x 64, 8 RHS: 695 -> 680 us)
   if (a.nrhs >= (P == 16 ? 8 : 3)) launch_site_k<P, RECON, true>(epi, a, nb, st);
   else launch_site_k<P, RECON, false>(epi, a, nb, st);
 }

@@ -683,11 +683,10 @@ __global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
   dslash_site_body<P, RECON, EPI, STAGED>(A);
 }
 
-// FP16 with 1 or 2 RHS (no staging): held to 102 registers, 5 blocks per SM (the compiler's own
-// choice of 124-128 leaves 4)
-template <int RECON, int EPI>
+// FP16: held to 102 registers, 5 blocks per SM (the compiler's own choice of 124-128 leaves 4)
+template <int RECON, int EPI, bool STAGED>
 __global__ void __launch_bounds__(128, 5) dslash_site_fp16_kernel(DslashArgs A) {
-  dslash_site_body<16, RECON, EPI, false>(A);
+  dslash_site_body<16, RECON, EPI, STAGED>(A);
 }
 
 // The single-RHS FP16 operator is bound by latency: it is held to 64 registers, so that 8 blocks
