@@ -73,6 +73,7 @@ const int SITE_KERNEL_MIN_VH = QCD_SITE_KERNEL_MIN_VH;
 template <int P, int RECON>
 void launch_prec(int epi, const DslashArgs& a, cudaStream_t st) {
   if constexpr (P == 64) {
+    // (one thread per site measured within 7% either way: 16^4 90 vs 85 us, 32^3 x 64 2260 vs 2293 us)
     launch_split<P, RECON>(epi, a, st);
   } else {
     if (a.nrhs > 1 || a.g.Vh >= SITE_KERNEL_MIN_VH) launch_site<P, RECON>(epi, a, st);

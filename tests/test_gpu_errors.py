@@ -121,3 +121,38 @@ def test_barrier_wait_runs_out_and_context_survives(Q):
     c.clover_build(0.12, 1.0)
     x, stats, ok = c.cg_solve(to_dev(b))
     assert ok and stats[0]["true_rel_resid"] <= 1e-8
+
+
+def test_md_and_measurement_argument_and_state_errors(Q):
+    """The determinant, R-algorithm and measurement entry points check their state and arguments."""
+    dims = (4, 4, 4, 4)
+    c = Q.CloverWilson(dims)
+    L = Q.lib()
+    out2 = (ctypes.c_double * 2)()
+    assert L.qcd_clover_logdet(c.ctx, out2) == 4                 # no clover
+    assert L.qcd_polyakov(c.ctx, out2) == 4                      # no links
+    d = ctypes.c_double()
+    assert L.qcd_plaquette(c.ctx, ctypes.byref(d)) == 4
+    U, eta = synth.make_problem(dims, 0.2, 2, nrhs=9)
+    Ut = to_dev(U)
+    P = torch.zeros_like(Ut)
+    pu, pp = ctypes.c_void_p(Ut.data_ptr()), ctypes.c_void_p(P.data_ptr())
+    e = to_dev(eta)
+    pe = ctypes.c_void_p(e.data_ptr())
+    prm = Q.solver_params()
+    assert L.qcd_r_step(c.ctx, pu, pp, pe, 1, ctypes.c_double(0.01), ctypes.c_double(5.6), 0,
+                        ctypes.byref(prm), None) == 4            # no clover term yet
+    c.load_gauge(Ut)
+    c.clover_build(0.12, 1.0)
+    assert L.qcd_update_links(c.ctx, pu, pu, ctypes.c_double(0.1)) == 1          # U and P overlap
+    assert L.qcd_gauge_force(c.ctx, pp, ctypes.c_double(5.6), 0x40) == 1         # flags
+    assert L.qcd_r_step(c.ctx, pu, pp, pe, 1, ctypes.c_double(0.01), ctypes.c_double(5.6), 2,
+                        ctypes.byref(prm), None) == 1            # unknown flag
+    vals = (ctypes.c_double * 9)()
+    assert L.qcd_pbp(c.ctx, pe, pe, 9, vals, ctypes.byref(prm), None) == 1       # nrhs > 8
+    assert L.qcd_fermion_force(c.ctx, pp, None, 0, 0, None, None) == 1           # nrhs 0 without the flag
+    x = torch.zeros((1, 128, 4, 3), dtype=torch.complex128, device="cuda")
+    px = ctypes.c_void_p(x.data_ptr())
+    assert L.qcd_reconstruct_odd(c.ctx, px, px, None, 1) == 1                    # output overlaps input
+    # the context stays usable
+    assert abs(c.plaquette() - 1.0) < 0.5 and np.isfinite(c.clover_logdet()[1])
