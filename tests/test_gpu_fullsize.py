@@ -1,5 +1,6 @@
 """GPU checks at the full sizes of the workloads.
 
+8x8x16x16 (eps 0.2, seed 1): the plain FP64 solve and the full-field Mhat against the oracle.
 16^4 (kappa 0.12, c_sw 1.0, eps 0.2, seeds 2 and 3):
   * Mhat / Mhat^dag Mhat in FP64 and FP32 element by element against the whole-lattice oracle;
   * mixed FP32 and FP16 solves: true residual <= 1e-8 recomputed by the oracle;
@@ -31,6 +32,33 @@ KAPPA, CSW, TBC = synth.KAPPA, synth.CSW, synth.T_BC
 
 def true_residual_oracle(ref, x, b):
     return float(np.linalg.norm((b - ref.MdagM(x)).reshape(-1)) / np.linalg.norm(b.reshape(-1)))
+
+
+def test_c0_plain_fp64_solve_against_oracle():
+    """8x8x16x16 (eps 0.2, seed 1): plain FP64 CG to 1e-8 on the GPU; the true residual recomputed
+    by the oracle's operator, the solution against the oracle's own CG solution, and the full-field
+    Mhat in FP64 and FP32 element by element."""
+    require_gpu()
+    from paper_0910_0262_gb300 import qcd as Q
+    from paper_0910_0262_gb300.qcd import CloverWilson
+    from oracle import cg as ocg
+    w = synth.WORKLOADS["c0_8x8x16x16"]
+    U, b = synth.make_problem(w["dims"], w["eps"], w["seed"], 1)
+    ref = evenodd.SchurOperator(U, KAPPA, CSW, TBC)
+    op = CloverWilson(w["dims"], TBC)
+    op.load_gauge(to_dev(U))
+    op.clover_build(KAPPA, CSW)
+    want = ref.Mhat(b[0])
+    assert rel_l2(to_np(op.dslash(to_dev(b), Q.QCD_OP_MHAT, precision=64))[0], want) <= 1e-13
+    assert rel_l2(to_np(op.dslash(to_dev(b), Q.QCD_OP_MHAT, precision=32))[0], want) <= 1e-6
+    x, stats, ok = op.cg_solve(to_dev(b), tol=1e-8, inner_prec=64)
+    assert ok
+    x = to_np(x)[0]
+    assert true_residual_oracle(ref, x, b[0]) <= 1e-8 * (1 + 1e-6)
+    xo, iters, res = ocg.cg(ref.MdagM, b[0], tol=1e-8)
+    assert abs(stats[0]["iters"] - iters) <= 2
+    assert rel_l2(x, xo) <= 1e-6
+    op.close()
 
 
 @pytest.fixture(scope="module")
