@@ -290,11 +290,7 @@ def run_ours(args, world, rank, local):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 inner / f64 reliable",
         "data": "synthetic (seeded near-unit SU(3) links, Gaussian source)",
-        "config": {"workload": args.workload, "dims": list(dims), "nrhs": nrhs, "kappa": w["kappa"],
-                   "csw": w["csw"], "eps": w["eps"], "seed": w["seed"], "tol": 1e-8,
-                   "inner": "fp32, 12-real links, reliable update every 50 its or 0.1 drop",
-                   "l2": "flushed (256 MiB write) before every step, outside the step's events",
-                   "parallelism": f"replicas x{world}"},
+        "config": step_config(args.workload, w, world),
         "parts_ms": {"load_gauge": float(np.mean(parts[:, 0])), "clover_build": float(np.mean(parts[:, 1])),
                      "cg_solve_mixed": solve_mixed, "fermion_force": float(np.mean(parts[:, 3]))},
         "solve": {"mixed_ms": solve_mixed, "fp64_ms": solve64, "speedup_mixed_vs_fp64": None if solve64 is None else solve64 / solve_mixed,
@@ -344,8 +340,9 @@ def run_ours(args, world, rank, local):
 
 def r_step_section(op, U, w, stream, warmup=2, reps=5, eps=0.02, beta=5.6):
     """One two-flavour R-algorithm step on the step's lattice (one pseudofermion, determinant term,
-    mixed FP32 solve to 1e-8): device time (CUDA events, median of `reps`) and its kernel classes
-    from one profiled step; momenta and noise drawn on the host with numpy (seeded)."""
+    mixed FP32 solve to 1e-8), as a step of a trajectory (the clover term of the new links is left to
+    the next step): device time (CUDA events, median of `reps`) and its kernel classes from one
+    profiled step; momenta and noise drawn on the host with numpy (seeded)."""
     import torch
     from paper_0910_0262_gb300 import synth
     rng = np.random.default_rng(71)
@@ -360,7 +357,7 @@ def r_step_section(op, U, w, stream, warmup=2, reps=5, eps=0.02, beta=5.6):
         if k == warmup:
             op.profile(True)
         e0.record(stream)
-        st, ok = op.r_step(Ut, P, eta, eps, beta, clover_det=True, **kw)
+        st, ok = op.r_step(Ut, P, eta, eps, beta, clover_det=True, defer_clover=True, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         if k == warmup:
@@ -587,6 +584,15 @@ def cpu_baseline(w, gpu_iters, cg_sample_iters=4):
                       f"{gpu_iters} iterations of the solve), force once; numpy FP64, one thread"}
 
 
+def step_config(name, w, world):
+    """The workload of one hot-path step (the same dict in both arms)."""
+    return {"workload": name, "dims": list(w["dims"]), "nrhs": w["nrhs"], "kappa": w["kappa"],
+            "csw": w["csw"], "eps": w["eps"], "seed": w["seed"], "tol": 1e-8,
+            "inner": "fp32, 12-real links, reliable update every 50 its or 0.1 drop",
+            "l2": "flushed (256 MiB write) before every step, outside the step's events",
+            "parallelism": f"replicas x{world}"}
+
+
 # -------------------------------------------------------------- reference --
 def run_reference(args, world, rank):
     """The oracle arm: each step is a bounded sample of the same workload on the host cores."""
@@ -600,7 +606,7 @@ def run_reference(args, world, rank):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": r["unit"], "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "dims": list(w["dims"])},
+            "config": step_config(args.workload, w, world),
             "cpu_baseline": {"value": v, "unit": r["unit"], "cores": 1, "kind": "oracle",
                              "sample": r["sample"]},
             "e2e": {"value": v, "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

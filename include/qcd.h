@@ -96,6 +96,7 @@ typedef struct {
 #define QCD_FORCE_GRADIENT 2          /* write G = dS/dRe U + i dS/dIm U instead of the Lie-algebra force */
 #define QCD_FORCE_CLOVER_DET 4        /* add the force of S_det = -2 sum_{x odd} log det A(x) */
 #define QCD_FORCE_ACCUMULATE 8        /* qcd_gauge_force: add to F instead of overwriting it */
+#define QCD_R_STEP_DEFER_CLOVER 16    /* qcd_r_step: leave the clover term of the new links unbuilt */
 
 /*
  * Create a context for a lattice of extents dims = {X, Y, Z, T}; all must be
@@ -217,7 +218,9 @@ qcd_status qcd_reconstruct_odd(qcd_ctx* ctx, double* x_o, const double* x_e, con
  *   eps (1 - N_f/2)/2 vanishes for the two flavours Mhat^dag Mhat describes).  kappa and c_sw are
  *   those of the last qcd_clover_build; flags: QCD_FORCE_CLOVER_DET adds the determinant term.
  *   params/stats as in qcd_fermion_force.  On return the context holds U's packed links and clover
- *   term.  Synchronises.
+ *   term; with QCD_R_STEP_DEFER_CLOVER the clover term is left unbuilt (operators return
+ *   QCD_ERR_STATE until qcd_clover_build; another qcd_r_step needs no rebuild), which saves one
+ *   clover build per step of a trajectory.  Synchronises.
  * All return QCD_ERR_STATE without loaded links (qcd_r_step: without a clover term).
  */
 qcd_status qcd_gauge_force(qcd_ctx* ctx, double* F, double beta, int flags);

@@ -127,6 +127,7 @@ struct qcd_ctx {
   void* Ainv16 = nullptr;
   double* logdet = nullptr;  // [parity][block][Vh] log det of each clover block
   bool have_clover = false;
+  bool have_kappa = false;  // kappa and c_sw of a clover_build are known (the term may be stale)
   double kappa = 0, csw = 0;
   // device status words: [0] clover not positive definite, [1] non-finite input
   int* flags = nullptr;
@@ -614,6 +615,7 @@ qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
   c->kappa = kappa;
   c->csw = csw;
   c->have_clover = true;
+  c->have_kappa = true;
   return QCD_OK;
 }
 
@@ -1438,8 +1440,8 @@ qcd_status qcd_r_step(qcd_ctx* c, double* U, double* P, const double* eta, int n
   if (s) return s;
   if (!U || !P || (!eta && nrhs > 0)) return fail(QCD_ERR_ARG, "null pointer");
   if (nrhs < 0) return fail(QCD_ERR_ARG, "nrhs must be >= 0");
-  if (flags & ~QCD_FORCE_CLOVER_DET) return fail(QCD_ERR_ARG, "unknown r_step flags");
-  if (!c->have_clover) return fail(QCD_ERR_STATE, "r_step needs a clover term (kappa, c_sw)");
+  if (flags & ~(QCD_FORCE_CLOVER_DET | QCD_R_STEP_DEFER_CLOVER)) return fail(QCD_ERR_ARG, "unknown r_step flags");
+  if (!c->have_kappa) return fail(QCD_ERR_STATE, "r_step needs kappa and c_sw from a clover_build");
   if (nrhs > 0 && (s = check_params(prm))) return s;
   const Geom& g = c->g;
   const double kappa = c->kappa, csw = c->csw;
@@ -1467,7 +1469,8 @@ qcd_status qcd_r_step(qcd_ctx* c, double* U, double* P, const double* eta, int n
   // P -= eps F, then the second half step
   launch_axpby(nlinks * 9, -eps, reinterpret_cast<const double2*>(F), 1.0, reinterpret_cast<double2*>(P), c->st);
   if ((s = qcd_update_links(c, U, P, 0.5 * eps))) return s;
-  if ((s = qcd_load_gauge(c, U, 1, gflags)) || (s = qcd_clover_build(c, kappa, csw))) return s;
+  if ((s = qcd_load_gauge(c, U, 1, gflags))) return s;
+  if (!(flags & QCD_R_STEP_DEFER_CLOVER) && (s = qcd_clover_build(c, kappa, csw))) return s;
   return solve_status;
 }
 

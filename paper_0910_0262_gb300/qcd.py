@@ -29,6 +29,7 @@ QCD_FORCE_INPUT_IS_SOLUTION = 1
 QCD_FORCE_GRADIENT = 2
 QCD_FORCE_CLOVER_DET = 4
 QCD_FORCE_ACCUMULATE = 8
+QCD_R_STEP_DEFER_CLOVER = 16
 
 
 class SolverParams(ctypes.Structure):
@@ -368,14 +369,16 @@ class CloverWilson:
         qcd_update_links(self.ctx, _ptr(U), _ptr(P), eps)
         return U
 
-    def r_step(self, U, P, eta, eps, beta, clover_det=True, **kw):
-        """One two-flavour R-algorithm step on U and P in place (noise eta [n, V/2, 4, 3] or None)."""
+    def r_step(self, U, P, eta, eps, beta, clover_det=True, defer_clover=False, **kw):
+        """One two-flavour R-algorithm step on U and P in place (noise eta [n, V/2, 4, 3] or None);
+        defer_clover leaves the new links' clover term unbuilt (for the steps of a trajectory)."""
         self._links(U)
         self._links(P)
         n = 0 if eta is None else self._spinor(eta)
         st = (SolverStats * max(n, 1))()
+        flags = (QCD_FORCE_CLOVER_DET if clover_det else 0) | (QCD_R_STEP_DEFER_CLOVER if defer_clover else 0)
         s = qcd_r_step(self.ctx, _ptr(U), _ptr(P), None if eta is None else _ptr(eta), n, eps, beta,
-                       QCD_FORCE_CLOVER_DET if clover_det else 0, solver_params(**kw) if n else None, st)
+                       flags, solver_params(**kw) if n else None, st)
         return [st[i].as_dict() for i in range(n)], s == QCD_OK
 
     def polyakov(self):

@@ -91,8 +91,15 @@ def test_r_step_matches_oracle_and_is_reversible():
     assert rel_l2(to_np(Pt), P1) <= 1e-9
     assert abs(c.plaquette() - md.mean_plaquette(U1)) <= 1e-9
     Pt.neg_()
-    c.r_step(Ut, Pt, to_dev(eta), 0.05, BETA, clover_det=True, tol=1e-12, inner_prec=64)
+    c.r_step(Ut, Pt, to_dev(eta), 0.05, BETA, clover_det=True, defer_clover=True, tol=1e-12, inner_prec=64)
     assert rel_l2(to_np(Ut), U) <= 1e-9 and rel_l2(-to_np(Pt), P) <= 1e-9
+    # with the clover term deferred the operators wait for clover_build; a further step does not
+    from paper_0910_0262_gb300 import qcd as Q
+    with pytest.raises(Q.QCDError) as e:
+        c.clover_logdet()
+    assert e.value.status == 4
+    stats, ok = c.r_step(Ut, Pt, to_dev(eta), 0.05, BETA, tol=1e-12, inner_prec=64)
+    assert ok and np.isfinite(c.clover_logdet()[1])
     c.close()
 
 
