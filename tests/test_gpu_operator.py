@@ -4,8 +4,10 @@ Every op of qcd_dslash (D_eo, D_oe and their adjoints, Mhat, Mhat^dag,
 Mhat^dag Mhat, A_ee, A_oo^-1) in FP64, FP32 and FP16, with 18- and 12-real link
 storage, on lattices whose half volume leaves a ragged last thread block
 (432 and 96 sites per parity: the 32-site blocks of the single-RHS kernels end
-ragged at 432, the 64-site blocks of the 2-RHS kernel at 96), with 3
-right-hand sides (a batch of 2 plus a batch of 1) and with 13 (8 + 4 + 1).
+ragged at 432, the 64-site blocks of the 2-RHS kernel at 96), on the degenerate
+extent-2 lattices where the forward and backward neighbours coincide (8 and 48
+sites per parity: a single partial block), with 3 right-hand sides (a batch of
+2 plus a batch of 1) and with 13 (8 + 4 + 1).
 
 Tolerances (relative L2 per field): FP64 1e-13 and FP32 1e-6 (the targets of
 the method's statement); FP16 with per-site norms is stated, gated at 5e-3.
@@ -25,7 +27,8 @@ TOL = {64: 1e-13, 32: 1e-6, 16: 5e-3}
 NRHS = 3
 
 
-@pytest.fixture(scope="module", params=[(6, 6, 4, 6), (4, 2, 6, 4)], ids=["6x6x4x6", "4x2x6x4"])
+@pytest.fixture(scope="module", params=[(6, 6, 4, 6), (4, 2, 6, 4), (2, 2, 2, 2), (2, 4, 2, 6)],
+                ids=["6x6x4x6", "4x2x6x4", "2x2x2x2", "2x4x2x6"])
 def lattice(request):
     require_gpu()
     from paper_0910_0262_gb300.qcd import CloverWilson
