@@ -70,54 +70,59 @@ __device__ M3 field_strength(const Geom& g, const double2* g64, const int c[4], 
   return F;
 }
 
-__device__ __forceinline__ int tri(int i, int j) { return i * (i - 1) / 2 + j; }
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i - 1) / 2 + j; }
 
-// Cholesky-based inverse of a Hermitian positive definite 6x6 matrix given as
-// (diag d, strictly-lower L), and log det = sum_j log L_jj^2.  Returns false on a non-positive pivot.
-__device__ bool invert6(const double d[6], const C L[15], double di[6], C Li[15], double* logdet) {
-  C a[6][6];
-  for (int i = 0; i < 6; i++) {
-    a[i][i] = cmk(d[i], 0.0);
-    for (int j = 0; j < i; j++) {
-      a[i][j] = L[tri(i, j)];
-      a[j][i] = conj(L[tri(i, j)]);
-    }
-  }
-  C l[6][6];
-  double ild[6];  // 1 / L_jj: one division per pivot, multiplications elsewhere
+// Cholesky-based inverse of a Hermitian positive definite 6x6 matrix given as (diag d,
+// strictly-lower L), and log det = sum_j log L_jj^2.  Returns false on a non-positive pivot.  All
+// loops are unrolled, so the packed triangles stay in registers: A = l l^dag (l lower, diagonal ld),
+// m = l^-1 (lower), A^-1 = m^dag m.
+__device__ __forceinline__ bool invert6(const double d[6], const C L[15], double di[6], C Li[15], double* logdet) {
+  double ild[6];  // 1 / l_jj: one division per pivot, multiplications elsewhere
+  C lo[15];       // strictly-lower part of l
   double ldet = 0.0;
+  bool ok = true;
+#pragma unroll
   for (int j = 0; j < 6; j++) {
-    double s = a[j][j].re;
-    for (int k = 0; k < j; k++) s -= norm2(l[j][k]);
-    if (!(s > 0.0)) return false;
+    double s = d[j];
+#pragma unroll
+    for (int k = 0; k < j; k++) s -= norm2(lo[tri(j, k)]);
+    ok = ok && s > 0.0;
+    s = s > 0.0 ? s : 1.0;  // keeps the arithmetic finite; the result is discarded when !ok
     ldet += log(s);
-    const double ld = sqrt(s);
-    ild[j] = 1.0 / ld;
-    l[j][j] = cmk(ld, 0.0);
+    ild[j] = 1.0 / sqrt(s);
+#pragma unroll
     for (int i = j + 1; i < 6; i++) {
-      C v = a[i][j];
-      for (int k = 0; k < j; k++) v = v - l[i][k] * conj(l[j][k]);
-      l[i][j] = cmk(v.re * ild[j], v.im * ild[j]);
+      C v = L[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; k++) v = v - lo[tri(i, k)] * conj(lo[tri(j, k)]);
+      lo[tri(i, j)] = cmk(v.re * ild[j], v.im * ild[j]);
     }
   }
-  // m = L^-1 (lower triangular)
-  C m[6][6];
-  for (int j = 0; j < 6; j++) {
-    for (int i = 0; i < j; i++) m[i][j] = cmk(0.0, 0.0);
-    m[j][j] = cmk(ild[j], 0.0);
+  if (!ok) return false;
+  // m = l^-1: m_jj = 1 / l_jj, m_ij = -(sum_{k=j}^{i-1} l_ik m_kj) / l_ii for i > j
+  C mo[15];
+#pragma unroll
+  for (int j = 0; j < 6; j++)
+#pragma unroll
     for (int i = j + 1; i < 6; i++) {
-      C s = cmk(0.0, 0.0);
-      for (int k = j; k < i; k++) s = s + l[i][k] * m[k][j];
-      m[i][j] = cmk(-s.re * ild[i], -s.im * ild[i]);
+      C s = cmk(lo[tri(i, j)].re * ild[j], lo[tri(i, j)].im * ild[j]);
+#pragma unroll
+      for (int k = j + 1; k < i; k++) s = cfma(lo[tri(i, k)], mo[tri(k, j)], s);
+      mo[tri(i, j)] = cmk(-s.re * ild[i], -s.im * ild[i]);
     }
-  }
-  // A^-1 = m^dag m
+  // A^-1 = m^dag m: (A^-1)_ij = sum_{k >= i} conj(m_ki) m_kj for i >= j
+#pragma unroll
   for (int i = 0; i < 6; i++) {
-    for (int j = 0; j <= i; j++) {
-      C s = cmk(0.0, 0.0);
-      for (int k = i; k < 6; k++) s = cfmac(m[k][i], m[k][j], s);
-      if (i == j) di[i] = s.re;
-      else Li[tri(i, j)] = s;
+    double sd = ild[i] * ild[i];
+#pragma unroll
+    for (int k = i + 1; k < 6; k++) sd += norm2(mo[tri(k, i)]);
+    di[i] = sd;
+#pragma unroll
+    for (int j = 0; j < i; j++) {
+      C s = cmk(ild[i] * mo[tri(i, j)].re, ild[i] * mo[tri(i, j)].im);  // k = i: m_ii m_ij
+#pragma unroll
+      for (int k = i + 1; k < 6; k++) s = cfmac(mo[tri(k, i)], mo[tri(k, j)], s);
+      Li[tri(i, j)] = s;
     }
   }
   *logdet = ldet;
@@ -126,35 +131,44 @@ __device__ bool invert6(const double d[6], const C L[15], double di[6], C Li[15]
 
 __device__ __forceinline__ void store_block64(double2* base, int Vh, int h, int b, const double d[6], const C L[15]) {
   double2* q = base + (size_t)(b * 18) * Vh + h;
+#pragma unroll
   for (int k = 0; k < 3; k++) q[(size_t)k * Vh] = make_double2(d[2 * k], d[2 * k + 1]);
+#pragma unroll
   for (int k = 0; k < 15; k++) q[(size_t)(3 + k) * Vh] = make_double2(L[k].re, L[k].im);
 }
 
-__device__ __forceinline__ void store_block32(float4* base, int Vh, int h, int b, const double d[6], const C L[15]) {
-  float f[36];
-  for (int k = 0; k < 6; k++) f[k] = (float)d[k];
-  for (int k = 0; k < 15; k++) {
-    f[6 + 2 * k] = (float)L[k].re;
-    f[7 + 2 * k] = (float)L[k].im;
-  }
-  float4* q = base + (size_t)(b * 9) * Vh + h;
-  for (int k = 0; k < 9; k++) q[(size_t)k * Vh] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+// the 36 values of a block in storage order: 6 diagonal reals, then the 15 lower entries re, im
+__device__ __forceinline__ double block_value(const double d[6], const C L[15], int k) {
+  return k < 6 ? d[k] : ((k & 1) ? L[(k - 7) / 2].im : L[(k - 6) / 2].re);
 }
 
-// 36 halves of block b at halves [36b, 36b+36) of the site's 72 ([9][Vh] uint4 layout)
+__device__ __forceinline__ void store_block32(float4* base, int Vh, int h, int b, const double d[6], const C L[15]) {
+  float4* q = base + (size_t)(b * 9) * Vh + h;
+#pragma unroll
+  for (int k = 0; k < 9; k++)
+    q[(size_t)k * Vh] = make_float4((float)block_value(d, L, 4 * k), (float)block_value(d, L, 4 * k + 1),
+                                    (float)block_value(d, L, 4 * k + 2), (float)block_value(d, L, 4 * k + 3));
+}
+
+// 36 halves of block B at halves [36B, 36B+36) of the site's 72 ([9][Vh] uint4 layout): four whole
+// uint4 and one half of the uint4 the two blocks share (its low 8 bytes for block 0, high for 1)
+template <int B>
+__device__ __forceinline__ void store_block16_b(uint4* base, int Vh, int h, const double d[6], const C L[15]) {
+  auto pack = [&](int k) { return f2h((float)block_value(d, L, k), (float)block_value(d, L, k + 1)); };
+  constexpr int w0 = B == 0 ? 0 : 5;  // first whole uint4 of the block
+  constexpr int k0 = B == 0 ? 0 : 4;  // block value stored at its start
+#pragma unroll
+  for (int w = 0; w < 4; w++) {
+    const int k = k0 + 8 * w;
+    base[(size_t)(w0 + w) * Vh + h] = make_uint4(pack(k), pack(k + 2), pack(k + 4), pack(k + 6));
+  }
+  constexpr int ks = B == 0 ? 32 : 0;  // the four values in the shared uint4 4
+  *(reinterpret_cast<uint2*>(base + (size_t)4 * Vh + h) + B) = make_uint2(pack(ks), pack(ks + 2));
+}
+
 __device__ __forceinline__ void store_block16(uint4* base, int Vh, int h, int b, const double d[6], const C L[15]) {
-  uint16_t* q = reinterpret_cast<uint16_t*>(base);
-  float f[36];
-  for (int k = 0; k < 6; k++) f[k] = (float)d[k];
-  for (int k = 0; k < 15; k++) {
-    f[6 + 2 * k] = (float)L[k].re;
-    f[7 + 2 * k] = (float)L[k].im;
-  }
-  for (int k = 0; k < 36; k++) {
-    const int j = 36 * b + k;  // half index within the site
-    __half hv = __float2half_rn(f[k]);
-    q[((size_t)(j >> 3) * Vh + h) * 8 + (j & 7)] = *reinterpret_cast<uint16_t*>(&hv);
-  }
+  if (b == 0) store_block16_b<0>(base, Vh, h, d, L);
+  else store_block16_b<1>(base, Vh, h, d, L);
 }
 
 // F_{mu nu} for one (site, plane) per thread into Fbuf[plane][9][V] (V = all sites, lexicographic)
@@ -192,6 +206,7 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const doub
   // planes xy xz xt yz yt zt = 0..5
   const double sg = b == 0 ? -1.0 : 1.0;
   C B1[9], B2[9], B3[9];
+#pragma unroll
   for (int e = 0; e < 9; e++) {
     B1[e] = Fe(3, e) + sg * Fe(2, e);
     B2[e] = Fe(1, e) - sg * Fe(4, e);
@@ -200,9 +215,11 @@ __global__ void __launch_bounds__(128) clover_assemble_kernel(Geom g, const doub
   const double kc = kappa * csw;
   double d[6];
   C L[15];
+#pragma unroll
   for (int ii6 = 0; ii6 < 6; ii6++) {
     const int ii = ii6 % 3;
     d[ii6] = 1.0 - kc * (ii6 < 3 ? B3[4 * ii].re : -B3[4 * ii].re);
+#pragma unroll
     for (int j = 0; j < ii6; j++) {
       const int jj = j % 3;
       C hv;
