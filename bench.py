@@ -272,7 +272,8 @@ def run_ours(args, world, rank, local):
     total_launches = next((p["launches"] for p in prof if p["name"] == "launches_total"), None)
     # per-step device time of each kernel class: sampled average duration x launches per step
     per_step_launches = {"dslash_p32": 4 * iters, "dslash_p64": 4 * max(stats[0].reliable_updates, 0),
-                         "force_links": 1, "force_clover_coeff": 1, "clover_build": 1, "cg_update": iters,
+                         "force_links": 1, "force_edges": 1, "force_clover_coeff": 1, "clover_build": 1,
+                         "cg_update": iters,
                          "p_update": iters}
     classes = {}
     for key, n in per_step_launches.items():

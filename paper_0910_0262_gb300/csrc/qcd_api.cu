@@ -50,7 +50,7 @@ enum Slot {
   S_B_HI, S_X_HI, S_AP_HI, S_T_HI, S_Y_HI,               // FP64 solver fields
   S_X_LO, S_R_LO, S_P, S_AP, S_TL, S_YL,                 // inner solver fields
   S_X_LO_N, S_R_LO_N, S_P_N, S_AP_N, S_TL_N, S_YL_N,
-  S_F_X, S_F_Y, S_F_CL,                                  // force work fields
+  S_F_X, S_F_Y, S_F_CL, S_F_E,                           // force work fields
   S_MD_F, S_MD_PHI,                                      // R-algorithm step
   S_PBP,                                                 // psi-bar psi estimate
   S_COUNT
@@ -1197,8 +1197,14 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
       launch_force_det_coeff(g, c->kappa, c->csw, static_cast<const double2*>(clover_ptr(c, 64, true, 1)),
                              static_cast<double2*>(clf), c->st);
     }
-    ProfScope ps(c, "force_links", 4 * V * 504.0, 4 * V * force_link_flops(0, true));
-    launch_force_links(g, c->kappa, 0, c->g64, nullptr, nullptr, nullptr, nullptr, static_cast<const double2*>(clf),
+    void* ef;
+    if ((s = ws_get(c, S_F_E, force_edge_bytes(g), &ef))) return s;
+    {
+      ProfScope ps(c, "force_edges", V * (6 + 4 + 12) * 144.0, V * force_edge_flops());
+      launch_force_edges(g, c->g64, static_cast<const double2*>(clf), static_cast<double2*>(ef), c->st);
+    }
+    ProfScope ps(c, "force_links", 4 * V * (144.0 + 3 * 144.0 + 144.0), 4 * V * force_link_flops(0, true));
+    launch_force_links(g, c->kappa, 0, c->g64, nullptr, nullptr, nullptr, nullptr, static_cast<const double2*>(ef),
                        reinterpret_cast<double2*>(F), (flags & QCD_FORCE_GRADIENT) != 0, true, false, c->st);
     return sync_and_check(c, "fermion_force");
   }
@@ -1218,9 +1224,9 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
   }
   // native FP64 X_e, Y_e = Mhat X_e, X_o = A^-1 D_oe X_e, Y_o = g5 A^-1 D_oe g5 Y_e; batches of <= 8 RHS
   const size_t hi1 = spinor_bytes(g, 64, 1);
-  void *xf, *yf, *clf;
+  void *xf, *yf, *clf, *ef;
   if ((s = ws_get(c, S_F_X, 2 * hi1 * nrhs, &xf)) || (s = ws_get(c, S_F_Y, 2 * hi1 * nrhs, &yf)) ||
-      (s = ws_get(c, S_F_CL, force_clover_bytes(g), &clf)))
+      (s = ws_get(c, S_F_CL, force_clover_bytes(g), &clf)) || (s = ws_get(c, S_F_E, force_edge_bytes(g), &ef)))
     return s;
   double2* Xe = static_cast<double2*>(xf);
   double2* Xo = Xe + (size_t)nrhs * 12 * g.Vh;
@@ -1258,13 +1264,20 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
     launch_force_det_coeff(g, c->kappa, c->csw, static_cast<const double2*>(clover_ptr(c, 64, true, 1)),
                            static_cast<double2*>(clf), c->st);
   }
+  {
+    ProfScope ps(c, "force_edges", V * (6 + 4 + 12) * 144.0, V * force_edge_flops());
+    launch_force_edges(g, c->g64, static_cast<const double2*>(clf), static_cast<double2*>(ef), c->st);
+  }
   // per link: the hopping part of every batch, the clover part once (F is linear in G)
   for (size_t k = 0; k < batches.size(); k++) {
     const size_t off = batches[k].first;
     const int nb = batches[k].second;
-    ProfScope ps(c, "force_links", 4 * V * (504.0 + 96.0 * nb), 4 * V * force_link_flops(nb, k == 0));
+    // compulsory bytes per link: the link, its share of the E fields (three per link), the output,
+    // and a quarter of each site's four FP64 spinors per RHS
+    ProfScope ps(c, "force_links", 4 * V * (144.0 + (k == 0 ? 3 * 144.0 : 0.0) + 144.0 + 192.0 * nb),
+                 4 * V * force_link_flops(nb, k == 0));
     launch_force_links(g, c->kappa, nb, c->g64, Xe + off, Xo + off, Ye + off, Yo + off,
-                       static_cast<const double2*>(clf), reinterpret_cast<double2*>(F),
+                       static_cast<const double2*>(ef), reinterpret_cast<double2*>(F),
                        (flags & QCD_FORCE_GRADIENT) != 0, k == 0, k > 0, c->st);
   }
   return sync_and_check(c, "fermion_force");

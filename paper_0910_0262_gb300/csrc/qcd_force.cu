@@ -13,14 +13,20 @@
 //  1. clover_coeff: per site and plane, C_{mu nu}(x) = -i (kappa c_sw / 4)(S + S^dag)
 //     with S the traceless part of sum_s [sigma_{mu nu} X(x)]_s W(x)_s^dag (summed
 //     over right-hand sides).
-//  2. link_force: per link, the hopping term and the clover leaves through it.
+//  2. edge_insert: per link and plane containing it, the two corner insertions next
+//     to the link, E = C(x) U_mu(x) + U_mu(x) C(x+mu).
+//  3. link_force: per link, the hopping term and the clover leaves through it.
 //     A link l sits in two plaquettes of each of its three planes; each plaquette
 //     contributes one leaf at each of its four corners, and every such leaf is a
 //     cyclic rotation l s1 s2 s3 of the plaquette.  The four corner terms of one
 //     plaquette sum to the staple s1 s2 s3 with the corner's C inserted at each
-//     corner:  c0 s1 s2 s3 + s1 c1 s2 s3 + s1 s2 c2 s3 + s1 s2 s3 c3.
+//     corner:  c0 s1 s2 s3 + s1 c1 s2 s3 + s1 s2 c2 s3 + s1 s2 s3 c3
+//            = (c0 s1 + s1 c1) s2 s3 + s1 s2 (c2 s3 + s3 c3),
+//     and each bracket is the E of s1 or s3 from kernel 2 (for a link walked
+//     backwards, s = U^dag, the bracket is -E^dag because C^dag = -C): four
+//     products per plaquette instead of eight.
 //     The result is either G or F = -1/2 P_TA(U G^dag).
-//  3. det_coeff (optional): the clover determinant term's coefficients, added to C before 2.
+//  4. det_coeff (optional): the clover determinant term's coefficients, added to C before 2.
 #include "qcd_dslash.cuh"
 #include "qcd_force.h"
 #include "qcd_su3.cuh"
@@ -245,19 +251,41 @@ __global__ void __launch_bounds__(FB) det_coeff_kernel(Geom g, double kappa, dou
   }
 }
 
-// c0 s1 s2 s3 + s1 c1 s2 s3 + s1 s2 c2 s3 + s1 s2 s3 c3
-__device__ __forceinline__ M3 corner_staple(const M3& s1, const M3& s2, const M3& s3, const M3& c0, const M3& c1,
-                                           const M3& c2, const M3& c3) {
-  const M3 s23 = mul(s2, s3);
-  const M3 q3 = m3_add(mul(c2, s3), mul(s3, c3));
-  const M3 q2 = m3_add(mul(c1, s23), mul(s2, q3));
-  return m3_add(mul(c0, mul(s1, s23)), mul(s1, q2));
+// 2. per site x and plane (mu, nu): E of U_mu(x) into field 2 pl, E of U_nu(x) into field 2 pl + 1
+__global__ void __launch_bounds__(FB) edge_insert_kernel(Geom g, const double2* g64, const double2* Cbuf,
+                                                         double2* Ebuf) {
+  const int V = 2 * g.Vh;
+  const long long tid = (long long)blockIdx.x * FB + threadIdx.x;
+  if (tid >= 6LL * V) return;
+  const int pl = (int)(tid / V), i = (int)(tid - (long long)pl * V);
+  int mu, nu;
+  plane_dirs(pl, mu, nu);
+  int c[4];
+  lex_coords(g, i, c);
+  const M3 C0 = load_m3(Cbuf, pl, V, i);
+  int q[4] = {c[0], c[1], c[2], c[3]};
+  q[mu] += 1;
+  M3 U = link_at(g, g64, c[0], c[1], c[2], c[3], mu);
+  M3 Cn = load_m3(Cbuf, pl, V, lex_index(g, q[0], q[1], q[2], q[3]));
+  store_m3(Ebuf, 2 * pl, V, i, m3_add(mul(C0, U), mul(U, Cn)));
+  q[mu] -= 1;
+  q[nu] += 1;
+  U = link_at(g, g64, c[0], c[1], c[2], c[3], nu);
+  Cn = load_m3(Cbuf, pl, V, lex_index(g, q[0], q[1], q[2], q[3]));
+  store_m3(Ebuf, 2 * pl + 1, V, i, m3_add(mul(C0, U), mul(U, Cn)));
 }
 
-// 2. per link (y, lambda): hopping term + the clover leaves through the link
+__device__ __forceinline__ M3 m3_sub(const M3& a, const M3& b) {
+  M3 c;
+#pragma unroll
+  for (int k = 0; k < 9; k++) c.e[k] = a.e[k] - b.e[k];
+  return c;
+}
+
+// 3. per link (y, lambda): hopping term + the clover leaves through the link
 __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, int nrhs, const double2* g64,
                                                         const double2* Xe, const double2* Xo, const double2* Ye,
-                                                        const double2* Yo, const double2* Cbuf, double2* out,
+                                                        const double2* Yo, const double2* Ebuf, double2* out,
                                                         int gradient, int with_clover, int accumulate) {
   const int V = 2 * g.Vh;
   const long long tid = (long long)blockIdx.x * FB + threadIdx.x;
@@ -290,7 +318,7 @@ __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, in
     }
   }
   M3 G = m3_add(m3_dag(Ah), Bh);
-  // clover part: the two plaquettes of each plane containing lambda
+  // clover part: the two plaquettes of each plane containing lambda, each as E s2 s3 + s1 s2 E'
   auto site_off = [&](int d1, int s1, int d2, int s2) {
     int q[4] = {c[0], c[1], c[2], c[3]};
     q[d1] += s1;
@@ -307,25 +335,36 @@ __global__ void __launch_bounds__(FB) link_force_kernel(Geom g, double kappa, in
     int mu, nu;
     plane_dirs(pl, mu, nu);
     if (mu != lam && nu != lam) continue;
-    auto Cat = [&](int dm, int dn) { return load_m3(Cbuf, pl, V, site_off(mu, dm, nu, dn)); };
     if (lam == mu) {
-      // plaquette at y: U_mu(y) U_nu(y+mu) U_mu(y+nu)^dag U_nu(y)^dag
-      M3 T = corner_staple(link_off(mu, 1, nu, 0, nu), m3_dag(link_off(mu, 0, nu, 1, mu)),
-                           m3_dag(link_off(mu, 0, nu, 0, nu)), Cat(1, 0), Cat(1, 1), Cat(0, 1), Cat(0, 0));
-      G = m3_add(G, m3_dag(T));
-      // plaquette at y-nu, where the link enters daggered: staple U_nu(y-nu)^dag U_mu(y-nu) U_nu(y+mu-nu)
-      T = corner_staple(m3_dag(link_off(mu, 0, nu, -1, nu)), link_off(mu, 0, nu, -1, mu), link_off(mu, 1, nu, -1, nu),
-                        Cat(0, 0), Cat(0, -1), Cat(1, -1), Cat(1, 0));
-      G = m3_add(G, T);
+      // E of the nu links of the plane
+      auto Eat = [&](int dm, int dn) { return load_m3(Ebuf, 2 * pl + 1, V, site_off(mu, dm, nu, dn)); };
+      // plaquette at y: s1 = U_nu(y+mu), s2 = A^dag, s3 = B^dag with A = U_mu(y+nu), B = U_nu(y);
+      // T = E_nu(y+mu) s2 s3 - s1 s2 E_nu(y)^dag and G += T^dag = (B A) E_nu(y+mu)^dag - E_nu(y) (A s1^dag)
+      {
+        const M3 A = link_off(mu, 0, nu, 1, mu), B = link_off(mu, 0, nu, 0, nu), s1 = link_off(mu, 1, nu, 0, nu);
+        G = m3_add(G, m3_sub(mul_nd(mul(B, A), Eat(1, 0)), mul(Eat(0, 0), mul_nd(A, s1))));
+      }
+      // plaquette at y-nu (the link enters daggered): s1 = D^dag, s2 = P, s3 = Q with D = U_nu(y-nu),
+      // P = U_mu(y-nu), Q = U_nu(y+mu-nu); G += -E_nu(y-nu)^dag (P Q) + (D^dag P) E_nu(y+mu-nu)
+      {
+        const M3 D = link_off(mu, 0, nu, -1, nu), P = link_off(mu, 0, nu, -1, mu), Q = link_off(mu, 1, nu, -1, nu);
+        G = m3_add(G, m3_sub(mul(mul_dn(D, P), Eat(1, -1)), mul_dn(Eat(0, -1), mul(P, Q))));
+      }
     } else {
-      // plaquette at y-mu: staple U_mu(y-mu+nu)^dag U_nu(y-mu)^dag U_mu(y-mu)
-      M3 T = corner_staple(m3_dag(link_off(mu, -1, nu, 1, mu)), m3_dag(link_off(mu, -1, nu, 0, nu)),
-                           link_off(mu, -1, nu, 0, mu), Cat(0, 1), Cat(-1, 1), Cat(-1, 0), Cat(0, 0));
-      G = m3_add(G, m3_dag(T));
-      // plaquette at y, where the link enters daggered: staple U_mu(y) U_nu(y+mu) U_mu(y+nu)^dag
-      T = corner_staple(link_off(mu, 0, nu, 0, mu), link_off(mu, 1, nu, 0, nu), m3_dag(link_off(mu, 0, nu, 1, mu)),
-                        Cat(0, 0), Cat(1, 0), Cat(1, 1), Cat(0, 1));
-      G = m3_add(G, T);
+      // E of the mu links of the plane
+      auto Eat = [&](int dm, int dn) { return load_m3(Ebuf, 2 * pl, V, site_off(mu, dm, nu, dn)); };
+      // plaquette at y-mu: s1 = A^dag, s2 = B^dag, s3 = S with A = U_mu(y-mu+nu), B = U_nu(y-mu),
+      // S = U_mu(y-mu); G += T^dag = -(S^dag B) E_mu(y-mu+nu) + E_mu(y-mu)^dag (B A)
+      {
+        const M3 A = link_off(mu, -1, nu, 1, mu), B = link_off(mu, -1, nu, 0, nu), S = link_off(mu, -1, nu, 0, mu);
+        G = m3_add(G, m3_sub(mul_dn(Eat(-1, 0), mul(B, A)), mul(mul_dn(S, B), Eat(-1, 1))));
+      }
+      // plaquette at y (the link enters daggered): s1 = S0 = U_mu(y), s2 = R = U_nu(y+mu),
+      // s3 = A^dag with A = U_mu(y+nu); G += E_mu(y) (R A^dag) - (S0 R) E_mu(y+nu)^dag
+      {
+        const M3 S0 = link_off(mu, 0, nu, 0, mu), R = link_off(mu, 1, nu, 0, nu), A = link_off(mu, 0, nu, 1, mu);
+        G = m3_add(G, m3_sub(mul(Eat(0, 0), mul_nd(R, A)), mul_nd(mul(S0, R), Eat(0, 1))));
+      }
     }
   }
   M3 res;
@@ -371,13 +410,22 @@ void launch_force_coeff(const Geom& g, double kappa, double csw, int nrhs, const
                                                         accumulate ? 1 : 0);
 }
 
+size_t force_edge_bytes(const Geom& g) { return 2 * force_clover_bytes(g); }
+
+void launch_force_edges(const Geom& g, const void* g64, const double2* Cbuf, double2* Ebuf, cudaStream_t st) {
+  g_kernel_launches += 1;
+  const int V = 2 * g.Vh;
+  edge_insert_kernel<<<(int)((6LL * V + FB - 1) / FB), FB, 0, st>>>(g, static_cast<const double2*>(g64), Cbuf,
+                                                                     Ebuf);
+}
+
 void launch_force_links(const Geom& g, double kappa, int nrhs, const void* g64, const double2* Xe, const double2* Xo,
-                        const double2* Ye, const double2* Yo, const double2* Cbuf, double2* out, bool gradient,
+                        const double2* Ye, const double2* Yo, const double2* Ebuf, double2* out, bool gradient,
                         bool with_clover, bool accumulate, cudaStream_t st) {
   g_kernel_launches += 1;
   const int V = 2 * g.Vh;
   link_force_kernel<<<(int)((4LL * V + FB - 1) / FB), FB, 0, st>>>(g, kappa, nrhs, static_cast<const double2*>(g64),
-                                                                    Xe, Xo, Ye, Yo, Cbuf, out, gradient ? 1 : 0,
+                                                                    Xe, Xo, Ye, Yo, Ebuf, out, gradient ? 1 : 0,
                                                                     with_clover ? 1 : 0, accumulate ? 1 : 0);
 }
 
@@ -387,7 +435,10 @@ void launch_force_det_coeff(const Geom& g, double kappa, double csw, const doubl
   det_coeff_kernel<<<(g.Vh + FB - 1) / FB, FB, 0, st>>>(g, kappa, csw, Ainv_odd, Cbuf);
 }
 
-double force_link_flops(int nrhs, bool with_clover) { return (with_clover ? 6.0 * 1800.0 : 0.0) + 744.0 * nrhs + 274.0; }
+// clover part per link: 6 plaquettes x (4 products of 198 flops + 36 adds); per site of kernel 2:
+// 6 planes x 2 links x (2 products + 18 adds)
+double force_link_flops(int nrhs, bool with_clover) { return (with_clover ? 6.0 * 828.0 : 0.0) + 744.0 * nrhs + 274.0; }
+double force_edge_flops() { return 6.0 * 2 * (2 * 198.0 + 18.0); }
 double force_coeff_flops(int nrhs) { return 6.0 * (4 * 3 * 3 * 8.0) * nrhs + 6.0 * 60.0; }
 
 }  // namespace qcd
