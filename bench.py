@@ -31,6 +31,10 @@ import sys
 import threading
 import time
 
+# the oracle timed as the CPU baseline runs on one host thread: no BLAS / OpenMP thread pools
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -574,15 +578,28 @@ def cpu_baseline(w, gpu_iters, cg_sample_iters=4):
     t0 = time.perf_counter()
     oforce.lie_force(U, oforce.gradient(op, xx))
     t_force = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    op.Mhat(b[0])
+    t_mhat = time.perf_counter() - t0
     est = t_clover + t_it * gpu_iters + t_force
     try:
         cores = len(os.sched_getaffinity(0))
     except AttributeError:
         cores = os.cpu_count()
+    # the oracle's Mhat on the large lattices, scaled by volume from the timed application (the numpy
+    # operator is vectorised over sites, so its cost is linear in V); its solves there are not run
+    V = int(np.prod(w["dims"]))
+    large = {name: {"dims": list(synth.WORKLOADS[name]["dims"]),
+                    "mhat_apply_ms": t_mhat * 1e3 * np.prod(synth.WORKLOADS[name]["dims"]) / V,
+                    "solve": "not run"}
+             for name in ("c3_32^3x64", "c4_48^3x96")}
     return {"value": est * 1e3, "unit": "ms per hot-path step (16^4, solve to 1e-8)", "cores": 1,
             "cores_available": cores, "kind": "oracle",
             "sample": f"clover+inverse once, {cg_sample_iters} CG iterations ({t_it:.2f} s each, scaled to the "
-                      f"{gpu_iters} iterations of the solve), force once; numpy FP64, one thread"}
+                      f"{gpu_iters} iterations of the solve), force once; numpy FP64, one thread",
+            "mhat_apply_ms": t_mhat * 1e3,
+            "large_volumes": dict(large, note=f"one Mhat application timed on {'x'.join(map(str, w['dims']))} "
+                                              f"({t_mhat:.2f} s) and scaled by the site count")}
 
 
 def step_config(name, w, world):
