@@ -259,7 +259,8 @@ typedef struct {
   double flops;          /* conventional flops summed over the launches */
 } qcd_kernel_stat;
 
-/* Copy up to max_entries kernel classes into out (synchronises the stream). */
+/* Copy up to max_entries kernel classes with at least one launch since the last
+ * qcd_profile(ctx, 1) into out, then a "launches_total" entry (synchronises the stream). */
 qcd_status qcd_profile_read(qcd_ctx* ctx, qcd_kernel_stat* out, int max_entries, int* n_entries);
 
 /*

@@ -153,23 +153,33 @@ struct qcd_ctx {
   cudaStream_t cap = nullptr;
   CaptureSink* sink = nullptr;
   std::vector<ItGraph*> graphs;
-  std::vector<std::pair<ItGraph*, int>> launched;  // graphs launched since the last collection, with iteration offset
+  struct Launched {
+    ItGraph* g;
+    int offset;  // CG iteration offset of the graph's first iteration
+    int round;   // reliable-update graph of a pipelined round (-1: always counted)
+  };
+  std::vector<Launched> launched;  // graphs launched since the last collection
   double last_rho = 0.0;                            // per-iteration |r|^2 ratio seen by the last solve
   // persistent single-RHS iteration: per-block partial sums and the grid barrier words
   double* pc_part = nullptr;   // 2 x pc_slots
   int pc_slots = 0;
   unsigned* pc_bar = nullptr;  // [0] barrier arrivals, [2] error
   bool persistent = true;
-  struct {
+  // per round of a batch of persistent launches: 2 x iterations run + 1 if it raised a reliable update
+  int* pc_rounds = nullptr;
+  int* h_pc_rounds = nullptr;
+  struct PcPending {
     cudaEvent_t a, b;
     double bytes_per_iter, flops_per_iter;
-  } pc_pending{};
-  bool pc_has_pending = false;
+  };
+  std::vector<PcPending> pc_pending;
 };
 
 namespace {
 
 const int MAX_RHS = 8;
+// rounds (persistent segment + gated reliable update) enqueued per look at the solver state
+const int PC_MAX_ROUNDS = 32;
 
 size_t spinor_bytes(const Geom& g, int prec, int nrhs) {
   const size_t per = prec == 64 ? 192 : (prec == 32 ? 96 : 48);
@@ -340,7 +350,8 @@ ReduceArgs reduce_args(qcd_ctx* c, int mode) {
 // out = Mhat in (dagger: Mhat^dag) on even sites, t: odd temporary.
 // red (may be null) reduces |out|^2 per RHS.
 void apply_mhat(qcd_ctx* c, int prec, int nrhs, bool dagger, const void* in, const float* in_n, void* out,
-                float* out_n, void* t, float* t_n, const ReduceArgs* red, const int* halt) {
+                float* out_n, void* t, float* t_n, const ReduceArgs* red, const int* halt,
+                const int* gate = nullptr) {
   const double k2 = c->kappa * c->kappa;
   DslashArgs a = base_args(c, prec, 1, nrhs);
   a.in = in;
@@ -350,6 +361,7 @@ void apply_mhat(qcd_ctx* c, int prec, int nrhs, bool dagger, const void* in, con
   a.clover = clover_ptr(c, prec, true, 1);
   a.in_g5 = dagger;
   a.halt = halt;
+  a.gate = gate;
   run_dslash(c, prec, EPI_CLOVER_INV, a);
   DslashArgs b = base_args(c, prec, 0, nrhs);
   b.in = t;
@@ -363,6 +375,7 @@ void apply_mhat(qcd_ctx* c, int prec, int nrhs, bool dagger, const void* in, con
   b.x_g5 = dagger;
   b.out_g5 = dagger;
   b.halt = halt;
+  b.gate = gate;
   if (red) {
     b.do_norm = 1;
     b.red = *red;
@@ -372,9 +385,10 @@ void apply_mhat(qcd_ctx* c, int prec, int nrhs, bool dagger, const void* in, con
 
 // out = Mhat^dag Mhat in; y: even temporary, t: odd temporary; pap reduces |Mhat in|^2
 void apply_mdagm(qcd_ctx* c, int prec, int nrhs, const void* in, const float* in_n, void* out, float* out_n, void* t,
-                 float* t_n, void* y, float* y_n, const ReduceArgs* pap, const int* halt) {
-  apply_mhat(c, prec, nrhs, false, in, in_n, y, y_n, t, t_n, pap, halt);
-  apply_mhat(c, prec, nrhs, true, y, y_n, out, out_n, t, t_n, nullptr, halt);
+                 float* t_n, void* y, float* y_n, const ReduceArgs* pap, const int* halt,
+                 const int* gate = nullptr) {
+  apply_mhat(c, prec, nrhs, false, in, in_n, y, y_n, t, t_n, pap, halt, gate);
+  apply_mhat(c, prec, nrhs, true, y, y_n, out, out_n, t, t_n, nullptr, halt, gate);
 }
 
 qcd_status check_ctx(qcd_ctx* c) {
@@ -477,7 +491,9 @@ qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* strea
             cudaMallocHost(&c->h_flags, 4 * sizeof(int)) == cudaSuccess &&
             cudaMallocHost(&c->h_cg, sizeof(CGState) * MAX_RHS) == cudaSuccess &&
             cudaMallocHost(&c->h_ctl, sizeof(CGControl)) == cudaSuccess &&
-            cudaMallocHost(&c->h_results, sizeof(double) * MAX_RHS) == cudaSuccess;
+            cudaMallocHost(&c->h_results, sizeof(double) * MAX_RHS) == cudaSuccess &&
+            cudaMalloc(&c->pc_rounds, sizeof(int) * PC_MAX_ROUNDS) == cudaSuccess &&
+            cudaMallocHost(&c->h_pc_rounds, sizeof(int) * PC_MAX_ROUNDS) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     qcd_destroy(c);
@@ -522,13 +538,13 @@ qcd_status qcd_destroy(qcd_ctx* c) {
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   void* dev[] = {c->g64, c->g32, c->g16, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, c->logdet, c->flags,
-                 c->pc_part, c->pc_bar,
+                 c->pc_part, c->pc_bar, c->pc_rounds,
                  c->partials, c->counter, c->results, c->cg, c->ctl};
   for (void* p : dev)
     if (p) cudaFree(p);
   for (auto& b : c->ws)
     if (b.ptr) cudaFree(b.ptr);
-  void* host[] = {c->h_flags, c->h_cg, c->h_ctl, c->h_results};
+  void* host[] = {c->h_flags, c->h_cg, c->h_ctl, c->h_results, c->h_pc_rounds};
   for (void* p : host)
     if (p) cudaFreeHost(p);
   for (auto& p : c->pending) {
@@ -776,13 +792,18 @@ void enqueue_iteration(qcd_ctx* c, const SolverFields& f, int nrhs) {
 }
 
 // x_hi += x_lo, r = b - Mhat^dag Mhat x_hi in FP64 (true residual, convergence test, halt cleared
-// unless every RHS is done), p = r + beta p.
-void enqueue_reliable(qcd_ctx* c, const SolverFields& f, int nrhs) {
+// unless every RHS is done), p = r + beta p.  gated: every step returns at once unless a trigger
+// raised ctl->rel_go, which the last step lowers (so the update can be enqueued before it is known
+// to be due).
+void enqueue_reliable(qcd_ctx* c, const SolverFields& f, int nrhs, bool gated) {
   const Geom& g = c->g;
-  launch_accumulate_x(f.pr, g, nrhs, f.x_hi, f.x_lo, f.x_lo_n, c->cur);
-  apply_mdagm(c, 64, nrhs, f.x_hi, nullptr, f.ap_hi, nullptr, f.t_hi, nullptr, f.y_hi, nullptr, nullptr, nullptr);
-  launch_true_residual(f.pr, g, nrhs, f.b_hi, f.ap_hi, f.r_lo, f.r_lo_n, reduce_args(c, FIN_CG_TRUE), c->cur);
-  launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->cur);
+  const int* gate = gated ? &c->ctl->rel_go : nullptr;
+  launch_accumulate_x(f.pr, g, nrhs, f.x_hi, f.x_lo, f.x_lo_n, c->cur, gate);
+  apply_mdagm(c, 64, nrhs, f.x_hi, nullptr, f.ap_hi, nullptr, f.t_hi, nullptr, f.y_hi, nullptr, nullptr, nullptr,
+              gate);
+  launch_true_residual(f.pr, g, nrhs, f.b_hi, f.ap_hi, f.r_lo, f.r_lo_n, reduce_args(c, FIN_CG_TRUE), c->cur, gate);
+  launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->cur, gate);
+  if (gated) launch_gate_clear(&c->ctl->rel_go, c->cur);
 }
 
 // --- CUDA graphs of that work ----------------------------------------------------------------------
@@ -811,7 +832,7 @@ qcd_status capture_graph(qcd_ctx* c, ItGraph* gph) {
         enqueue_iteration(c, gph->f, gph->nrhs);
       }
     } else {
-      enqueue_reliable(c, gph->f, gph->nrhs);
+      enqueue_reliable(c, gph->f, gph->nrhs, true);
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(c->cap, &graph);
@@ -857,19 +878,21 @@ qcd_status get_graph(qcd_ctx* c, int kind, int len, const SolverFields& f, int n
   return QCD_OK;
 }
 
-qcd_status launch_graph(qcd_ctx* c, ItGraph* gph, int iter_offset) {
+qcd_status launch_graph(qcd_ctx* c, ItGraph* gph, int iter_offset, int round = -1) {
   CUDA_TRY(cudaGraphLaunch(gph->exec, c->st));
   g_kernel_launches += gph->kernels;
-  if (gph->prof) c->launched.push_back({gph, iter_offset});
+  if (gph->prof) c->launched.push_back({gph, iter_offset, round});
   return QCD_OK;
 }
 
 // after a synchronisation: fold the event pairs of the graphs launched since the last call into the
-// kernel classes, counting only CG iterations that ran (the first `real_iters` of the segment)
-void collect_graphs(qcd_ctx* c, int real_iters) {
+// kernel classes, counting only CG iterations that ran (the first `real_iters` of the segment) and
+// only the reliable updates of pipelined rounds whose gate was raised (rounds[k] odd; null: all)
+void collect_graphs(qcd_ctx* c, int real_iters, const int* rounds = nullptr) {
   for (auto& lg : c->launched) {
-    for (const ProfSlot& sl : lg.first->slots) {
-      if (sl.iter >= 0 && lg.second + sl.iter >= real_iters) continue;
+    if (lg.round >= 0 && rounds && !(rounds[lg.round] & 1)) continue;
+    for (const ProfSlot& sl : lg.g->slots) {
+      if (sl.iter >= 0 && lg.offset + sl.iter >= real_iters) continue;
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, sl.a, sl.b) != cudaSuccess) {
         cudaGetLastError();
@@ -915,8 +938,9 @@ qcd_status read_state(qcd_ctx* c, int nrhs) {
 const int PERSISTENT_MAX_VH = 1 << 30;
 
 // One segment of CG iterations of a single RHS in the persistent kernel: it stops itself at the
-// next reliable-update or convergence trigger, or after max_iters iterations.
-qcd_status launch_persistent(qcd_ctx* c, const SolverFields& f, int max_iters) {
+// next reliable-update or convergence trigger, or once the RHS has run iter_limit iterations in
+// total; round: its slot in pc_rounds.
+qcd_status launch_persistent(qcd_ctx* c, const SolverFields& f, int iter_limit, int round) {
   const Geom& g = c->g;
   PersistentCGArgs q;
   memset(&q, 0, sizeof q);
@@ -940,7 +964,8 @@ qcd_status launch_persistent(qcd_ctx* c, const SolverFields& f, int max_iters) {
   q.slots = c->pc_slots;
   q.bar_count = c->pc_bar;
   q.bar_err = reinterpret_cast<int*>(c->pc_bar + 2);
-  q.max_iters = max_iters < 1 ? 1 : max_iters;
+  q.iter_limit = iter_limit;
+  q.round_out = c->pc_rounds + round;
   CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, sizeof(unsigned), c->st));
   CUDA_TRY(cudaMemsetAsync(c->pc_bar + 2, 0, sizeof(unsigned), c->st));
   cudaEvent_t ea = nullptr, eb = nullptr;
@@ -958,8 +983,7 @@ qcd_status launch_persistent(qcd_ctx* c, const SolverFields& f, int max_iters) {
     dslash_cost(c, f.pp, EPI_XPAY, 1, &b2, &f2);
     dslash_cost(c, f.pp, EPI_XPAY_CG, 1, &bx, &fx);
     const double sp = 24.0 * real_bytes(f.pp) + (f.pp == 16 ? 4 : 0), sr = 24.0 * real_bytes(f.pr);
-    c->pc_pending = {ea, eb, 2 * b1 + b2 + bx + (double)g.Vh * (sr + 2 * sp), 2 * f1 + f2 + fx};
-    c->pc_has_pending = true;
+    c->pc_pending.push_back({ea, eb, 2 * b1 + b2 + bx + (double)g.Vh * (sr + 2 * sp), 2 * f1 + f2 + fx});
   }
   return QCD_OK;
 }
@@ -997,6 +1021,24 @@ int predict_iterations(const qcd_ctx* c, int nrhs, const std::vector<double>& rh
   best += 1;
   if (best > 2 * MAX_GRAPH_LEN - 1) best = 2 * MAX_GRAPH_LEN - 1;
   return (int)best;
+}
+
+// Rounds of the persistent path (segment + reliable update) expected before convergence: each
+// reliable update is due once |r|^2 fell by delta2 (or after reliable_every iterations, at the
+// per-iteration ratio rho), and the last one confirms |r|^2 <= tol2.  first: before any look at the
+// state, with |r_0| = |b| (a zero initial guess).  Too many rounds cost a few empty launches each, too
+// few one more look.
+int predict_rounds(const qcd_ctx* c, const qcd_solver_params* prm, bool first, double rho) {
+  const CGControl& ctl = *c->h_ctl;
+  const CGState& st = c->h_cg[0];
+  const double ratio = first ? prm->tol * prm->tol : (st.rr_reliable > 0.0 ? st.tol2 / st.rr_reliable : 1.0);
+  double n = 1.0;
+  if (ratio > 0.0 && ratio < 1.0) {
+    if (ctl.delta2 > 0.0 && ctl.delta2 < 1.0) n = std::max(n, ceil(log(ratio) / log(ctl.delta2) - 1e-9));
+    if (rho > 0.0 && rho < 1.0 && ctl.reliable_every > 0)
+      n = std::max(n, ceil(log(ratio) / log(rho) / ctl.reliable_every - 1e-9));
+  }
+  return (int)std::min<double>(n, PC_MAX_ROUNDS);
 }
 
 // Solve for one batch of nrhs (1, 2, 4 or 8) canonical fields.
@@ -1038,7 +1080,9 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
   launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->st);
 
   std::vector<double> rho(nrhs, c->last_rho);
-  // one RHS: the persistent kernel runs each segment of iterations
+  // one RHS: the persistent kernel runs each segment of iterations, and the rounds (segment, gated
+  // reliable update) expected before convergence are enqueued together, with one look at the state
+  // after them
   const bool use_pc = c->persistent && nrhs == 1 && g.Vh <= PERSISTENT_MAX_VH;
   qcd_status result = QCD_OK;
   bool after_reliable = true;
@@ -1047,8 +1091,16 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
   while (true) {
     // the state is only known after a synchronisation; right after the set-up or a reliable
     // update the host copy is stale, which predict_iterations accounts for
+    int rounds = 0;
     if (use_pc) {
-      if ((s = launch_persistent(c, f, prm->max_iter - done_iters))) return s;
+      rounds = predict_rounds(c, prm, done_iters == 0, rho[0]);
+      for (int k = 0; k < rounds; k++) {
+        if ((s = launch_persistent(c, f, prm->max_iter, k))) return s;
+        ItGraph* rk;
+        if ((s = get_graph(c, 1, k, f, nrhs, &rk))) return s;
+        if ((s = launch_graph(c, rk, 0, k))) return s;
+      }
+      CUDA_TRY(cudaMemcpyAsync(c->h_pc_rounds, c->pc_rounds, sizeof(int) * rounds, cudaMemcpyDeviceToHost, c->st));
     } else {
       const int n = std::min(predict_iterations(c, nrhs, rho, after_reliable), std::max(1, prm->max_iter - done_iters));
       if ((s = launch_iterations(c, f, nrhs, n))) return s;
@@ -1065,24 +1117,31 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
       if (st.active && st.since_reliable > 0 && st.rr_reliable > 0.0 && st.rr > 0.0)
         rho[r] = pow(st.rr / st.rr_reliable, 1.0 / st.since_reliable);
     }
-    if (c->prof_on) collect_graphs(c, max_it - done_iters);
-    if (c->pc_has_pending) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, c->pc_pending.a, c->pc_pending.b) == cudaSuccess) {
-        ProfClass& pc = c->prof[prof_class(c, f.pp == 64 ? "cg_persistent_p64" : (f.pp == 32 ? "cg_persistent_p32"
-                                                                                               : "cg_persistent_p16"))];
-        const int n_it = max_it - done_iters;
-        pc.launches += 1;
-        pc.ms += ms;
-        pc.bytes += n_it * c->pc_pending.bytes_per_iter;
-        pc.flops += n_it * c->pc_pending.flops_per_iter;
-      } else {
-        cudaGetLastError();
+    if (c->prof_on) collect_graphs(c, max_it - done_iters, use_pc ? c->h_pc_rounds : nullptr);
+    if (!c->pc_pending.empty()) {
+      // the persistent launches of this look, each with the iterations it ran (no-op launches of
+      // rounds past convergence are not counted)
+      const int cls = prof_class(c, f.pp == 64 ? "cg_persistent_p64"
+                                               : (f.pp == 32 ? "cg_persistent_p32" : "cg_persistent_p16"));
+      for (size_t k = 0; k < c->pc_pending.size(); k++) {
+        const auto& pp = c->pc_pending[k];
+        const int n_it = k < (size_t)rounds ? c->h_pc_rounds[k] >> 1 : 0;
+        float ms = 0.f;
+        if (n_it > 0 && cudaEventElapsedTime(&ms, pp.a, pp.b) == cudaSuccess) {
+          ProfClass& pc = c->prof[cls];
+          pc.launches += 1;
+          pc.ms += ms;
+          pc.bytes += n_it * pp.bytes_per_iter;
+          pc.flops += n_it * pp.flops_per_iter;
+        } else {
+          cudaGetLastError();
+        }
+        c->ev_free.push_back(pp.a);
+        c->ev_free.push_back(pp.b);
       }
-      c->ev_free.push_back(c->pc_pending.a);
-      c->ev_free.push_back(c->pc_pending.b);
-      c->pc_has_pending = false;
+      c->pc_pending.clear();
     }
+    const bool progress = max_it > done_iters;
     done_iters = max_it;
     if (c->h_ctl->overflow) return fail(QCD_ERR_CUDA, "reduction buffer too small (internal sizing error)");
     if (c->h_ctl->nan) {
@@ -1092,6 +1151,11 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
     if (!active) break;
     if (max_it >= prm->max_iter) {
       result = fail(QCD_ERR_NOT_CONVERGED, "CG did not converge in %d iterations", prm->max_iter);
+      break;
+    }
+    if (use_pc && !progress) {
+      // every round returned at once with the RHS still active: nothing more would change
+      result = fail(QCD_ERR_NOT_CONVERGED, "persistent CG stopped making progress after %d iterations", max_it);
       break;
     }
     after_reliable = false;
@@ -1116,7 +1180,7 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
   for (int r = 0; r < nrhs; r++)
     if (rho[r] > 0.0 && rho[r] < 1.0) c->last_rho = rho[r];
   // not converged: fold the progress into x and recompute the true residual for the stats
-  if (result == QCD_ERR_NOT_CONVERGED) enqueue_reliable(c, f, nrhs);
+  if (result == QCD_ERR_NOT_CONVERGED) enqueue_reliable(c, f, nrhs, false);
   // fold the last low-precision increment into x and write out
   launch_accumulate_x(f.pr, g, nrhs, f.x_hi, f.x_lo, f.x_lo_n, c->st);
   launch_spinor_to_canon(64, g, f.x_hi, nullptr, x, nrhs, c->st);
@@ -1577,7 +1641,12 @@ qcd_status qcd_profile(qcd_ctx* c, int enable) {
   if ((s = sync_and_check(c, "profile"))) return s;
   prof_collect(c);
   if (enable) {
-    c->prof.clear();
+    // counters restart; the classes keep their indices, which the event slots of recorded CUDA
+    // graphs hold
+    for (ProfClass& pc : c->prof) {
+      pc.launches = 0;
+      pc.ms = pc.bytes = pc.flops = 0;
+    }
     g_kernel_launches = 0;
   }
   c->prof_on = enable != 0;
@@ -1592,6 +1661,7 @@ qcd_status qcd_profile_read(qcd_ctx* c, qcd_kernel_stat* out, int max_entries, i
   prof_collect(c);
   int n = 0;
   for (auto& p : c->prof) {
+    if (p.launches == 0) continue;
     if (n >= max_entries) break;
     memset(&out[n], 0, sizeof(qcd_kernel_stat));
     snprintf(out[n].name, sizeof out[n].name, "%s", p.name.c_str());

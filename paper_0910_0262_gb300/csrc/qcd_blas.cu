@@ -15,10 +15,10 @@ constexpr int BB = 256;  // block size of the BLAS kernels
 
 template <int PR, int PP>
 __global__ void __launch_bounds__(BB) p_update_kernel(Geom g, const void* r, const float* rn, void* p, float* pn,
-                                                      const CGState* cg, const int* halt) {
+                                                      const CGState* cg, const int* halt, const int* gate) {
   using RR = typename Real<PR>::T;
   using RP = typename Real<PP>::T;
-  if (halt && *halt) return;
+  if ((halt && *halt) || (gate && !*gate)) return;
   const int k = blockIdx.y;
   const int h = blockIdx.x * BB + threadIdx.x;
   if (h >= g.Vh || !cg[k].active) return;
@@ -37,8 +37,10 @@ __global__ void __launch_bounds__(BB) p_update_kernel(Geom g, const void* r, con
 }
 
 template <int PR>
-__global__ void __launch_bounds__(BB) accumulate_x_kernel(Geom g, double2* x_hi, void* x_lo, float* xn) {
+__global__ void __launch_bounds__(BB) accumulate_x_kernel(Geom g, double2* x_hi, void* x_lo, float* xn,
+                                                          const int* gate) {
   using RR = typename Real<PR>::T;
+  if (gate && !*gate) return;
   const int k = blockIdx.y;
   const int h = blockIdx.x * BB + threadIdx.x;
   if (h >= g.Vh) return;
@@ -58,8 +60,9 @@ __global__ void __launch_bounds__(BB) accumulate_x_kernel(Geom g, double2* x_hi,
 
 template <int PR>
 __global__ void __launch_bounds__(BB) true_residual_kernel(Geom g, int nrhs, const double2* b, const double2* Ap,
-                                                           void* r_lo, float* rn, ReduceArgs red) {
+                                                           void* r_lo, float* rn, ReduceArgs red, const int* gate) {
   using RR = typename Real<PR>::T;
+  if (gate && !*gate) return;  // every block: the reduction's counter is left untouched
   const int k = blockIdx.y;
   const int h = blockIdx.x * BB + threadIdx.x;
   double v = 0.0;
@@ -127,30 +130,37 @@ __global__ void __launch_bounds__(BB) axpby_kernel(size_t n, double a, const dou
   y[j] = make_double2(fma(a, u.x, b * w.x), fma(a, u.y, b * w.y));
 }
 
+__global__ void gate_clear_kernel(int* gate) { *gate = 0; }
+
 dim3 grid2(const Geom& g, int nrhs) { return dim3((g.Vh + BB - 1) / BB, nrhs); }
 
 }  // namespace
 
 void launch_p_update(int prec_r, int prec_p, const Geom& g, int nrhs, const void* r, const float* rn, void* p,
-                     float* pn, const CGState* cg, const int* halt, cudaStream_t st) {
+                     float* pn, const CGState* cg, const int* halt, cudaStream_t st, const int* gate) {
   g_kernel_launches += 1;
-  if (prec_r == 64) p_update_kernel<64, 64><<<grid2(g, nrhs), BB, 0, st>>>(g, r, rn, p, pn, cg, halt);
-  else if (prec_p == 32) p_update_kernel<32, 32><<<grid2(g, nrhs), BB, 0, st>>>(g, r, rn, p, pn, cg, halt);
-  else p_update_kernel<32, 16><<<grid2(g, nrhs), BB, 0, st>>>(g, r, rn, p, pn, cg, halt);
+  if (prec_r == 64) p_update_kernel<64, 64><<<grid2(g, nrhs), BB, 0, st>>>(g, r, rn, p, pn, cg, halt, gate);
+  else if (prec_p == 32) p_update_kernel<32, 32><<<grid2(g, nrhs), BB, 0, st>>>(g, r, rn, p, pn, cg, halt, gate);
+  else p_update_kernel<32, 16><<<grid2(g, nrhs), BB, 0, st>>>(g, r, rn, p, pn, cg, halt, gate);
 }
 
 void launch_accumulate_x(int prec_r, const Geom& g, int nrhs, double2* x_hi, void* x_lo, float* x_lon,
-                         cudaStream_t st) {
+                         cudaStream_t st, const int* gate) {
   g_kernel_launches += 1;
-  if (prec_r == 64) accumulate_x_kernel<64><<<grid2(g, nrhs), BB, 0, st>>>(g, x_hi, x_lo, x_lon);
-  else accumulate_x_kernel<32><<<grid2(g, nrhs), BB, 0, st>>>(g, x_hi, x_lo, x_lon);
+  if (prec_r == 64) accumulate_x_kernel<64><<<grid2(g, nrhs), BB, 0, st>>>(g, x_hi, x_lo, x_lon, gate);
+  else accumulate_x_kernel<32><<<grid2(g, nrhs), BB, 0, st>>>(g, x_hi, x_lo, x_lon, gate);
 }
 
 void launch_true_residual(int prec_r, const Geom& g, int nrhs, const double2* b, const double2* Ap, void* r_lo,
-                          float* r_lon, const ReduceArgs& red, cudaStream_t st) {
+                          float* r_lon, const ReduceArgs& red, cudaStream_t st, const int* gate) {
   g_kernel_launches += 1;
-  if (prec_r == 64) true_residual_kernel<64><<<grid2(g, nrhs), BB, 0, st>>>(g, nrhs, b, Ap, r_lo, r_lon, red);
-  else true_residual_kernel<32><<<grid2(g, nrhs), BB, 0, st>>>(g, nrhs, b, Ap, r_lo, r_lon, red);
+  if (prec_r == 64) true_residual_kernel<64><<<grid2(g, nrhs), BB, 0, st>>>(g, nrhs, b, Ap, r_lo, r_lon, red, gate);
+  else true_residual_kernel<32><<<grid2(g, nrhs), BB, 0, st>>>(g, nrhs, b, Ap, r_lo, r_lon, red, gate);
+}
+
+void launch_gate_clear(int* gate, cudaStream_t st) {
+  g_kernel_launches += 1;
+  gate_clear_kernel<<<1, 1, 0, st>>>(gate);
 }
 
 void launch_norm2(const Geom& g, int nrhs, const double2* v, const ReduceArgs& red, cudaStream_t st) {

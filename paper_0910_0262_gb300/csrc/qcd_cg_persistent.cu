@@ -5,6 +5,9 @@
 // that fits in L2.  This cooperative kernel keeps every block resident and runs the iteration's
 // five phases back to back, separated by grid barriers, until a reliable-update or convergence
 // trigger (or an iteration cap) -- the same arithmetic, in the same order, as the graph of launches.
+// At a reliable-update trigger it raises the update's gate (ctl->rel_go), so that the update's
+// launches, enqueued behind it before the trigger is known, run; a launch that finds the RHS
+// converged or halted returns at once.
 //
 //   phase 1  t  = A_oo^-1 D_oe p
 //   phase 2  y  = A_ee p - kappa^2 D_eo t,     |y|^2 = <p, Mhat^dag Mhat p>  -> alpha
@@ -126,7 +129,10 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
   __shared__ cx<R> part[4][12][32];
   __shared__ uint4 stage[Stage<P, EPI_XPAY_CG>::U4];  // the largest staging of the three epilogues
   const CGState st0 = *Q.cg;
-  if (!st0.active || Q.ctl->halt) return;
+  if (!st0.active || Q.ctl->halt || st0.iters >= Q.iter_limit) {
+    if (Q.round_out && blockIdx.x == 0 && threadIdx.x == 0) *Q.round_out = 0;
+    return;
+  }
   double rr = st0.rr, rr_prev = st0.rr_prev;
   int iters = st0.iters, since = st0.since_reliable;
   const int every = Q.ctl->reliable_every;
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
 
   double alpha = 0.0, beta = 0.0, pAp = 0.0;
   unsigned bar_target = 0;
-  for (int it = 0; it < Q.max_iters; it++) {
+  while (true) {
     // phase 1
     a1.in = Q.p;
     a1.in_norm = Q.p_n;
@@ -175,6 +181,7 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         Q.ctl->nan = 1;
         Q.ctl->halt = 1;
+        if (Q.round_out) *Q.round_out = 2 * (iters - st0.iters);
       }
       return;
     }
@@ -205,6 +212,7 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         Q.ctl->nan = 1;
         Q.ctl->halt = 1;
+        if (Q.round_out) *Q.round_out = 2 * (iters - st0.iters);
       }
       return;
     }
@@ -231,7 +239,7 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
       }
       if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     }
-    if (want || it == Q.max_iters - 1) {
+    if (want || iters >= Q.iter_limit) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         CGState& s = *Q.cg;
         s.rr = rr;
@@ -244,7 +252,9 @@ __global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) 
         if (want) {
           s.pending = 1;
           Q.ctl->halt = 1;
+          Q.ctl->rel_go = 1;
         }
+        if (Q.round_out) *Q.round_out = 2 * (iters - st0.iters) + (want ? 1 : 0);
       }
       return;
     }

@@ -42,6 +42,7 @@ struct DslashArgs {
   int do_norm;             // reduce |out|^2 per RHS
   ReduceArgs red;
   const int* halt;         // non-null: return immediately when *halt != 0
+  const int* gate;         // non-null: return immediately unless *gate != 0
   // EPI_XPAY_CG: the CG vectors (x_lo, r_lo in FP64 for P = 64, else FP32; p in precision P)
   void* cg_x;
   void* cg_r;
@@ -447,7 +448,7 @@ __device__ __forceinline__ void dslash_split_body(const DslashArgs& A) {
   using R = typename Real<P>::T;
   __shared__ cx<R> part[4][12][32];
   __shared__ uint4 stage[Stage<P, EPI>::U4];
-  if (A.halt && *A.halt) return;
+  if ((A.halt && *A.halt) || (A.gate && !*A.gate)) return;
   int hh;
   bool valid;
   Site s;
@@ -502,7 +503,7 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
   constexpr bool SCL = STAGED && EPI != EPI_NONE;
   __shared__ cx<R> sl[STAGED ? 8 * 9 * 32 : 1];  // [link 2 mu + bwd][element][site]
   __shared__ float scl[SCL ? 72 * 32 : 1];       // [clover value][site]
-  if (A.halt && *A.halt) return;
+  if ((A.halt && *A.halt) || (A.gate && !*A.gate)) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int G = STAGED ? 1 : (A.nrhs == 1 ? 4 : (A.nrhs == 2 ? 2 : 1)), W = 4 / G;
   const int grp = w / W, k = w - grp * W;

@@ -578,6 +578,8 @@ struct CGControl {
   int nan;              // non-finite reduction or breakdown
   int reliable_every;
   int overflow;         // a reduction launch needed more partial slots than allocated (skipped)
+  int rel_go;           // a reliable update is due: its kernels run only while this is set
+  int pad_;
   double delta2;        // reliable update when |r|^2 < delta2 * rr_reliable
 };
 
@@ -639,6 +641,7 @@ __device__ __forceinline__ void finalize_total(const ReduceArgs& ra, int r, doub
       if (want) {
         s.pending = 1;
         ra.ctl->halt = 1;
+        ra.ctl->rel_go = 1;
       }
       break;
     }

@@ -26,7 +26,9 @@ struct PersistentCGArgs {
   int slots;                   // slots in each; the grid never exceeds it
   unsigned* bar_count;         // barrier arrivals, zeroed before the launch
   int* bar_err;                // set when a barrier wait gave up
-  int max_iters;               // iterations this launch may run
+  int iter_limit;              // total iterations of the RHS (over all launches) at which to stop
+  int* round_out;              // non-null: 2 x iterations this launch ran, + 1 if it raised a reliable
+                               // update, written at its end
 };
 cudaError_t launch_cg_persistent(int prec, int recon, const PersistentCGArgs& q, cudaStream_t st);
 // one grid barrier that a block never reaches (the wait must give up and set *err)
@@ -57,15 +59,19 @@ struct DslashArgs;
 void launch_dslash(int prec, int recon, int epi, const DslashArgs& a, cudaStream_t st);
 
 // ---- BLAS-1 and CG steps (qcd_blas.cu); 2-D grids (sites x RHS)
+// gate (these three): non-null, the kernel returns at once unless *gate != 0 (the reliable-update
+// steps, enqueued ahead of knowing whether an update is due)
 // p = r + beta p
 void launch_p_update(int prec_r, int prec_p, const Geom& g, int nrhs, const void* r, const float* rn, void* p,
-                     float* pn, const CGState* cg, const int* halt, cudaStream_t st);
+                     float* pn, const CGState* cg, const int* halt, cudaStream_t st, const int* gate = nullptr);
 // x_hi += x_lo ; x_lo = 0
 void launch_accumulate_x(int prec_r, const Geom& g, int nrhs, double2* x_hi, void* x_lo, float* x_lon,
-                         cudaStream_t st);
+                         cudaStream_t st, const int* gate = nullptr);
 // r_lo = b - Ap_hi ; |b - Ap_hi|^2 -> reduction (FIN_CG_TRUE)
 void launch_true_residual(int prec_r, const Geom& g, int nrhs, const double2* b, const double2* Ap, void* r_lo,
-                          float* r_lon, const ReduceArgs& red, cudaStream_t st);
+                          float* r_lon, const ReduceArgs& red, cudaStream_t st, const int* gate = nullptr);
+// *gate = 0
+void launch_gate_clear(int* gate, cudaStream_t st);
 // |v|^2 (FP64 native) -> reduction
 void launch_norm2(const Geom& g, int nrhs, const double2* v, const ReduceArgs& red, cudaStream_t st);
 // ---- molecular dynamics (qcd_md.cu); canonical link fields [V][4][3][3] complex128
