@@ -47,7 +47,7 @@ WORKLOAD = "c1_16^4"
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel, with the summary
 # that holds the command; a kernel changed since its capture has no entry (traffic null)
 NCU_TRAFFIC = {
-    "cg_persistent_p32": (41.3e6, "profiles/cg_persistent_16x16x16x16.md"),
+    "cg_persistent_p32": (41.2e6, "profiles/cg_persistent_16x16x16x16.md"),
 }
 
 
