@@ -87,3 +87,62 @@ def test_cg_on_degenerate_lattices(dims, inner):
         for r in range(n):
             assert true_residual(ref, x[r], b[r]) <= 1e-8 * (1 + 1e-6)
     c.close()
+
+
+def _ctx(dims, U, persistent):
+    import os
+    from paper_0910_0262_gb300.qcd import CloverWilson
+    old = os.environ.get("QCD_CG_PERSISTENT")
+    os.environ["QCD_CG_PERSISTENT"] = "1" if persistent else "0"
+    try:
+        c = CloverWilson(dims, -1.0)
+    finally:
+        if old is None:
+            del os.environ["QCD_CG_PERSISTENT"]
+        else:
+            os.environ["QCD_CG_PERSISTENT"] = old
+    c.load_gauge(to_dev(U), recon12=True)
+    c.clover_build(KAPPA, CSW)
+    return c
+
+
+@pytest.mark.parametrize("inner", [32, 16])
+def test_persistent_rounds_beyond_the_prediction(problem, inner):
+    """A reliable update every 5 iterations: far more rounds (persistent segment + gated update) than
+    the first batch enqueues, so the solve takes several looks; it must agree with the graph path
+    (one launch per pass) in iterations, reliable updates and the oracle's true residual."""
+    dims, U, b, ref, _ = problem
+    kw = dict(tol=1e-8, inner_prec=inner, reliable_every=5, reliable_delta=0.1, max_iter=5000)
+    res = {}
+    for persistent in (True, False):
+        c = _ctx(dims, U, persistent)
+        x, st, ok = c.cg_solve(to_dev(b[:1]), **kw)
+        c.close()
+        assert ok
+        assert true_residual(ref, to_np(x)[0], b[0]) <= 1e-8 * (1 + 1e-6)
+        res[persistent] = st[0]
+    assert res[True]["reliable_updates"] >= res[True]["iters"] // 5
+    assert abs(res[True]["iters"] - res[False]["iters"]) <= 2
+    assert abs(res[True]["reliable_updates"] - res[False]["reliable_updates"]) <= 1
+
+
+@pytest.mark.parametrize("inner", [32, 16])
+def test_persistent_rounds_past_convergence(problem, inner):
+    """From an initial guess good to ~1e-5 the mixed solve to 1e-8 needs few reliable updates while
+    the first batch enqueues rounds for a solve from zero: the rounds after convergence must do
+    nothing (no FP64 hopping launches in the profile beyond the set-up's and the updates that ran)."""
+    dims, U, b, ref, c = problem
+    x0, _, ok = c.cg_solve(to_dev(b[:1]), tol=1e-5, inner_prec=64)
+    assert ok
+    c.profile(True)
+    x, st, ok = c.cg_solve(to_dev(b[:1]), x0=x0, tol=1e-8, inner_prec=inner, reliable_delta=0.1)
+    rows = {r["name"]: r["launches"] for r in c.profile_read()}
+    c.profile(False)
+    assert ok
+    assert true_residual(ref, to_np(x)[0], b[0]) <= 1e-8 * (1 + 1e-6)
+    n = st[0]["reliable_updates"]
+    assert 1 <= n <= 4
+    # the set-up's true residual from x0 plus one M^dag M per reliable update that ran
+    assert rows.get("dslash_p64_r18_cloverinv") == 2 * (n + 1)
+    assert rows.get("dslash_p64_r18_xpay") == 2 * (n + 1)
+    assert rows.get(f"cg_persistent_p{inner}") == n
