@@ -7,12 +7,13 @@ corresponding pin from the other oracle tests must then fail.
 import numpy as np
 import pytest
 
-from oracle import dirac, force, evenodd, cloverdet, md
+from oracle import dirac, force, evenodd, cloverdet, md, measure
 import test_oracle_operator as t_op
 import test_oracle_md as t_md
 import test_oracle_cloverdet as t_cd
 import test_oracle_clover as t_cl
 import test_oracle_force as t_fo
+import test_oracle_measure as t_me
 
 
 def _fails(fn, *args):
@@ -138,3 +139,49 @@ def test_noise_drawn_before_the_half_step_is_caught(monkeypatch):
         return md.update_links(Uh, P, eps / 2.0), P
     monkeypatch.setattr(md, "r_step", r_step_early)
     assert _fails(t_md.test_r_step_is_reversible_for_fixed_noise)
+
+
+def test_polyakov_along_the_wrong_direction_is_caught(monkeypatch):
+    def along_z(U):
+        Z = U.shape[1]
+        prod = U[:, 0, ..., 2, :, :]
+        for z in range(1, Z):
+            prod = prod @ U[:, z, ..., 2, :, :]
+        return complex(np.mean(np.trace(prod, axis1=-2, axis2=-1)) / 3.0)
+    monkeypatch.setattr(measure, "polyakov_loop", along_z)
+    assert _fails(t_me.test_polyakov_unit_and_closed_form)
+
+
+def test_polyakov_product_in_reverse_order_is_caught(monkeypatch):
+    def reversed_product(U):
+        T = U.shape[0]
+        prod = U[T - 1, ..., 3, :, :]
+        for t in range(T - 2, -1, -1):
+            prod = prod @ U[t, ..., 3, :, :]
+        return complex(np.mean(np.trace(prod, axis1=-2, axis2=-1)) / 3.0)
+    monkeypatch.setattr(measure, "polyakov_loop", reversed_product)
+    assert _fails(t_me.test_polyakov_centre_and_gauge_transformations)
+
+
+def test_pbp_without_the_odd_sites_is_caught(monkeypatch):
+    def even_only(op, eta_e, eta_o, tol=1e-12):
+        x_e, _ = measure.solve_full(op, eta_e, eta_o, tol)
+        return float(np.vdot(eta_e.reshape(-1), x_e.reshape(-1)).real / (4.0 * eta_e.shape[0]))
+    monkeypatch.setattr(measure, "pbp", even_only)
+    assert _fails(t_me.test_pbp_estimator_against_dense_inverse)
+
+
+def test_link_update_with_the_wrong_sign_is_caught(monkeypatch):
+    orig = md.update_links
+    monkeypatch.setattr(md, "update_links", lambda U, P, eps: orig(U, P, -eps))
+    assert _fails(t_md.test_link_update_special_cases)
+
+
+def test_reunitarisation_without_conjugate_is_caught(monkeypatch):
+    def reunit_noconj(U):
+        r0 = U[..., 0, :] / np.linalg.norm(U[..., 0, :], axis=-1, keepdims=True)
+        r1 = U[..., 1, :] - np.sum(np.conj(r0) * U[..., 1, :], axis=-1, keepdims=True) * r0
+        r1 = r1 / np.linalg.norm(r1, axis=-1, keepdims=True)
+        return np.stack([r0, r1, np.cross(r0, r1)], axis=-2)
+    monkeypatch.setattr(md, "reunitarise", reunit_noconj)
+    assert _fails(t_md.test_link_update_special_cases)
