@@ -122,7 +122,7 @@ __device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Rea
 }
 
 template <int P, int RECON>
-__global__ void __launch_bounds__(128) cg_persistent_kernel(PersistentCGArgs Q) {
+__global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs Q) {
   using R = typename Real<P>::T;
   constexpr int PR = P == 64 ? 64 : 32;
   using RR = typename Real<PR>::T;
