@@ -966,8 +966,9 @@ qcd_status launch_persistent(qcd_ctx* c, const SolverFields& f, int iter_limit, 
   q.bar_err = reinterpret_cast<int*>(c->pc_bar + 2);
   q.iter_limit = iter_limit;
   q.round_out = c->pc_rounds + round;
+  // the arrival counter restarts with every launch; the error word is cleared once per batch of
+  // rounds (cg_batch), so that a timed-out round stops every later one at its first barrier
   CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, sizeof(unsigned), c->st));
-  CUDA_TRY(cudaMemsetAsync(c->pc_bar + 2, 0, sizeof(unsigned), c->st));
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (c->prof_on) {
     ea = prof_event(c);
@@ -1094,6 +1095,7 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
     int rounds = 0;
     if (use_pc) {
       rounds = predict_rounds(c, prm, done_iters == 0, rho[0]);
+      CUDA_TRY(cudaMemsetAsync(c->pc_bar + 2, 0, sizeof(unsigned), c->st));
       for (int k = 0; k < rounds; k++) {
         if ((s = launch_persistent(c, f, prm->max_iter, k))) return s;
         ItGraph* rk;

@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
   __shared__ cx<R> part[4][12][32];
   __shared__ uint4 stage[Stage<P, EPI_XPAY_CG>::U4];  // the largest staging of the three epilogues
   const CGState st0 = *Q.cg;
-  if (!st0.active || Q.ctl->halt || st0.iters >= Q.iter_limit) {
+  // an earlier launch of the batch whose barrier gave up leaves *bar_err set: do nothing
+  if (!st0.active || Q.ctl->halt || st0.iters >= Q.iter_limit || *reinterpret_cast<volatile int*>(Q.bar_err)) {
     if (Q.round_out && blockIdx.x == 0 && threadIdx.x == 0) *Q.round_out = 0;
     return;
   }
