@@ -1081,6 +1081,14 @@ qcd_status cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, const qc
   launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->st);
 
   std::vector<double> rho(nrhs, c->last_rho);
+  // event pairs of persistent launches and graphs left by a solve that returned early (an error)
+  // are dropped
+  for (const auto& pp : c->pc_pending) {
+    c->ev_free.push_back(pp.a);
+    c->ev_free.push_back(pp.b);
+  }
+  c->pc_pending.clear();
+  c->launched.clear();
   // one RHS: the persistent kernel runs each segment of iterations, and the rounds (segment, gated
   // reliable update) expected before convergence are enqueued together, with one look at the state
   // after them
