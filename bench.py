@@ -41,7 +41,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Dslash GFLOPS & HBM GB/s; time to 1e-8 CG solve, mixed vs FP64, 1 GB300"
-# FP64 peak of GB300 derived from its unit counts and clock: 2 FP64 FMA / clock / SM x 152 SMs x 2.07 GHz
+# FP64 peak of GB300 derived from its unit counts and clock (2 FP64 FMA / clock / SM x 152 SMs x
+# 2.07 GHz), reported beside the probe's measured figure, which the ALU rooflines divide by
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 WORKLOAD = "c1_16^4"
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel, with the summary
@@ -66,8 +67,9 @@ def parse():
                     help="skip the 32^3x64 8-RHS batched-mixed vs sequential-FP64 solve comparison")
     ap.add_argument("--no-md", action="store_true",
                     help="skip the clover-determinant, full-solve and R-algorithm sections")
-    ap.add_argument("--only", default=None, choices=[None, "dslash"],
-                    help="dslash: only apply Mhat^dag Mhat (FP32 and FP64) a few times, for profiler captures")
+    ap.add_argument("--only", default=None, choices=[None, "dslash", "peaks"],
+                    help="dslash: only apply Mhat^dag Mhat (FP32 and FP64) a few times, for profiler captures; "
+                         "peaks: only measure the FP64 / FP32 FMA and L2 copy denominators")
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides for --only dslash")
     ap.add_argument("--precs", default="32,64", help="precisions for --only dslash")
     return ap.parse_args()
@@ -95,15 +97,15 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, device_id):
+        self.device_id = device_id  # what nvidia-smi -i selects: the GPU's UUID, else its PCI bus id
         self.proc = None
         self.lines = []
         self.thread = None
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device_id), "--query-gpu=" + self.QUERY,
                                           "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
@@ -144,7 +146,22 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "device": str(self.device_id)}
+
+
+def smi_device_id(dev):
+    """The nvidia-smi selector of torch device `dev`: its UUID ("GPU-..."), else its PCI bus id, so that
+    the clocks sampled are this GPU's even when CUDA_VISIBLE_DEVICES renumbers the devices."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None and str(uuid):
+        u = str(uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    bus = getattr(props, "pci_bus_id", None)
+    if bus is not None:
+        return "%08X:%02X:%02X.0" % (getattr(props, "pci_domain_id", 0), bus, getattr(props, "pci_device_id", 0))
+    return str(dev.index if hasattr(dev, "index") else dev)
 
 
 def max_over_ranks(x, device=None):
@@ -169,6 +186,11 @@ def run_ours(args, world, rank, local):
     from paper_0910_0262_gb300 import qcd as Q
 
     build.build()
+    # the oracle's full hot-path steps (the CPU-baseline leg) run in spawned processes on host cores of
+    # their own while the GPU sections run; started before the first GPU call
+    jobs = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        jobs = OracleJobs([(args.workload, True), ("c0_8x8x16x16", False)])
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = workload_params(args.workload)
@@ -214,7 +236,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize(dev)
 
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(smi_device_id(dev))
     sampler.start()
     Q.qcd_profile(op.ctx, 1)
     if world > 1:
@@ -239,6 +261,7 @@ def run_ours(args, world, rank, local):
 
     if world > 1:
         ms_per_step = max_over_ranks(ms_per_step, dev)
+    x_mixed, F_step = x.clone(), F.clone()  # the last timed step's solution and force
 
     # plain FP64 GPU solve on the same lattice, for the mixed-vs-FP64 comparison
     fp64 = Q.solver_params(tol=1e-8, inner_prec=64, max_iter=20000)
@@ -258,7 +281,8 @@ def run_ours(args, world, rank, local):
         prof64 = Q.qcd_profile_read(op.ctx)
         Q.qcd_profile(op.ctx, 0)
 
-    result = dict(metric=METRIC, value=ms_per_step * 1.0, unit="ms per hot-path step (16^4, solve to 1e-8)")
+    x_fp64 = x.clone()
+    result = dict(metric=METRIC, value=ms_per_step * 1.0, unit=step_unit(w))
     solve_mixed = float(np.mean(parts[:, 2]))
     solve64 = None if args.no_fp64 else float(np.mean(times64))
 
@@ -280,6 +304,7 @@ def run_ours(args, world, rank, local):
     except OSError:
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    device_peaks = measure_device_peaks(Q)
     total_launches = next((p["launches"] for p in prof if p["name"] == "launches_total"), None)
     # per-step device time of each kernel class: sampled average duration x launches per step
     per_step_launches = {"dslash_p32": 4 * iters, "dslash_p64": 4 * max(stats[0].reliable_updates, 0),
@@ -314,38 +339,46 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "wall_s_timed_region": wall,
     })
+    result["device_peaks"] = device_peaks
     # roofline of the kernel with the largest device time per step
     dk = classes[dominant]
-    if dominant == "dslash_p32" or dominant.startswith("cg_persistent_p32") or dominant.startswith("cg_persistent_p16"):
-        tr = NCU_TRAFFIC.get(dominant)
-        result["roofline"] = {"kernel": dominant, "bound": "hbm", "achieved": dk["gbs"], "peak": hbm_peak,
-                              "unit": "GB/s", "frac": dk["gbs"] / hbm_peak,
-                              "traffic": None if tr is None else tr[0],
-                              "algorithmic_bytes_per_launch": dk["bytes_per_launch"],
-                              "traffic_source": None if tr is None else tr[1],
-                              "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    tr = NCU_TRAFFIC.get(dominant)
+    common = {"kernel": dominant, "traffic": None if tr is None else tr[0],
+              "traffic_source": None if tr is None else tr[1],
+              "algorithmic_bytes_per_launch": dk["bytes_per_launch"]}
+    if dominant.startswith("cg_persistent") and dominant != "cg_persistent_p64" and V_HALF(w) <= L2_RESIDENT_VH:
+        # the persistent iteration's working set (links, clover pair, six spinor fields) stays in the
+        # 129 MB L2 at this size (ncu: DRAM traffic a few percent of the algorithmic bytes), so its
+        # roofline is the measured L2-resident copy bandwidth; its fraction of HBM is given beside it
+        result["roofline"] = dict(common, bound="l2", achieved=dk["gbs"], peak=device_peaks["l2_copy_gbs"],
+                                  unit="GB/s", frac=dk["gbs"] / device_peaks["l2_copy_gbs"],
+                                  peak_source="L2-resident copy measured in this run (of measured)",
+                                  hbm_peak=hbm_peak, hbm_frac=dk["gbs"] / hbm_peak)
+    elif dominant.startswith("dslash_p32") or dominant.startswith("cg_persistent"):
+        result["roofline"] = dict(common, bound="hbm", achieved=dk["gbs"], peak=hbm_peak, unit="GB/s",
+                                  frac=dk["gbs"] / hbm_peak, peak_source="MEASURED_PEAKS.json hbm_gbs (of measured)")
     else:
-        fp64_peak = FP64_PEAK_TFLOPS * 1e3
-        tr = NCU_TRAFFIC.get(dominant)
-        result["roofline"] = {"kernel": dominant, "bound": "alu", "achieved": dk["gflops"] / 1e3,
-                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": dk["gflops"] / fp64_peak,
-                              "traffic": None if tr is None else tr[0],
-                              "traffic_source": None if tr is None else tr[1],
-                              "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (derived; probe measured 1.19)"}
-    result["roofline_dslash_fp32_in_solve"] = {"bound": "hbm", "achieved": d32["gbs"], "peak": hbm_peak,
-                                               "unit": "GB/s", "frac": d32["gbs"] / hbm_peak,
-                                               "note": "16^4 working set is L2-resident inside a solve"}
+        p64 = device_peaks["fp64_tflops"]
+        result["roofline"] = dict(common, bound="alu", achieved=dk["gflops"] / 1e3, peak=p64, unit="TFLOP/s",
+                                  frac=dk["gflops"] / 1e3 / p64,
+                                  peak_source="FP64 FMA probe measured in this run (of measured)")
     if not args.no_md:
         result["clover_det_and_full_solve"] = clover_det_section(op, x, b, stream)
         result["r_algorithm_step"] = r_step_section(op, U, w, stream)
     if not args.no_hbm or not args.no_batched:
-        result.update(large_volume(dev, hbm_peak, not args.no_hbm, not args.no_batched))
+        result.update(large_volume(dev, hbm_peak, not args.no_hbm, not args.no_batched, jobs is not None))
     if not args.no_hbm:
-        result["dslash_largest_volume"] = largest_volume(dev, hbm_peak)
+        result["dslash_largest_volume"] = largest_volume(dev, hbm_peak, jobs is not None)
     if not args.no_e2e:
         result["e2e"] = run_e2e(op, U_np, b_np, w, stream, dev)
-    if rank == 0 and world == 1 and not args.no_cpu:
-        result["cpu_baseline"] = cpu_baseline(w, iters)
+    if jobs is not None:
+        cn = lambda t: t.detach().cpu().numpy()
+        gpu = {"mhat": {p: cn(op.dslash(b, Q.QCD_OP_MHAT, precision=p))[0] for p in (64, 32, 16)},
+               "x_mixed": cn(x_mixed)[0], "x_fp64": cn(x_fp64)[0], "F_step": cn(F_step),
+               "force_from": lambda xo: cn(op.fermion_force(torch.from_numpy(xo[None]).to(dev),
+                                                            input_is_solution=True)[0])}
+        result["cpu_baseline"], result["errors"] = cpu_baseline(jobs, args.workload, gpu)
+        jobs.close()
     op.close()
     return result
 
@@ -457,7 +490,26 @@ def dslash_bandwidth(op, b, hbm_peak, rhs_list, warmup=5, reps=20):
     return out
 
 
-def large_volume(dev, hbm_peak, do_hbm, do_batched):
+def sampled_mhat_errors(op, U_np, b, dims, kappa, csw, t_bc, nsites=32, seed=11):
+    """Relative L2 error of the GPU's Mhat (FP64, FP32, FP16) on the first RHS against the oracle's
+    single-site Mhat at nsites sampled even sites (the first and last half index among them)."""
+    from paper_0910_0262_gb300 import qcd as Q
+    vh = b.shape[1]
+    sites = np.unique(np.concatenate([[0, vh - 1], np.random.default_rng(seed).choice(vh, nsites - 2)]))
+    b0 = b[:1].contiguous()
+    want = oracle_sampled_mhat(U_np, b0[0].cpu().numpy(), dims, sites, kappa, csw, t_bc)
+    idx = torch_index(sites, b.device)
+    return {f"mhat_fp{p}_vs_oracle_sampled": rel_l2(op.dslash(b0, Q.QCD_OP_MHAT, precision=p)[0][idx].cpu().numpy(),
+                                                     want)
+            for p in (64, 32, 16)} | {"sites": int(len(sites))}
+
+
+def torch_index(a, device):
+    import torch
+    return torch.as_tensor(np.asarray(a, dtype=np.int64), device=device)
+
+
+def large_volume(dev, hbm_peak, do_hbm, do_batched, do_errors=False):
     """32^3 x 64 lattice (eps 0.15, seed 4, 8 RHS; working set far above the 129 MB L2).
 
     dslash_large_volume: Mhat^dag Mhat in FP32 and FP16 with 12-real links, 1 and 8 RHS
@@ -481,33 +533,66 @@ def large_volume(dev, hbm_peak, do_hbm, do_batched):
         res["dslash_large_volume"] = {"dims": list(dims), "op": "Mhat^dag Mhat (4 hopping launches with fused "
                                       "clover epilogues)", "peak_gbs": hbm_peak,
                                       "results": dslash_bandwidth(op, b, hbm_peak, (1, 8))}
+        if do_errors:
+            res["dslash_large_volume"]["errors"] = sampled_mhat_errors(op, U_np, b, dims, 0.12, 1.0, -1.0)
     if do_batched:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         kw = dict(tol=1e-8, reliable_every=50, reliable_delta=0.1)
+
+        def timed(fn):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return out, e0.elapsed_time(e1)
+
         op.cg_solve(b[:1], inner_prec=16, **kw)  # warm up graph capture
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        xb, stb, okb = op.cg_solve(b, inner_prec=16, **kw)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        t_batched = e0.elapsed_time(e1)
-        e0.record(stream)
-        seq = [op.cg_solve(b[r:r + 1].contiguous(), inner_prec=64, **kw) for r in range(b.shape[0])]
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        t_seq = e0.elapsed_time(e1)
+        op.cg_solve(b, inner_prec=16, **kw)
+        (xb, stb, okb), t_batched = timed(lambda: op.cg_solve(b, inner_prec=16, **kw))
+        # where the batched solve's time goes: the library's per-launch events in one more (profiled) solve
+        op.profile(True)
+        _, t_prof = timed(lambda: op.cg_solve(b, inner_prec=16, **kw))
+        prof = op.profile_read()
+        op.profile(False)
+        seq16, t_seq16 = timed(lambda: [op.cg_solve(b[r:r + 1].contiguous(), inner_prec=16, **kw)
+                                        for r in range(b.shape[0])])
+        seq, t_seq = timed(lambda: [op.cg_solve(b[r:r + 1].contiguous(), inner_prec=64, **kw)
+                                    for r in range(b.shape[0])])
+        n_it = max(s["iters"] for s in stb)
+
+        def cls(prefix):
+            rows = [p for p in prof if p["name"].startswith(prefix)]
+            return sum(p["total_ms"] for p in rows), sum(p["launches"] for p in rows)
+
+        hop_ms, hop_n = cls("dslash_p16")
+        pu_ms, pu_n = cls("p_update")
+        rel_ms, rel_n = cls("dslash_p64")
+        parts = {"inner_hopping_fp16": hop_ms / max(hop_n, 1) * 4 * n_it,
+                 "inner_p_update": pu_ms / max(pu_n, 1) * n_it,
+                 "reliable_update_hopping_fp64": rel_ms}
+        parts["rest"] = t_prof - sum(parts.values())
         res["batched_solve"] = {
             "dims": list(dims), "nrhs": int(b.shape[0]),
-            "batched_mixed_fp16_ms": t_batched, "sequential_fp64_ms": t_seq, "speedup": t_seq / t_batched,
-            "batched_iters": [s["iters"] for s in stb], "batched_true_rel_resid": max(s["true_rel_resid"] for s in stb),
+            "batched_mixed_fp16_ms": t_batched, "sequential_mixed_fp16_ms": t_seq16, "sequential_fp64_ms": t_seq,
+            "speedup": t_seq / t_batched, "batching_gain_vs_sequential_mixed": t_seq16 / t_batched,
+            "batched_iters": [s["iters"] for s in stb], "batched_reliable_updates": stb[0]["reliable_updates"],
+            "batched_true_rel_resid": max(s["true_rel_resid"] for s in stb),
+            "sequential_mixed_iters": [s[1][0]["iters"] for s in seq16],
+            "sequential_mixed_true_rel_resid": max(s[1][0]["true_rel_resid"] for s in seq16),
             "sequential_iters": [s[1][0]["iters"] for s in seq],
             "sequential_true_rel_resid": max(s[1][0]["true_rel_resid"] for s in seq),
-            "converged": bool(okb and all(s[2] for s in seq))}
+            "converged": bool(okb and all(s[2] for s in seq) and all(s[2] for s in seq16)),
+            "breakdown_ms": {"profiled_solve_ms": t_prof, **parts,
+                             "how": "per-launch CUDA events of the library (inner kernels sampled on the first "
+                                    "iteration of each graph, times the iterations run; every reliable-update "
+                                    "launch); rest = the profiled solve's time minus these: the reliable "
+                                    "updates' BLAS, launch gaps and host looks at the solver state"}}
     op.close()
     return res
 
 
-def largest_volume(dev, hbm_peak):
+def largest_volume(dev, hbm_peak, do_errors=False):
     """48^3 x 96 lattice (eps 0.15, seed 5, 4 RHS; 10.6 M sites): the hopping-kernel bandwidth of
     Mhat^dag Mhat in FP32 and FP16 for 1 and 4 RHS (dslash_bandwidth)."""
     import torch
@@ -518,11 +603,14 @@ def largest_volume(dev, hbm_peak):
     U_np, b_np = synth.make_problem(dims, w["eps"], w["seed"], w["nrhs"])
     op = Q.CloverWilson(dims, -1.0, stream=torch.cuda.current_stream(dev))
     op.load_gauge(torch.from_numpy(U_np).to(dev), recon12=True)
-    del U_np
+    if not do_errors:
+        del U_np
     op.clover_build(0.12, 1.0)
     b = torch.from_numpy(b_np).to(dev)
     res = {"dims": list(dims), "op": "Mhat^dag Mhat (4 hopping launches with fused clover epilogues)",
            "peak_gbs": hbm_peak, "results": dslash_bandwidth(op, b, hbm_peak, (1, 4))}
+    if do_errors:
+        res["errors"] = sampled_mhat_errors(op, U_np, b, dims, 0.12, 1.0, -1.0)
     op.close()
     return res
 
@@ -558,55 +646,189 @@ def run_e2e(op, U_np, b_np, w, stream, dev):
 
 
 # ------------------------------------------------------------ CPU oracle --
-def cpu_baseline(w, gpu_iters, cg_sample_iters=4):
-    """The numpy FP64 oracle on the host: clover term + inverse, cg_sample_iters CG iterations
-    (each one Mhat^dag Mhat plus BLAS) and the force, then scaled to a full step with the
-    iteration count of the GPU mixed solve."""
+# The CPU-baseline leg and the reference arm: the numpy FP64 oracle as it stands (oracle/), timed on
+# the host cores, one thread per job (the BLAS / OpenMP pools are pinned to one thread above).  No
+# other part of this file imports oracle/.
+
+def _host_cores():
+    try:
+        return sorted(os.sched_getaffinity(0))
+    except AttributeError:
+        return list(range(os.cpu_count() or 1))
+
+
+def oracle_hot_path(name, out_dir=None, with_force=True, tick=None):
+    """One hot-path step of the oracle on workload `name`, on the calling thread: the clover term and
+    its inverse (SchurOperator), the CG of oracle.cg on Mhat^dag Mhat to a true relative residual of
+    1e-8 with the oracle's own iteration count, and the force from that solution; each part timed by
+    the wall clock.  tick() (optional) is called before each unit of work: the clover build, every
+    Mhat^dag Mhat application of the CG, the force.  With out_dir the solution (x), the force (F) and
+    Mhat b (Mb, timed separately as one operator application) are saved there as <name>_<key>.npy."""
     from paper_0910_0262_gb300 import synth
-    from oracle import evenodd, force as oforce
+    from oracle import evenodd, cg as ocg, force as oforce
+    w = workload_params(name)
     U, b = synth.make_problem(w["dims"], w["eps"], w["seed"], w["nrhs"])
+    tick = tick or (lambda: None)
+    tick()
     t0 = time.perf_counter()
     op = evenodd.SchurOperator(U, w["kappa"], w["csw"], w["t_bc"])
     t_clover = time.perf_counter() - t0
+    applications = [0]
+
+    def apply_A(v):
+        tick()
+        applications[0] += 1
+        return op.MdagM(v)
+
     t0 = time.perf_counter()
-    r = b[0].copy()
-    p = r.copy()
-    xx = np.zeros_like(r)
-    rr = np.vdot(r, r).real
-    for _ in range(cg_sample_iters):
-        Ap = op.MdagM(p)
-        a = rr / np.vdot(p, Ap).real
-        xx += a * p
-        r -= a * Ap
-        rn = np.vdot(r, r).real
-        p = r + (rn / rr) * p
-        rr = rn
-    t_it = (time.perf_counter() - t0) / cg_sample_iters
-    t0 = time.perf_counter()
-    oforce.lie_force(U, oforce.gradient(op, xx))
-    t_force = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    op.Mhat(b[0])
-    t_mhat = time.perf_counter() - t0
-    est = t_clover + t_it * gpu_iters + t_force
+    x, iters, true_res = ocg.cg(apply_A, b[0], tol=1e-8)
+    t_solve = time.perf_counter() - t0
+    res = {"workload": name, "dims": list(w["dims"]), "clover_s": t_clover, "solve_s": t_solve, "cg_iters": iters,
+           "mdagm_applications": applications[0], "true_rel_resid": true_res}
+    if with_force:
+        tick()
+        t0 = time.perf_counter()
+        F = oforce.lie_force(U, oforce.gradient(op, x))
+        res["force_s"] = time.perf_counter() - t0
+    res["step_s"] = t_clover + t_solve + res.get("force_s", 0.0)
+    if out_dir is not None:
+        t0 = time.perf_counter()
+        Mb = op.Mhat(b[0])
+        res["mhat_apply_s"] = time.perf_counter() - t0
+        np.save(os.path.join(out_dir, f"{name}_x.npy"), x)
+        np.save(os.path.join(out_dir, f"{name}_Mb.npy"), Mb)
+        if with_force:
+            np.save(os.path.join(out_dir, f"{name}_F.npy"), F)
+    return res
+
+
+def _oracle_job(name, out_dir, core, with_force):
+    """Body of one spawned oracle process: pinned to `core`, writes <name>.json (and the arrays)."""
+    if core is not None:
+        try:
+            os.sched_setaffinity(0, {core})
+        except (AttributeError, OSError):
+            core = None
     try:
-        cores = len(os.sched_getaffinity(0))
-    except AttributeError:
-        cores = os.cpu_count()
-    # the oracle's Mhat on the large lattices, scaled by volume from the timed application (the numpy
-    # operator is vectorised over sites, so its cost is linear in V); its solves there are not run
-    V = int(np.prod(w["dims"]))
-    large = {name: {"dims": list(synth.WORKLOADS[name]["dims"]),
-                    "mhat_apply_ms": t_mhat * 1e3 * np.prod(synth.WORKLOADS[name]["dims"]) / V,
-                    "solve": "not run"}
-             for name in ("c3_32^3x64", "c4_48^3x96")}
-    return {"value": est * 1e3, "unit": "ms per hot-path step (16^4, solve to 1e-8)", "cores": 1,
-            "cores_available": cores, "kind": "oracle",
-            "sample": f"clover+inverse once, {cg_sample_iters} CG iterations ({t_it:.2f} s each, scaled to the "
-                      f"{gpu_iters} iterations of the solve), force once; numpy FP64, one thread",
-            "mhat_apply_ms": t_mhat * 1e3,
-            "large_volumes": dict(large, note=f"one Mhat application timed on {'x'.join(map(str, w['dims']))} "
-                                              f"({t_mhat:.2f} s) and scaled by the site count")}
+        res = oracle_hot_path(name, out_dir, with_force)
+    except Exception as e:  # reported in the bench line instead of a number
+        res = {"error": repr(e)}
+    res["core"] = core
+    with open(os.path.join(out_dir, f"{name}.json"), "w") as f:
+        json.dump(res, f)
+
+
+class OracleJobs:
+    """Full hot-path steps of the oracle for the CPU baseline, each in a spawned process on a host
+    core of its own (the last cores of this process's affinity set), started before the first GPU
+    call and collected after the GPU sections."""
+
+    def __init__(self, jobs):
+        import multiprocessing as mp
+        import tempfile
+        self.dir = tempfile.mkdtemp(prefix="qcd_oracle_")
+        ctx = mp.get_context("spawn")
+        cores = _host_cores()
+        self.procs = {}
+        for k, (name, with_force) in enumerate(jobs):
+            core = cores[-1 - k] if len(cores) > len(jobs) else None
+            p = ctx.Process(target=_oracle_job, args=(name, self.dir, core, with_force), daemon=True)
+            p.start()
+            self.procs[name] = p
+
+    def result(self, name, timeout=1200.0):
+        p = self.procs[name]
+        p.join(timeout)
+        if p.is_alive():
+            p.terminate()
+            return {"error": f"oracle job {name} did not finish in {timeout:.0f} s"}
+        try:
+            with open(os.path.join(self.dir, f"{name}.json")) as f:
+                return json.load(f)
+        except OSError:
+            return {"error": f"oracle job {name} exited with {p.exitcode} and no result"}
+
+    def array(self, name, key):
+        return np.load(os.path.join(self.dir, f"{name}_{key}.npy"))
+
+    def close(self):
+        import shutil
+        for p in self.procs.values():
+            if p.is_alive():
+                p.terminate()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def rel_l2(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def oracle_true_residual(name, x):
+    """|b - Mhat^dag Mhat x| / |b| of a GPU solution x of workload `name`, recomputed by the oracle."""
+    from paper_0910_0262_gb300 import synth
+    from oracle import evenodd
+    w = workload_params(name)
+    U, b = synth.make_problem(w["dims"], w["eps"], w["seed"], w["nrhs"])
+    op = evenodd.SchurOperator(U, w["kappa"], w["csw"], w["t_bc"])
+    return rel_l2(op.MdagM(x), b[0])
+
+
+def oracle_sampled_mhat(U, v, dims, sites, kappa, csw, t_bc):
+    """Mhat v at the sampled even half indices `sites`, evaluated one site at a time by the oracle's
+    single-site operator (lattices too large for the whole-lattice oracle)."""
+    from oracle import local
+    out = []
+    for h in sites:
+        i = next(i for i in (2 * int(h), 2 * int(h) + 1) if sum(local.coords(dims, i)) % 2 == 0)
+        out.append(local.mhat_site(U, v, dims, local.coords(dims, i), kappa, csw, t_bc))
+    return np.array(out)
+
+
+def cpu_baseline(jobs, name, gpu):
+    """The CPU-baseline leg of the GPU arm: the oracle's measured hot-path steps (jobs started by
+    run_ours) and the error of every GPU result of the step's workload against the oracle's.
+
+    gpu: numpy copies of the GPU results on workload `name` -- "mhat" {precision: Mhat b}, "x_mixed",
+    "x_fp64", "F_step" (force from the mixed solution) -- and "force_from" (a function returning the
+    GPU force for a given solution, evaluated here on the oracle's own solution)."""
+    c1 = jobs.result(name)
+    c0 = jobs.result("c0_8x8x16x16")
+    cores = _host_cores()
+    out = {"unit": step_unit(workload_params(name)), "kind": "oracle", "cores": 1,
+           "cores_available": len(cores)}
+    if "error" in c1:
+        out.update(value=None, sample=c1["error"])
+        return out, {}
+    out.update({
+        "value": c1["step_s"] * 1e3,
+        "sample": f"one full hot-path step of the numpy FP64 oracle on {'x'.join(map(str, c1['dims']))}: clover "
+                  f"term + inverse, CG to a true residual of 1e-8 ({c1['cg_iters']} iterations, "
+                  f"{c1['mdagm_applications']} Mhat^dag Mhat applications, true residual "
+                  f"{c1['true_rel_resid']:.2e}), force; one thread, measured (nothing scaled)",
+        "parts_s": {k: c1[k] for k in ("clover_s", "solve_s", "force_s")},
+        "s_per_cg_iteration": c1["solve_s"] / max(c1["mdagm_applications"], 1),
+        "mhat_apply_ms": c1["mhat_apply_s"] * 1e3, "core": c1["core"],
+        "c0_8x8x16x16_solve": c0 if "error" in c0 else {
+            "solve_ms": c0["solve_s"] * 1e3, "clover_ms": c0["clover_s"] * 1e3, "cg_iters": c0["cg_iters"],
+            "true_rel_resid": c0["true_rel_resid"], "core": c0["core"]},
+    })
+    x_or = jobs.array(name, "x")
+    F_or = jobs.array(name, "F")
+    Mb_or = jobs.array(name, "Mb")
+    errors = {"reference": f"numpy FP64 oracle on {name}; relative L2 over the whole field"}
+    for prec, y in sorted(gpu["mhat"].items()):
+        errors[f"mhat_fp{prec}_vs_oracle"] = rel_l2(y, Mb_or)
+    errors["solution_mixed_vs_oracle_solution"] = rel_l2(gpu["x_mixed"], x_or)
+    errors["solution_fp64_vs_oracle_solution"] = rel_l2(gpu["x_fp64"], x_or)
+    errors["true_rel_resid_mixed_by_oracle"] = oracle_true_residual(name, gpu["x_mixed"])
+    errors["force_kernels_vs_oracle_same_solution"] = rel_l2(gpu["force_from"](x_or), F_or)
+    errors["force_step_vs_oracle"] = rel_l2(gpu["F_step"], F_or)
+    errors["note"] = ("two solutions to a residual of 1e-8 differ by up to the condition number times 1e-8, "
+                      "so the step's force differs from the oracle's by as much; the force kernels on one "
+                      "solution agree to rounding")
+    return out, errors
 
 
 def step_config(name, w, world):
@@ -618,29 +840,111 @@ def step_config(name, w, world):
             "parallelism": f"replicas x{world}"}
 
 
+def step_unit(w):
+    """The metric's unit for workload w (the same string in both arms)."""
+    d = w["dims"]
+    lat = f"{d[0]}^4" if len(set(d)) == 1 else "x".join(map(str, d))
+    return f"ms per hot-path step ({lat}, solve to 1e-8)"
+
+
+def V_HALF(w):
+    return int(np.prod(w["dims"])) // 2
+
+
+# half volume up to which a single-RHS iteration's working set (about 1.6 kB per even site at FP32
+# with 12-real links) stays in the 129 MB L2
+L2_RESIDENT_VH = 1 << 16
+
+
+def measure_device_peaks(Q):
+    """The rooflines' ALU and L2 denominators, measured here with the library's probes (CUDA events):
+    FP64 and FP32 FMA throughput, and the bandwidth of a copy between two 24 MiB buffers (48 MiB in
+    L2), beside the derived FP64 figure of the unit counts and the maximum clock."""
+    return {"fp64_tflops": Q.qcd_probe_fma_peak(64), "fp32_tflops": Q.qcd_probe_fma_peak(32),
+            "l2_copy_gbs": Q.qcd_probe_copy_bandwidth(24 << 20, 20),
+            "fp64_tflops_derived": FP64_PEAK_TFLOPS,
+            "how": "qcd_probe_fma_peak (8 FMA chains per thread, 8 x 256 threads per SM) and "
+                   "qcd_probe_copy_bandwidth (24 MiB -> 24 MiB, 32 passes per launch, read + write bytes)"}
+
+
 # -------------------------------------------------------------- reference --
+class SliceRunner:
+    """Runs fn(tick) on a worker thread in consecutive slices: each run_slice(n) lets the worker pass
+    n more calls of tick() (None: run to the end) and returns the wall time the slice took."""
+
+    def __init__(self, fn):
+        self._go = threading.Semaphore(0)
+        self._parked = threading.Semaphore(0)
+        self._left = 0
+        self.finished = False
+        self.result = None
+        self.error = None
+        self._thread = threading.Thread(target=self._run, args=(fn,), daemon=True)
+        self._thread.start()
+        self._parked.acquire()  # the worker waits at its first tick
+
+    def _tick(self):
+        if self._left == 0:
+            self._parked.release()
+            self._go.acquire()
+        self._left -= 1
+
+    def _run(self, fn):
+        try:
+            self.result = fn(self._tick)
+        except BaseException as e:  # re-raised by the caller
+            self.error = e
+        self.finished = True
+        self._parked.release()
+
+    def run_slice(self, n=None):
+        if self.finished:
+            return 0.0
+        self._left = (1 << 60) if n is None else n
+        t0 = time.perf_counter()
+        self._go.release()
+        self._parked.acquire()
+        return time.perf_counter() - t0
+
+
 def run_reference(args, world, rank):
-    """The oracle arm: each step is a bounded sample of the same workload on the host cores."""
+    """The oracle arm: ONE full hot-path step of the numpy FP64 oracle on the workload (clover term and
+    inverse, CG to a true relative residual of 1e-8 with the oracle's own iteration count, force), on
+    one host thread, measured in `steps` consecutive timed slices: slice k < steps runs the next unit
+    of work (the clover build, one Mhat^dag Mhat application of the CG, the force), the last slice the
+    rest.  value = the sum of the slices = one measured hot-path step; ms_per_step = that sum / steps,
+    the mean duration of a timed slice.  Each warm-up step applies the oracle's Mhat once."""
+    from paper_0910_0262_gb300 import synth
+    from oracle import evenodd
     w = workload_params(args.workload)
-    vals = []
-    for k in range(args.warmup + args.steps):
-        r = cpu_baseline(w, gpu_iters=WORKLOAD_ITERS, cg_sample_iters=1)
-        if k >= args.warmup:
-            vals.append(r["value"])
-    v = float(np.mean(vals))
-    return {"impl": "reference", "metric": METRIC, "value": v, "unit": r["unit"], "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    U, b = synth.make_problem(w["dims"], w["eps"], w["seed"], w["nrhs"])
+    if args.warmup:
+        op = evenodd.SchurOperator(U, w["kappa"], w["csw"], w["t_bc"])
+        for _ in range(args.warmup):
+            op.Mhat(b[0])
+        del op
+    del U, b
+    runner = SliceRunner(lambda tick: oracle_hot_path(args.workload, tick=tick))
+    slices = [runner.run_slice(1 if k < args.steps - 1 else None) for k in range(args.steps)]
+    if not runner.finished:
+        slices[-1] += runner.run_slice(None)
+    if runner.error is not None:
+        raise runner.error
+    r = runner.result
+    total_ms = 1e3 * float(np.sum(slices))
+    unit = step_unit(w)
+    sample = (f"one full hot-path step of the numpy FP64 oracle, measured in {args.steps} timed slices: clover term "
+              f"+ inverse, CG to a true residual of 1e-8 ({r['cg_iters']} iterations, {r['mdagm_applications']} "
+              f"Mhat^dag Mhat applications, true residual {r['true_rel_resid']:.2e}), force; one thread")
+    cores = 1
+    return {"impl": "reference", "metric": METRIC, "value": total_ms, "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": step_config(args.workload, w, world),
-            "cpu_baseline": {"value": v, "unit": r["unit"], "cores": 1, "kind": "oracle",
-                             "sample": r["sample"]},
-            "e2e": {"value": v, "unit": r["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-
-
-# CG iterations the 16^4 solve to 1e-8 takes (58 for the FP64 and the mixed solve alike, as the
-# GPU runs of this workload report): scales the oracle's per-iteration sample in the reference arm,
-# which runs no GPU solve to count them
-WORKLOAD_ITERS = 58
+            "timed": {"hot_path_steps": 1, "slices": args.steps, "slice_ms": [1e3 * t for t in slices],
+                      "parts_s": {k: r[k] for k in ("clover_s", "solve_s", "force_s")}},
+            "cpu_baseline": {"value": total_ms, "unit": unit, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": total_ms, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def run_dslash_only(args):
@@ -670,6 +974,13 @@ def main():
     world, rank, local = dist_env()
     if args.only == "dslash":
         run_dslash_only(args)
+        return
+    if args.only == "peaks":
+        from paper_0910_0262_gb300 import build
+        from paper_0910_0262_gb300 import qcd as Q
+        build.build()
+        print(json.dumps({"only": "peaks", **measure_device_peaks(Q),
+                          "hbm_copy_gbs_1GiB": Q.qcd_probe_copy_bandwidth(1 << 30, 10)}))
         return
     if args.impl == "reference":
         if rank == 0:

@@ -32,6 +32,9 @@
  * on the CUDA stream given to qcd_create.  qcd_load_gauge, qcd_clover_build,
  * qcd_cg_solve and qcd_fermion_force synchronise that stream before returning
  * (they report device-side status); qcd_dslash returns after enqueueing.
+ * A call that takes a context makes the context's device current while it runs
+ * and restores the caller's current device before it returns.  Each call is an
+ * NVTX range named after it (visible to Nsight tools; free without one).
  *
  * Errors.  Every call returns a qcd_status; on failure qcd_last_error() gives a
  * message for the calling thread.  No C++ exception crosses the ABI.  Argument
@@ -39,6 +42,8 @@
  */
 #ifndef QCD_H
 #define QCD_H
+
+#include <stddef.h>
 
 #ifdef __cplusplus
 extern "C" {
@@ -277,7 +282,9 @@ qcd_status qcd_profile_read(qcd_ctx* ctx, qcd_kernel_stat* out, int max_entries,
  * GPU loading the library holds until exit; lattices needing more than
  * 3 * 192 * V/2 bytes of it are rejected with QCD_ERR_ARG before any launch.  The
  * first call on a device looks up the array's device address for that device
- * (make it before any stream capture).  All calls share the array, which keeps
+ * (make it before any stream capture) and keeps it for the life of the process,
+ * which assumes that the device's primary context is not reset (cudaDeviceReset)
+ * while the library is loaded.  All calls share the array, which keeps
  * the last call's contents (each call writes everything it reads); calls whose
  * work overlaps on the GPU race on it.  Needs qcd_load_gauge and
  * qcd_clover_build (QCD_ERR_STATE otherwise).  Enqueued on the context's stream;
@@ -303,6 +310,19 @@ qcd_status qcd_selftest_barrier_timeout(qcd_ctx* ctx);
  * (0 on success); needs no GPU and no context.
  */
 long long qcd_selftest_fastdiv(void);
+
+/*
+ * Device-limit probes for the kernels' rooflines (the paper has no counterpart; it quotes the Cell's
+ * peak rates, Sec. 2, and measures its DMA bandwidths, Sec. 3).  Both run on the current device,
+ * ordered on cuda_stream (NULL: the legacy default stream), allocate their own buffers and
+ * synchronise.  qcd_probe_fma_peak: the FMA throughput in TFLOP/s (2 flops per FMA) of a kernel
+ * running 8 independent FMA chains per thread on every SM, in precision 64 or 32.
+ * qcd_probe_copy_bandwidth: the bandwidth in GB/s (bytes read + written) of a copy between two
+ * buffers of `bytes` each (a multiple of 16), timed over `reps` launches after one untimed launch;
+ * buffers of at most 64 MiB are copied 32 times per launch (an L2-resident copy), larger ones once.
+ */
+qcd_status qcd_probe_fma_peak(int precision, void* cuda_stream, double* tflops);
+qcd_status qcd_probe_copy_bandwidth(size_t bytes, int reps, void* cuda_stream, double* gbs);
 
 /* Message describing the last failed call on this thread ("" if none). */
 const char* qcd_last_error(void);

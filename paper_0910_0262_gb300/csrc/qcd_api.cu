@@ -21,6 +21,7 @@
 #include "qcd_dslash.cuh"
 #include "qcd_kernels.h"
 #include "qcd_force.h"
+#include "qcd_api_scope.h"
 
 using namespace qcd;
 
@@ -37,6 +38,11 @@ qcd_status fail(qcd_status s, const char* fmt, ...) {
   g_err = buf;
   return s;
 }
+
+// opens the call's ApiScope (NVTX range, the context's device current until the call returns)
+#define QCD_API_ENTER(name, ctx)                                      \
+  ApiScope api_scope_(name, (ctx) ? (ctx)->device : -1);              \
+  if (api_scope_.status() != QCD_OK) return api_scope_.status()
 
 #define CUDA_TRY(call)                                                                        \
   do {                                                                                        \
@@ -391,12 +397,6 @@ void apply_mdagm(qcd_ctx* c, int prec, int nrhs, const void* in, const float* in
   apply_mhat(c, prec, nrhs, true, y, y_n, out, out_n, t, t_n, nullptr, halt, gate);
 }
 
-qcd_status check_ctx(qcd_ctx* c) {
-  if (!c) return fail(QCD_ERR_ARG, "null context");
-  CUDA_TRY(cudaSetDevice(c->device));
-  return QCD_OK;
-}
-
 qcd_status sync_and_check(qcd_ctx* c, const char* what) {
   cudaError_t e = cudaStreamSynchronize(c->st);
   if (e == cudaSuccess) e = cudaGetLastError();
@@ -452,7 +452,19 @@ extern "C" {
 
 const char* qcd_last_error(void) { return g_err.c_str(); }
 
+static qcd_status create_ctx(qcd_ctx** out, const int dims[4], double t_bc, void* stream);
+
 qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* stream) {
+  nvtxRangePushA("qcd_create");
+  const qcd_status s = create_ctx(out, dims, t_bc, stream);
+  nvtxRangePop();
+  return s;
+}
+
+}  // extern "C"
+
+// the body of qcd_create, on the caller's current device
+static qcd_status create_ctx(qcd_ctx** out, const int dims[4], double t_bc, void* stream) {
   if (!out || !dims) return fail(QCD_ERR_ARG, "null argument");
   *out = nullptr;
   for (int k = 0; k < 4; k++)
@@ -532,9 +544,11 @@ qcd_status qcd_create(qcd_ctx** out, const int dims[4], double t_bc, void* strea
   return QCD_OK;
 }
 
+extern "C" {
+
 qcd_status qcd_destroy(qcd_ctx* c) {
   if (!c) return QCD_OK;
-  cudaSetDevice(c->device);
+  QCD_API_ENTER("qcd_destroy", c);
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
   void* dev[] = {c->g64, c->g32, c->g16, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, c->logdet, c->flags,
@@ -563,8 +577,8 @@ qcd_status qcd_destroy(qcd_ctx* c) {
 }
 
 qcd_status qcd_load_gauge(qcd_ctx* c, const double* U, int on_device, int flags) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_load_gauge", c);
+  qcd_status s = QCD_OK;
   if (!U) return fail(QCD_ERR_ARG, "null gauge pointer");
   if (flags & ~QCD_GAUGE_RECON12) return fail(QCD_ERR_ARG, "unknown gauge flags 0x%x", flags);
   const Geom& g = c->g;
@@ -598,8 +612,8 @@ qcd_status qcd_load_gauge(qcd_ctx* c, const double* U, int on_device, int flags)
 }
 
 qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_clover_build", c);
+  qcd_status s = QCD_OK;
   if (!c->have_gauge) return fail(QCD_ERR_STATE, "clover_build before load_gauge");
   if (!(kappa == kappa) || !(csw == csw)) return fail(QCD_ERR_ARG, "kappa/csw not finite");
   const Geom& g = c->g;
@@ -636,8 +650,8 @@ qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
 }
 
 qcd_status qcd_dslash(qcd_ctx* c, double* out, const double* in, int op, int dagger, int prec, int nrhs) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_dslash", c);
+  qcd_status s = QCD_OK;
   if (!out || !in) return fail(QCD_ERR_ARG, "null field pointer");
   if (op < QCD_OP_DSLASH_EO || op > QCD_OP_CLOVER_INV) return fail(QCD_ERR_ARG, "unknown op %d", op);
   if (!valid_prec(prec)) return fail(QCD_ERR_ARG, "precision must be 64, 32 or 16");
@@ -1225,8 +1239,8 @@ extern "C" {
 
 qcd_status qcd_cg_solve(qcd_ctx* c, double* x, const double* b, int nrhs, const qcd_solver_params* prm,
                         qcd_solver_stats* stats) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_cg_solve", c);
+  qcd_status s = QCD_OK;
   if (!x || !b) return fail(QCD_ERR_ARG, "null field pointer");
   if (nrhs < 1) return fail(QCD_ERR_ARG, "nrhs must be >= 1");
   if ((s = check_params(prm))) return s;
@@ -1251,8 +1265,8 @@ qcd_status qcd_cg_solve(qcd_ctx* c, double* x, const double* b, int nrhs, const 
 
 qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int nrhs, int flags,
                              const qcd_solver_params* prm, qcd_solver_stats* stats) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_fermion_force", c);
+  qcd_status s = QCD_OK;
   const bool det = (flags & QCD_FORCE_CLOVER_DET) != 0;
   if (!F || (!phi_or_x && nrhs > 0)) return fail(QCD_ERR_ARG, "null pointer");
   if (nrhs < (det ? 0 : 1)) return fail(QCD_ERR_ARG, "nrhs must be >= 1 (>= 0 with QCD_FORCE_CLOVER_DET)");
@@ -1358,8 +1372,8 @@ qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int 
 }
 
 qcd_status qcd_selftest_barrier_timeout(qcd_ctx* c) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_selftest_barrier_timeout", c);
+  qcd_status s = QCD_OK;
   CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 4 * sizeof(unsigned), c->st));
   CUDA_TRY(launch_barrier_probe(c->pc_bar, reinterpret_cast<int*>(c->pc_bar + 2), c->st));
   CUDA_TRY(cudaMemcpyAsync(c->h_flags + 2, c->pc_bar + 2, sizeof(int), cudaMemcpyDeviceToHost, c->st));
@@ -1370,8 +1384,8 @@ qcd_status qcd_selftest_barrier_timeout(qcd_ctx* c) {
 }
 
 qcd_status qcd_clover_logdet(qcd_ctx* c, double out[2]) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_clover_logdet", c);
+  qcd_status s = QCD_OK;
   if (!out) return fail(QCD_ERR_ARG, "null pointer");
   if (!c->have_clover) return fail(QCD_ERR_STATE, "clover_logdet before clover_build");
   launch_parity_sum(c->g, c->logdet, reduce_args(c, FIN_STORE), c->st);
@@ -1384,8 +1398,6 @@ qcd_status qcd_clover_logdet(qcd_ctx* c, double out[2]) {
 
 // shared checks of the two full-lattice helpers
 static qcd_status eo_check(qcd_ctx* c, const void* out, const void* in1, const void* in2, int nrhs) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
   if (!out || !in1) return fail(QCD_ERR_ARG, "null field pointer");
   if (nrhs < 1) return fail(QCD_ERR_ARG, "nrhs must be >= 1");
   if (!c->have_clover) return fail(QCD_ERR_STATE, "needs clover_build");
@@ -1397,6 +1409,7 @@ static qcd_status eo_check(qcd_ctx* c, const void* out, const void* in1, const v
 }
 
 qcd_status qcd_prepare_source(qcd_ctx* c, double* bhat_e, const double* b_e, const double* b_o, int nrhs) {
+  QCD_API_ENTER("qcd_prepare_source", c);
   qcd_status s = eo_check(c, bhat_e, b_e, b_o, nrhs);
   if (s) return s;
   const Geom& g = c->g;
@@ -1429,6 +1442,7 @@ qcd_status qcd_prepare_source(qcd_ctx* c, double* bhat_e, const double* b_e, con
 }
 
 qcd_status qcd_reconstruct_odd(qcd_ctx* c, double* x_o, const double* x_e, const double* b_o, int nrhs) {
+  QCD_API_ENTER("qcd_reconstruct_odd", c);
   qcd_status s = eo_check(c, x_o, x_e, b_o, nrhs);
   if (s) return s;
   const Geom& g = c->g;
@@ -1466,8 +1480,8 @@ qcd_status qcd_reconstruct_odd(qcd_ctx* c, double* x_o, const double* x_e, const
 }
 
 qcd_status qcd_gauge_force(qcd_ctx* c, double* F, double beta, int flags) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_gauge_force", c);
+  qcd_status s = QCD_OK;
   if (!F) return fail(QCD_ERR_ARG, "null pointer");
   if (flags & ~(QCD_FORCE_GRADIENT | QCD_FORCE_ACCUMULATE)) return fail(QCD_ERR_ARG, "unknown gauge force flags");
   if (!c->have_gauge) return fail(QCD_ERR_STATE, "gauge_force before load_gauge");
@@ -1484,8 +1498,8 @@ qcd_status qcd_gauge_force(qcd_ctx* c, double* F, double beta, int flags) {
 }
 
 qcd_status qcd_plaquette(qcd_ctx* c, double* mean) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_plaquette", c);
+  qcd_status s = QCD_OK;
   if (!mean) return fail(QCD_ERR_ARG, "null pointer");
   if (!c->have_gauge) return fail(QCD_ERR_STATE, "plaquette before load_gauge");
   launch_plaquette(c->g, c->g64, reduce_args(c, FIN_STORE), c->st);
@@ -1496,8 +1510,8 @@ qcd_status qcd_plaquette(qcd_ctx* c, double* mean) {
 }
 
 qcd_status qcd_kinetic_energy(qcd_ctx* c, const double* P, double* K) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_kinetic_energy", c);
+  qcd_status s = QCD_OK;
   if (!P || !K) return fail(QCD_ERR_ARG, "null pointer");
   launch_flat_norm2((size_t)c->g.Vh * 2 * 4 * 9, reinterpret_cast<const double2*>(P), reduce_args(c, FIN_STORE),
                     c->st);
@@ -1508,8 +1522,8 @@ qcd_status qcd_kinetic_energy(qcd_ctx* c, const double* P, double* K) {
 }
 
 qcd_status qcd_update_links(qcd_ctx* c, double* U, const double* P, double eps) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_update_links", c);
+  qcd_status s = QCD_OK;
   if (!U || !P) return fail(QCD_ERR_ARG, "null pointer");
   const size_t nlinks = (size_t)c->g.Vh * 2 * 4;
   if ((const char*)U < (const char*)P + nlinks * 9 * sizeof(double2) &&
@@ -1526,8 +1540,8 @@ qcd_status qcd_update_links(qcd_ctx* c, double* U, const double* P, double eps) 
 
 qcd_status qcd_r_step(qcd_ctx* c, double* U, double* P, const double* eta, int nrhs, double eps, double beta,
                       int flags, const qcd_solver_params* prm, qcd_solver_stats* stats) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_r_step", c);
+  qcd_status s = QCD_OK;
   if (!U || !P || (!eta && nrhs > 0)) return fail(QCD_ERR_ARG, "null pointer");
   if (nrhs < 0) return fail(QCD_ERR_ARG, "nrhs must be >= 0");
   if (flags & ~(QCD_FORCE_CLOVER_DET | QCD_R_STEP_DEFER_CLOVER)) return fail(QCD_ERR_ARG, "unknown r_step flags");
@@ -1565,8 +1579,8 @@ qcd_status qcd_r_step(qcd_ctx* c, double* U, double* P, const double* eta, int n
 }
 
 qcd_status qcd_polyakov(qcd_ctx* c, double out[2]) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_polyakov", c);
+  qcd_status s = QCD_OK;
   if (!out) return fail(QCD_ERR_ARG, "null pointer");
   if (!c->have_gauge) return fail(QCD_ERR_STATE, "polyakov before load_gauge");
   launch_polyakov(c->g, c->g64, reduce_args(c, FIN_STORE), c->st);
@@ -1579,8 +1593,8 @@ qcd_status qcd_polyakov(qcd_ctx* c, double out[2]) {
 
 qcd_status qcd_pbp(qcd_ctx* c, const double* eta_e, const double* eta_o, int nrhs, double* out,
                    const qcd_solver_params* prm, qcd_solver_stats* stats) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_pbp", c);
+  qcd_status s = QCD_OK;
   if (!eta_e || !eta_o || !out) return fail(QCD_ERR_ARG, "null pointer");
   if (nrhs < 1 || nrhs > MAX_RHS) return fail(QCD_ERR_ARG, "nrhs must be in 1..%d", MAX_RHS);
   if (!c->have_clover) return fail(QCD_ERR_STATE, "pbp needs a clover term");
@@ -1646,8 +1660,8 @@ long long qcd_selftest_fastdiv(void) {
 }
 
 qcd_status qcd_profile(qcd_ctx* c, int enable) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_profile", c);
+  qcd_status s = QCD_OK;
   if ((s = sync_and_check(c, "profile"))) return s;
   prof_collect(c);
   if (enable) {
@@ -1664,8 +1678,8 @@ qcd_status qcd_profile(qcd_ctx* c, int enable) {
 }
 
 qcd_status qcd_profile_read(qcd_ctx* c, qcd_kernel_stat* out, int max_entries, int* n_entries) {
-  qcd_status s = check_ctx(c);
-  if (s) return s;
+  QCD_API_ENTER("qcd_profile_read", c);
+  qcd_status s = QCD_OK;
   if (!n_entries || (max_entries > 0 && !out)) return fail(QCD_ERR_ARG, "null output");
   CUDA_TRY(cudaStreamSynchronize(c->st));
   prof_collect(c);

@@ -20,6 +20,8 @@
 // the kernel are read with ordinary loads after the barrier.  Every barrier wait is bounded: a
 // block that has waited too long sets an error word and all blocks return (the host reports
 // QCD_ERR_TIMEOUT).
+#include <mutex>
+
 #include "qcd_dslash.cuh"
 #include "qcd_kernels.h"
 
@@ -270,15 +272,37 @@ __global__ void barrier_probe_kernel(unsigned* count, int* err, int absent) {
   grid_barrier(count, target, err);
 }
 
+// Resident blocks per SM of one kernel instance and the SM count, per device (looked up on a
+// device's first launch, under a lock, so that host threads and devices with different SM counts
+// each get their own figures).
+struct GridShape {
+  int per_sm = -1, sms = 0;
+};
+constexpr int kMaxDevices = 64;
+
 template <int P, int RECON>
 cudaError_t launch_pc(const PersistentCGArgs& q, cudaStream_t st) {
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_persistent_kernel<P, RECON>, 128, 0);
-    if (per_sm < 1) per_sm = 0;
+  static std::mutex mu;
+  static GridShape shape[kMaxDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  int per_sm, sms;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    GridShape& s = shape[dev];
+    if (s.per_sm < 0) {
+      int n = 0, k = 0;
+      if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, cg_persistent_kernel<P, RECON>, 128, 0)) !=
+          cudaSuccess)
+        return e;
+      s.sms = n;
+      s.per_sm = k < 1 ? 0 : k;
+    }
+    per_sm = s.per_sm;
+    sms = s.sms;
   }
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   const int nsb = (q.g.Vh + 31) / 32;

@@ -16,8 +16,12 @@
 //    3 * 192 * V/2 bytes <= QCD_STATIC_SCRATCH_BYTES (for example 16^4); larger
 //    lattices are rejected with QCD_ERR_ARG before anything is launched.
 //  * The device address of the array is looked up once per device, by the first
-//    call made on that device (cudaGetSymbolAddress, with that device current).
-//    Make that first call before any stream capture.
+//    call made on that device (cudaGetSymbolAddress, with that device current),
+//    and kept for the life of the process: it assumes the device's primary
+//    context is not reset (cudaDeviceReset) while the library is loaded.  Make
+//    that first call before any stream capture.
+//  * The call makes the context's device current while it runs and restores the
+//    caller's current device before it returns.
 //  * All calls share the one array and it keeps the last call's contents.  Every
 //    byte a call reads from it is written earlier in the same call, so nothing
 //    needs clearing; but calls whose work overlaps on the GPU (two streams, two
@@ -27,6 +31,7 @@
 #include <mutex>
 
 #include "qcd.h"
+#include "qcd_api_scope.h"
 #include "qcd_dslash.cuh"
 #include "qcd_kernels.h"
 
@@ -42,7 +47,6 @@ struct CtxView {
   bool have_gauge, have_clover;
 };
 bool ctx_view(const qcd_ctx* c, CtxView* v);
-qcd_status set_error(qcd_status s, const char* msg);
 }  // namespace qcd
 
 using namespace qcd;
@@ -72,7 +76,10 @@ cudaError_t scratch_on(int device, void** out) {
 
 extern "C" qcd_status qcd_mhat_static(qcd_ctx* ctx, double* out, const double* in, int dagger) {
   CtxView v;
-  if (!ctx_view(ctx, &v)) return set_error(QCD_ERR_ARG, "null context");
+  const bool have_ctx = ctx_view(ctx, &v);
+  // the context's device is current during the call; the caller's current device is restored on return
+  ApiScope scope("qcd_mhat_static", have_ctx ? v.device : -1);
+  if (scope.status() != QCD_OK) return scope.status();
   if (!out || !in) return set_error(QCD_ERR_ARG, "null field pointer");
   const size_t field = (size_t)192 * v.g.Vh;  // one FP64 even or odd field in the native layout
   if (3 * field > (size_t)QCD_STATIC_SCRATCH_BYTES) {
@@ -85,9 +92,8 @@ extern "C" qcd_status qcd_mhat_static(qcd_ctx* ctx, double* out, const double* i
   if (!v.have_gauge || !v.have_clover) return set_error(QCD_ERR_STATE, "qcd_mhat_static needs load_gauge and clover_build");
   if ((const char*)out < (const char*)in + field && (const char*)in < (const char*)out + field)
     return set_error(QCD_ERR_ARG, "in and out overlap");
-  cudaError_t e = cudaSetDevice(v.device);
   void* base = nullptr;
-  if (e == cudaSuccess) e = scratch_on(v.device, &base);
+  cudaError_t e = scratch_on(v.device, &base);
   if (e != cudaSuccess) return set_error(QCD_ERR_CUDA, cudaGetErrorString(e));
   unsigned char* s = static_cast<unsigned char*>(base);
   void* x_nat = s;

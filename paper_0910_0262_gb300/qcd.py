@@ -86,6 +86,8 @@ _SIGNATURES = {
     "qcd_polyakov": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "qcd_pbp": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
+    "qcd_probe_fma_peak": (ctypes.c_int, [ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
+    "qcd_probe_copy_bandwidth": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -233,6 +235,20 @@ def qcd_selftest_barrier_timeout(ctx):
 def qcd_selftest_fastdiv():
     """Mismatches of the kernels' division by a lattice extent against integer division (host only)."""
     return lib().qcd_selftest_fastdiv()
+
+
+def qcd_probe_fma_peak(precision=64, stream=None):
+    """Measured FMA throughput (TFLOP/s) of the current device in FP64 or FP32 (see include/qcd.h)."""
+    v = ctypes.c_double()
+    _check(lib().qcd_probe_fma_peak(int(precision), stream, ctypes.byref(v)))
+    return v.value
+
+
+def qcd_probe_copy_bandwidth(nbytes, reps=20, stream=None):
+    """Measured bandwidth (GB/s, read + write) of a device copy of nbytes (see include/qcd.h)."""
+    v = ctypes.c_double()
+    _check(lib().qcd_probe_copy_bandwidth(int(nbytes), int(reps), stream, ctypes.byref(v)))
+    return v.value
 
 
 def qcd_last_error():

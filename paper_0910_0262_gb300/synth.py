@@ -135,6 +135,8 @@ WORKLOADS = {
     'c2_16^4_force': dict(dims=(16, 16, 16, 16), eps=0.2, seed=3, nrhs=1),
     'c3_32^3x64': dict(dims=(32, 32, 32, 64), eps=0.15, seed=4, nrhs=8),
     'c4_48^3x96': dict(dims=(48, 48, 48, 96), eps=0.15, seed=5, nrhs=4),
+    # a small lattice for quick checks of the bench's two arms
+    't_4x4x4x8': dict(dims=(4, 4, 4, 8), eps=0.2, seed=1, nrhs=1),
 }
 KAPPA = 0.12
 CSW = 1.0
