@@ -107,18 +107,42 @@ __device__ __forceinline__ double grid_total(const double* part) {
 // invalidates, so neighbours shared by the sites of a block are read from L2 once
 constexpr int LDM = LD_CA;
 
+// FP32 / FP16 iterations run each phase as pair units (two warps per block of 32 sites, so that the
+// resident grid covers a 16^4 parity in one round); FP64 (bound by the FP64 pipe) keeps the
+// four-warp split unit.
+template <int P>
+struct PcSmem {
+  static constexpr bool PAIR = P != 64;
+  static constexpr int PAIR_STAGE = PairStage<P == 64 ? 32 : P, EPI_XPAY_CG>::U4;  // per warp
+  static constexpr int STAGE = PAIR ? 4 * PAIR_STAGE : Stage<P, EPI_XPAY_CG>::U4;
+};
+
+// one phase over the site blocks this block owns; returns the thread's share of the phase's sum
 template <int P, int RECON, int EPI>
 __device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Real<P>::T> (*part)[12][32],
-                                            uint4* stage, double alpha) {
-  using R = typename Real<P>::T;
+                                            PairXch<float> (*xch)[2], uint4* stage, double alpha) {
   const int nsb = (A.g.Vh + 31) / 32;
   double v = 0.0;
-  for (int sb = blockIdx.x; sb < nsb; sb += gridDim.x) {
-    int hh;
-    bool valid;
-    Site s;
-    split_prologue(A, sb, hh, valid, s);
-    v += split_unit<P, RECON, EPI, LDM>(A, hh, valid, s, 0, true, alpha, part, stage, true);
+  if constexpr (PcSmem<P>::PAIR) {
+    const int w = threadIdx.x >> 5, q = w >> 1, d = w & 1;
+    int slot = 0;
+    for (int sb = blockIdx.x * 2 + q; sb < nsb; sb += gridDim.x * 2) {
+      int hh;
+      bool valid;
+      Site s;
+      split_prologue(A, sb, hh, valid, s);
+      v += pair_unit<P, RECON, EPI, LDM>(A, hh, valid, s, d, q, true, alpha, &xch[q][slot],
+                                         stage + w * PcSmem<P>::PAIR_STAGE);
+      slot ^= 1;
+    }
+  } else {
+    for (int sb = blockIdx.x; sb < nsb; sb += gridDim.x) {
+      int hh;
+      bool valid;
+      Site s;
+      split_prologue(A, sb, hh, valid, s);
+      v += split_unit<P, RECON, EPI, LDM>(A, hh, valid, s, 0, true, alpha, part, stage, true);
+    }
   }
   return v;
 }
@@ -128,8 +152,10 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
   using R = typename Real<P>::T;
   constexpr int PR = P == 64 ? 64 : 32;
   using RR = typename Real<PR>::T;
-  __shared__ cx<R> part[4][12][32];
-  __shared__ uint4 stage[Stage<P, EPI_XPAY_CG>::U4];  // the largest staging of the three epilogues
+  constexpr bool PAIR = PcSmem<P>::PAIR;
+  __shared__ cx<R> part[PAIR ? 1 : 4][12][32];         // split unit: the four warps' partial sums
+  __shared__ PairXch<float> xch[PAIR ? 2 : 1][2];       // pair units: per pair, two alternating areas
+  __shared__ uint4 stage[PcSmem<P>::STAGE];            // the largest staging of the three epilogues
   const CGState st0 = *Q.cg;
   // an earlier launch of the batch whose barrier gave up leaves *bar_err set: do nothing
   if (!st0.active || Q.ctl->halt || st0.iters >= Q.iter_limit || *reinterpret_cast<volatile int*>(Q.bar_err)) {
@@ -165,7 +191,7 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
     a1.in = Q.p;
     a1.in_norm = Q.p_n;
     a1.in_g5 = 0;
-    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, stage, 0.0);
+    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, xch, stage, 0.0);
     if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     // phase 2
     {
@@ -175,7 +201,7 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
       a.out = Q.y;
       a.out_norm = Q.y_n;
       a.do_norm = 1;
-      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY>(a, part, stage, 0.0));
+      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY>(a, part, xch, stage, 0.0));
       if (threadIdx.x == 0) Q.part_pap[blockIdx.x] = v;
     }
     if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
@@ -193,7 +219,7 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
     a1.in = Q.y;
     a1.in_norm = Q.y_n;
     a1.in_g5 = 1;
-    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, stage, 0.0);
+    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, xch, stage, 0.0);
     if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     // phase 4
     {
@@ -206,7 +232,7 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
       a.cg_r = Q.r;
       a.cg_p = Q.p;
       a.cg_p_norm = Q.p_n;
-      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY_CG>(a, part, stage, alpha));
+      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY_CG>(a, part, xch, stage, alpha));
       if (threadIdx.x == 0) Q.part_rr[blockIdx.x] = v;
     }
     if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;

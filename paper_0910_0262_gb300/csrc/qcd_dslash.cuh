@@ -73,6 +73,52 @@ __device__ __forceinline__ void project(const cx<R> s[12], cx<R> h[6]) {
   }
 }
 
+// Spin rows 2 and 3 of (1 + sgn g_mu) expanded from rows 0 and 1 (h0, h1) of one colour.
+template <int MU, int SGN, typename R>
+__device__ __forceinline__ void expand_rows(cx<R> h0, cx<R> h1, cx<R>& lo, cx<R>& hi) {
+  if (MU == 0) {
+    lo = SGN < 0 ? times_i(h1) : times_mi(h1);
+    hi = SGN < 0 ? times_i(h0) : times_mi(h0);
+  } else if (MU == 1) {
+    lo = SGN < 0 ? -h1 : h1;
+    hi = SGN < 0 ? h0 : -h0;
+  } else if (MU == 2) {
+    lo = SGN < 0 ? times_i(h0) : times_mi(h0);
+    hi = SGN < 0 ? times_mi(h1) : times_i(h1);
+  } else {
+    lo = SGN < 0 ? -h0 : h0;
+    hi = SGN < 0 ? -h1 : h1;
+  }
+}
+
+// acc += f (expanded h) with the real factor f (the FP16 neighbour's norm, the time-boundary sign)
+// folded into fused multiply-adds, one per real component, instead of a multiply and an add;
+// FIRST: acc = f (expanded h).
+template <int MU, int SGN, bool FIRST = false, typename R>
+__device__ __forceinline__ void accumulate_scaled(const cx<R> h[6], R f, cx<R> acc[12]) {
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    if (FIRST) {
+      const cx<R> h0 = f * h[a], h1 = f * h[3 + a];
+      cx<R> lo, hi;
+      expand_rows<MU, SGN>(h0, h1, lo, hi);
+      acc[a] = h0;
+      acc[3 + a] = h1;
+      acc[6 + a] = lo;
+      acc[9 + a] = hi;
+    } else {
+      cx<R> lo, hi;
+      expand_rows<MU, SGN>(h[a], h[3 + a], lo, hi);
+      const cx<R> t[4] = {h[a], h[3 + a], lo, hi};
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        acc[3 * k + a].re = fma(f, t[k].re, acc[3 * k + a].re);
+        acc[3 * k + a].im = fma(f, t[k].im, acc[3 * k + a].im);
+      }
+    }
+  }
+}
+
 // Expand the multiplied half spinor back to four spins and accumulate (FIRST: the first term of
 // the sum, stored instead of added to a zero accumulator, which would cost an add per component).
 template <int MU, int SGN, bool FIRST = false, typename R>
@@ -81,19 +127,7 @@ __device__ __forceinline__ void accumulate(const cx<R> h[6], cx<R> acc[12]) {
   for (int a = 0; a < 3; a++) {
     const cx<R> h0 = h[a], h1 = h[3 + a];
     cx<R> lo, hi;  // the terms of spin rows 2 and 3
-    if (MU == 0) {
-      lo = SGN < 0 ? times_i(h1) : times_mi(h1);
-      hi = SGN < 0 ? times_i(h0) : times_mi(h0);
-    } else if (MU == 1) {
-      lo = SGN < 0 ? -h1 : h1;
-      hi = SGN < 0 ? h0 : -h0;
-    } else if (MU == 2) {
-      lo = SGN < 0 ? times_i(h0) : times_mi(h0);
-      hi = SGN < 0 ? times_mi(h1) : times_i(h1);
-    } else {
-      lo = SGN < 0 ? -h0 : h0;
-      hi = SGN < 0 ? -h1 : h1;
-    }
+    expand_rows<MU, SGN>(h0, h1, lo, hi);
     if (FIRST) {
       acc[a] = h0;
       acc[3 + a] = h1;
@@ -199,21 +233,15 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
   project<MU, -1>(sp, h);
   su3_mul(L.uf, h, w);
   if (MU == 3) f *= L.sf;
-  if (MU == 3 || P == 16) {
-#pragma unroll
-    for (int k = 0; k < 6; k++) w[k] = f * w[k];
-  }
-  accumulate<MU, -1, FIRST>(w, acc);
+  if (MU == 3 || P == 16) accumulate_scaled<MU, -1, FIRST>(w, f, acc);
+  else accumulate<MU, -1, FIRST>(w, acc);
   f = load_neighbor<P, COH>(A, r, L.nbb, sp);
   if (A.in_g5) apply_g5(sp);
   project<MU, +1>(sp, h);
   su3_adj_mul(L.ub, h, w);
   if (MU == 3) f *= L.sb;
-  if (MU == 3 || P == 16) {
-#pragma unroll
-    for (int k = 0; k < 6; k++) w[k] = f * w[k];
-  }
-  accumulate<MU, +1>(w, acc);
+  if (MU == 3 || P == 16) accumulate_scaled<MU, +1>(w, f, acc);
+  else accumulate<MU, +1>(w, acc);
 }
 
 // acc = the two hops along mu of one output site and RHS r, links loaded here.
@@ -384,21 +412,29 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
           SpinorIO<PR>::template load_block<COH>(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
           SpinorIO<PR>::template load_block<COH>(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
         }
+        RR n6 = RR(0);  // the site block's |r|^2 in the precision of r (FP32 below FP64)
 #pragma unroll
         for (int k = 0; k < 6; k++) {
           xs[k].re = fma(al, RR(ps[k].re), xs[k].re);
           xs[k].im = fma(al, RR(ps[k].im), xs[k].im);
           rs[k].re = fma(-al, RR(res[k].re), rs[k].re);
           rs[k].im = fma(-al, RR(res[k].im), rs[k].im);
-          nrm += double(rs[k].re) * rs[k].re + double(rs[k].im) * rs[k].im;
+          n6 = fma(rs[k].re, rs[k].re, n6);
+          n6 = fma(rs[k].im, rs[k].im, n6);
         }
+        nrm += double(n6);
         SpinorIO<PR>::store_block(A.cg_x, nullptr, A.g.Vh, r, hh, b, xs);
         SpinorIO<PR>::store_block(A.cg_r, nullptr, A.g.Vh, r, hh, b, rs);
       }
     } else {
       if (A.do_norm) {
+        R n6 = R(0);
 #pragma unroll
-        for (int k = 0; k < 6; k++) nrm += double(res[k].re) * res[k].re + double(res[k].im) * res[k].im;
+        for (int k = 0; k < 6; k++) {
+          n6 = fma(res[k].re, res[k].re, n6);
+          n6 = fma(res[k].im, res[k].im, n6);
+        }
+        nrm += double(n6);
       }
 #pragma unroll
       for (int k = 0; k < 6; k++) part[0][6 * b + k][lane] = res[k];
@@ -432,6 +468,260 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
   }
   __syncthreads();
   return nrm;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// Pair unit: one block of 32 output sites on two warps.  Warp d of the pair computes the four hops
+// along mu = 2d and 2d + 1 for its lane's site, then finishes chiral block d (components 6d .. 6d+5):
+// the two warps swap the other halves of their partial sums through shared memory, meet at one
+// named barrier of the pair, and run the epilogue of their block (clover, xpay, gamma_5, norm or CG
+// update) and its stores side by side, so no warp idles through the epilogue.  With two threads per
+// site, a grid of 4 resident blocks per SM covers the 1024 site blocks of a 16^4 parity in one round
+// (the four-warp split unit needs two).
+
+// named barrier of the 64 threads of pair q of a block (ids 1 and 2; id 0 is __syncthreads)
+__device__ __forceinline__ void pair_sync(int q) { asm volatile("bar.sync %0, 64;" ::"r"(q + 1) : "memory"); }
+
+// Per-warp staging of the epilogue operands of one chiral block (rows of 32 16-byte elements, lane =
+// site): the clover block, then the x block and, for EPI_XPAY_CG, the p block (FP16: the two uint4
+// rows the block touches -- the end row, then the shared middle row -- and the 32 site norms).
+template <int P, int EPI>
+struct PairStage {
+  static constexpr bool ON = P != 64 && EPI != EPI_NONE;
+  static constexpr int CL = P == 32 ? 9 : 5;            // clover rows of one chiral block
+  static constexpr int SPB = P == 32 ? 3 : 2;           // rows of one chiral block of a spinor
+  static constexpr int SPBN = SPB * 32 + (P == 16 ? 8 : 0);
+  static constexpr bool XR = EPI == EPI_XPAY || EPI == EPI_XPAY_CG;
+  static constexpr bool CG = EPI == EPI_XPAY_CG;
+  static constexpr int OFF_X = CL * 32;
+  static constexpr int OFF_P = OFF_X + (XR ? SPBN : 0);
+  static constexpr int U4 = ON ? OFF_P + (CG ? SPBN : 0) : 1;
+};
+
+// exchange area of one pair for one unit: the partial sums a warp passes to its partner ([block]
+// [component][lane]) and, for FP16 output, each block's largest magnitude per site
+template <typename R>
+struct PairXch {
+  cx<R> v[2][6][32];
+  float mx[2][32];
+};
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+// chiral block b of a spinor of precision P (RHS 0, sites hh0 .. hh0+n-1) into a warp's staging rows;
+// lane l copies site l
+template <int P>
+__device__ __forceinline__ void stage_spinor_block(uint4* dst, const void* base, const float* nrm, int Vh, int hh0,
+                                                   int b, int lane, int n) {
+  if (lane >= n) return;
+  const uint4* src = static_cast<const uint4*>(base);
+  if (P == 32) {
+#pragma unroll
+    for (int j = 0; j < 3; j++) cp_async16(dst + j * 32 + lane, src + sidx<6>(3 * b + j, Vh, 0, hh0 + lane));
+  } else {
+    cp_async16(dst + lane, src + sidx<3>(b == 0 ? 0 : 2, Vh, 0, hh0 + lane));
+    cp_async16(dst + 32 + lane, src + sidx<3>(1, Vh, 0, hh0 + lane));
+    cp_async4(reinterpret_cast<float*>(dst + 64) + lane, nrm + hh0 + lane);
+  }
+}
+
+// chiral block b of a spinor staged by stage_spinor_block (the values of SpinorIO<P>::load_block)
+template <int P>
+__device__ __forceinline__ void staged_spinor_block(const uint4* st, int lane, int b, cx<float> s[6]) {
+  if (P == 32) {
+    const float4* q = reinterpret_cast<const float4*>(st);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const float4 v = q[k * 32 + lane];
+      s[2 * k] = cmk(v.x, v.y);
+      s[2 * k + 1] = cmk(v.z, v.w);
+    }
+  } else {
+    const float n = reinterpret_cast<const float*>(st + 64)[lane];
+    const uint4 end = st[lane], mid = st[32 + lane];
+    const float2 e0 = h2f(end.x), e1 = h2f(end.y), e2 = h2f(end.z), e3 = h2f(end.w);
+    if (b == 0) {
+      const float2 m0 = h2f(mid.x), m1 = h2f(mid.y);
+      s[0] = cmk(e0.x * n, e0.y * n);
+      s[1] = cmk(e1.x * n, e1.y * n);
+      s[2] = cmk(e2.x * n, e2.y * n);
+      s[3] = cmk(e3.x * n, e3.y * n);
+      s[4] = cmk(m0.x * n, m0.y * n);
+      s[5] = cmk(m1.x * n, m1.y * n);
+    } else {
+      const float2 m2 = h2f(mid.z), m3 = h2f(mid.w);
+      s[0] = cmk(m2.x * n, m2.y * n);
+      s[1] = cmk(m3.x * n, m3.y * n);
+      s[2] = cmk(e0.x * n, e0.y * n);
+      s[3] = cmk(e1.x * n, e1.y * n);
+      s[4] = cmk(e2.x * n, e2.y * n);
+      s[5] = cmk(e3.x * n, e3.y * n);
+    }
+  }
+}
+
+// y = C x for chiral block b with the block's clover rows staged (FP32: 9 float4 rows; FP16: 5 uint4)
+template <int P>
+__device__ __forceinline__ void staged_clover_block(const uint4* st, int lane, int b, const cx<float> x[6],
+                                                    cx<float> y[6]) {
+  if (P == 32) {
+    CloverIO<32>::template apply<LD_SM>(st, 32, lane, 0, x, y);
+  } else {
+    if (b == 0) CloverIO<16>::template apply_block<0, LD_SM, 0>(st, 32, lane, x, y);
+    else CloverIO<16>::template apply_block<1, LD_SM, 0>(st, 32, lane, x, y);
+  }
+}
+
+// the hops along mu = 2B and 2B + 1 of one output site (acc = their sum)
+template <int P, int RECON, int COH, int B>
+__device__ __forceinline__ void pair_hops(const DslashArgs& A, const Site& s, cx<typename Real<P>::T> acc[12]) {
+  using R = typename Real<P>::T;
+  DirLinks<R> L;
+  dir_unit<P, RECON, 2 * B, COH>(A, s, 0, acc);
+  load_dir<P, RECON, 2 * B + 1>(A, s, L);
+  hop_dir<P, 2 * B + 1, COH>(A, L, 0, acc);
+}
+
+// The pair unit on warp B of its pair (B is the chiral block the warp finishes; a compile-time
+// constant, so that the partial sums stay in registers).
+template <int P, int RECON, int EPI, int COH, int B>
+__device__ __forceinline__ float pair_unit_b(const DslashArgs& A, int hh, bool valid, const Site& s, int q,
+                                             bool cg_active, double cg_alpha, PairXch<float>* xch, uint4* stage) {
+  static_assert(P == 32 || P == 16, "the pair unit serves the FP32 and FP16 inner iteration");
+  using ST = PairStage<P, EPI>;
+  constexpr int b = B;
+  const int lane = threadIdx.x & 31;
+  const int Vh = A.g.Vh;
+  if (ST::ON) {
+    const int hh0 = hh - lane, n = min(32, Vh - hh0);
+    if (lane < n) {
+      const uint4* cl = static_cast<const uint4*>(A.clover);
+      if (P == 32) {
+#pragma unroll
+        for (int j = 0; j < 9; j++) cp_async16(stage + j * 32 + lane, cl + (size_t)(9 * b + j) * Vh + hh0 + lane);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 5; j++) cp_async16(stage + j * 32 + lane, cl + (size_t)(4 * b + j) * Vh + hh0 + lane);
+      }
+    }
+    if (ST::XR) stage_spinor_block<P>(stage + ST::OFF_X, A.x, A.x_norm, Vh, hh0, b, lane, n);
+    if (ST::CG && cg_active) stage_spinor_block<P>(stage + ST::OFF_P, A.cg_p, A.cg_p_norm, Vh, hh0, b, lane, n);
+    cp_async_commit();
+  }
+  cx<float> acc[12];
+  if (valid) {
+    pair_hops<P, RECON, COH, B>(A, s, acc);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = cmk(0.f, 0.f);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; k++) xch->v[1 - b][k][lane] = acc[6 * (1 - b) + k];
+  if (ST::ON) cp_async_wait_all();
+  pair_sync(q);
+  float nrm = 0.f;
+  cx<float> res[6];
+  if (valid) {
+    cx<float> v[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = acc[6 * b + k] + xch->v[b][k][lane];
+    if (EPI == EPI_NONE) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = v[k];
+    } else if (EPI == EPI_CLOVER_INV) {
+      staged_clover_block<P>(stage, lane, b, v, res);
+    } else {  // EPI_XPAY, EPI_XPAY_CG
+      cx<float> xs[6], cxs[6];
+      staged_spinor_block<P>(stage + ST::OFF_X, lane, b, xs);
+      if (A.x_g5 && b == 1) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) xs[k] = -xs[k];
+      }
+      staged_clover_block<P>(stage, lane, b, xs, cxs);
+      const float a = float(A.a);
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        res[k].re = fmaf(a, v[k].re, cxs[k].re);
+        res[k].im = fmaf(a, v[k].im, cxs[k].im);
+      }
+    }
+    if (A.out_g5 && b == 1) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = -res[k];
+    }
+    if (EPI == EPI_XPAY_CG) {
+      // res = (A p)_b: advance x and r (FP32) of this RHS with alpha from the <p, A p> reduction
+      if (cg_active) {
+        const float al = float(cg_alpha);
+        cx<float> ps[6], xs[6], rs[6];
+        staged_spinor_block<P>(stage + ST::OFF_P, lane, b, ps);
+        SpinorIO<32>::template load_block<COH>(A.cg_x, nullptr, Vh, 0, hh, b, xs);
+        SpinorIO<32>::template load_block<COH>(A.cg_r, nullptr, Vh, 0, hh, b, rs);
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+          xs[k].re = fmaf(al, ps[k].re, xs[k].re);
+          xs[k].im = fmaf(al, ps[k].im, xs[k].im);
+          rs[k].re = fmaf(-al, res[k].re, rs[k].re);
+          rs[k].im = fmaf(-al, res[k].im, rs[k].im);
+          nrm = fmaf(rs[k].re, rs[k].re, nrm);
+          nrm = fmaf(rs[k].im, rs[k].im, nrm);
+        }
+        SpinorIO<32>::store_block(A.cg_x, nullptr, Vh, 0, hh, b, xs);
+        SpinorIO<32>::store_block(A.cg_r, nullptr, Vh, 0, hh, b, rs);
+      }
+    } else {
+      if (A.do_norm) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+          nrm = fmaf(res[k].re, res[k].re, nrm);
+          nrm = fmaf(res[k].im, res[k].im, nrm);
+        }
+      }
+      if (P == 32) SpinorIO<32>::store_block(A.out, nullptr, Vh, 0, hh, b, res);
+    }
+  }
+  if (P == 16 && EPI != EPI_XPAY_CG) {
+    // the FP16 site norm is the largest magnitude over both blocks: swap the blocks' maxima
+    float m = 0.f;
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) m = fmaxf(m, fmaxf(fabsf(res[k].re), fabsf(res[k].im)));
+    }
+    xch->mx[b][lane] = m;
+    pair_sync(q);
+    if (valid) {
+      m = fmaxf(m, xch->mx[1 - b][lane]);
+      const float inv = m > 0.f ? 1.0f / m : 0.f;
+      uint4* o = static_cast<uint4*>(A.out);
+      // block 0: uint4 row 0 and the first half of row 1; block 1: the second half of row 1 and row 2
+      const uint2 half1 = b == 0 ? make_uint2(f2h(res[4].re * inv, res[4].im * inv), f2h(res[5].re * inv, res[5].im * inv))
+                                 : make_uint2(f2h(res[0].re * inv, res[0].im * inv), f2h(res[1].re * inv, res[1].im * inv));
+      const int o0 = b == 0 ? 0 : 2;  // first of the four components that fill a whole row
+      uint4 full;
+      full.x = f2h(res[o0].re * inv, res[o0].im * inv);
+      full.y = f2h(res[o0 + 1].re * inv, res[o0 + 1].im * inv);
+      full.z = f2h(res[o0 + 2].re * inv, res[o0 + 2].im * inv);
+      full.w = f2h(res[o0 + 3].re * inv, res[o0 + 3].im * inv);
+      o[sidx<3>(b == 0 ? 0 : 2, Vh, 0, hh)] = full;
+      reinterpret_cast<uint2*>(o + sidx<3>(1, Vh, 0, hh))[b] = half1;
+      if (b == 0) A.out_norm[hh] = m;
+    }
+  }
+  return nrm;
+}
+
+// One pair unit (RHS 0) on warp d of pair q: returns the thread's share of |out|^2 (do_norm) or of
+// |r|^2 (EPI_XPAY_CG, with cg_alpha applied when cg_active), summed in FP32 over the site's
+// components.  xch: the pair's exchange area for this unit (alternate two per pair between units, so
+// that one barrier per unit suffices); stage: the warp's PairStage<P, EPI> rows.  P is 32 or 16.
+template <int P, int RECON, int EPI, int COH>
+__device__ __forceinline__ float pair_unit(const DslashArgs& A, int hh, bool valid, const Site& s, int d, int q,
+                                           bool cg_active, double cg_alpha, PairXch<float>* xch, uint4* stage) {
+  if (d == 0) return pair_unit_b<P, RECON, EPI, COH, 0>(A, hh, valid, s, q, cg_active, cg_alpha, xch, stage);
+  return pair_unit_b<P, RECON, EPI, COH, 1>(A, hh, valid, s, q, cg_active, cg_alpha, xch, stage);
 }
 
 // Site of a lane in the block of 32 sites starting at 32 * sb.
@@ -638,21 +928,29 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
             SpinorIO<P>::load_block(A.cg_p, A.cg_p_norm, Vh, r, hh, b, ps);
             SpinorIO<PR>::load_block(A.cg_x, nullptr, Vh, r, hh, b, xs);
             SpinorIO<PR>::load_block(A.cg_r, nullptr, Vh, r, hh, b, rs);
+            RR n6 = RR(0);  // the site block's |r|^2 in the precision of r (FP32 below FP64)
 #pragma unroll
             for (int j = 0; j < 6; j++) {
               xs[j].re = fma(alr, RR(ps[j].re), xs[j].re);
               xs[j].im = fma(alr, RR(ps[j].im), xs[j].im);
               rs[j].re = fma(-alr, RR(o[j].re), rs[j].re);
               rs[j].im = fma(-alr, RR(o[j].im), rs[j].im);
-              nrm += double(rs[j].re) * rs[j].re + double(rs[j].im) * rs[j].im;
+              n6 = fma(rs[j].re, rs[j].re, n6);
+              n6 = fma(rs[j].im, rs[j].im, n6);
             }
+            nrm += double(n6);
             SpinorIO<PR>::store_block(A.cg_x, nullptr, Vh, r, hh, b, xs);
             SpinorIO<PR>::store_block(A.cg_r, nullptr, Vh, r, hh, b, rs);
           }
         } else {
           if (A.do_norm) {
+            R n6 = R(0);
 #pragma unroll
-            for (int j = 0; j < 6; j++) nrm += double(o[j].re) * o[j].re + double(o[j].im) * o[j].im;
+            for (int j = 0; j < 6; j++) {
+              n6 = fma(o[j].re, o[j].re, n6);
+              n6 = fma(o[j].im, o[j].im, n6);
+            }
+            nrm += double(n6);
           }
 #pragma unroll
           for (int j = 0; j < 6; j++) res[6 * b + j] = o[j];

@@ -519,14 +519,15 @@ struct CloverIO<32> {
 template <>
 struct CloverIO<16> {
   static constexpr int NVEC = 9;  // uint4 per site
-  // block B occupies halves [36B, 36B+36): uint4 4B .. 4B+4 (the middle uint4 is shared)
-  template <int B, int LD = LD_NC>
+  // block B occupies halves [36B, 36B+36): uint4 4B .. 4B+4 (the middle uint4 is shared).  ROW0: the
+  // row of c holding uint4 4B (4B for a whole field; 0 for a copy of the block's five rows alone)
+  template <int B, int LD = LD_NC, int ROW0 = 4 * B>
   __device__ static void apply_block(const void* c, int Vh, int h, const cx<float> x[6], cx<float> y[6]) {
     const uint4* q = static_cast<const uint4*>(c) + h;
     float f[40];
 #pragma unroll
     for (int k = 0; k < 5; k++) {
-      uint4 v = ldv<LD>(q + (size_t)(4 * B + k) * Vh);
+      uint4 v = ldv<LD>(q + (size_t)(ROW0 + k) * Vh);
       float2 a0 = h2f(v.x), a1 = h2f(v.y), a2 = h2f(v.z), a3 = h2f(v.w);
       f[8 * k + 0] = a0.x;
       f[8 * k + 1] = a0.y;
