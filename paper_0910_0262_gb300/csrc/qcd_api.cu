@@ -169,7 +169,7 @@ struct qcd_ctx {
   // persistent single-RHS iteration: per-block partial sums and the grid barrier words
   double* pc_part = nullptr;   // 2 x pc_slots
   int pc_slots = 0;
-  unsigned* pc_bar = nullptr;  // [0] barrier arrivals, [2] error
+  unsigned* pc_bar = nullptr;  // [0] barrier arrivals, [1] release word of the summing barriers, [2] error
   bool persistent = true;
   // per round of a batch of persistent launches: 2 x iterations run + 1 if it raised a reliable update
   int* pc_rounds = nullptr;
@@ -522,7 +522,8 @@ static qcd_status create_ctx(qcd_ctx** out, const int dims[4], double t_bc, void
     c->persistent = coop != 0;
     const char* e = getenv("QCD_CG_PERSISTENT");
     if (e && e[0] == '0') c->persistent = false;
-    if (cudaMalloc(&c->pc_part, sizeof(double) * 2 * c->pc_slots) != cudaSuccess ||
+    // two sets of per-block partials, then the two grid totals
+    if (cudaMalloc(&c->pc_part, sizeof(double) * (2 * c->pc_slots + 2)) != cudaSuccess ||
         cudaMalloc(&c->pc_bar, 4 * sizeof(unsigned)) != cudaSuccess) {
       cudaGetLastError();
       qcd_destroy(c);
@@ -977,12 +978,14 @@ qcd_status launch_persistent(qcd_ctx* c, const SolverFields& f, int iter_limit, 
   q.part_rr = c->pc_part + c->pc_slots;
   q.slots = c->pc_slots;
   q.bar_count = c->pc_bar;
+  q.bar_flag = c->pc_bar + 1;
+  q.totals = c->pc_part + 2 * c->pc_slots;
   q.bar_err = reinterpret_cast<int*>(c->pc_bar + 2);
   q.iter_limit = iter_limit;
   q.round_out = c->pc_rounds + round;
-  // the arrival counter restarts with every launch; the error word is cleared once per batch of
+  // the arrival counter and the release word restart with every launch; the error word is cleared once per batch of
   // rounds (cg_batch), so that a timed-out round stops every later one at its first barrier
-  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, sizeof(unsigned), c->st));
+  CUDA_TRY(cudaMemsetAsync(c->pc_bar, 0, 2 * sizeof(unsigned), c->st));
   cudaEvent_t ea = nullptr, eb = nullptr;
   if (c->prof_on) {
     ea = prof_event(c);

@@ -67,14 +67,76 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned& target, 
   return ok != 0;
 }
 
-// sum of one double per thread over the block (thread 0 gets it)
-__device__ __forceinline__ double block_sum128(double v) {
-  __shared__ double sm[4];
+// Bounded wait of thread 0 until *word reaches target (an acquire at GPU scope); false if the wait
+// gave up (it then sets *err) or another block reported an error.
+__device__ __forceinline__ bool wait_word(const unsigned* word, unsigned target, int* err) {
+  unsigned spins = 0;
+  while (true) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(word) : "memory");
+    if ((int)(v - target) >= 0) return true;
+    if ((++spins & 31) == 0) {
+      if (*reinterpret_cast<volatile int*>(err)) return false;
+      if (spins > BARRIER_SPIN_LIMIT) {
+        atomicExch(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+template <int BLOCK>
+__device__ __forceinline__ double grid_total(const double* part);
+
+// Grid-wide barrier that also sums one double per block (`mine`, thread 0's value): every block
+// writes its partial and arrives on the counter with an acquire-release add; the block whose arrival
+// completes the count reads all partials (the add's acquire makes them visible), sums them in block
+// order -- the same bits whichever block arrives last -- publishes the total and releases the others
+// through *flag.  The total comes out of the barrier instead of after it (at 16^4 the separate sum of
+// 512 partials after a barrier took 2.5 us).  Returns false as grid_barrier does; *total: the sum.
+template <int BLOCK>
+__device__ __forceinline__ bool grid_barrier_sum(unsigned* count, unsigned* flag, unsigned& target, int* err,
+                                                 double* part, double* slot, double mine, double* total) {
+  __shared__ int ok, last;
+  __shared__ double tot;
+  target += gridDim.x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = mine;
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+    last = old == target - 1;
+    ok = 1;
+  }
+  __syncthreads();
+  if (last) {
+    const double t = grid_total<BLOCK>(part);
+    if (threadIdx.x == 0) {
+      *slot = t;
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(target) : "memory");
+    }
+  }
+  if (threadIdx.x == 0) {
+    ok = wait_word(flag, target, err) ? 1 : 0;
+    if (ok) tot = __ldcg(slot);
+  }
+  __syncthreads();
+  *total = tot;
+  return ok != 0;
+}
+
+// sum of one double per thread over the BLOCK threads of the block (thread 0 gets it)
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sm[BLOCK / 32];
   for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
   __syncthreads();
   double s = 0.0;
-  if (threadIdx.x == 0) s = (sm[0] + sm[1]) + (sm[2] + sm[3]);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < BLOCK / 32; w++) s += sm[w];
+  }
   __syncthreads();
   return s;
 }
@@ -82,14 +144,15 @@ __device__ __forceinline__ double block_sum128(double v) {
 // sum of the gridDim.x per-block partials, on every thread: each thread adds a fixed strided
 // subset (its loads issued together), then a fixed shuffle / shared-memory tree, so every block
 // gets the same bits
+template <int BLOCK>
 __device__ __forceinline__ double grid_total(const double* part) {
-  __shared__ double sm[4];
+  __shared__ double sm[BLOCK / 32];
   double s = 0.0;
-  for (int base = 0; base < (int)gridDim.x; base += 8 * 128) {
+  for (int base = 0; base < (int)gridDim.x; base += 8 * BLOCK) {
     double v[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-      const int j = base + (int)threadIdx.x + 128 * i;
+      const int j = base + (int)threadIdx.x + BLOCK * i;
       v[i] = j < (int)gridDim.x ? __ldcg(part + j) : 0.0;
     }
 #pragma unroll
@@ -98,7 +161,9 @@ __device__ __forceinline__ double grid_total(const double* part) {
   for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
   __syncthreads();
-  const double t = (sm[0] + sm[1]) + (sm[2] + sm[3]);
+  double t = 0.0;
+#pragma unroll
+  for (int w = 0; w < BLOCK / 32; w++) t += sm[w];
   __syncthreads();
   return t;
 }
@@ -107,14 +172,21 @@ __device__ __forceinline__ double grid_total(const double* part) {
 // invalidates, so neighbours shared by the sites of a block are read from L2 once
 constexpr int LDM = LD_CA;
 
-// FP32 / FP16 iterations run each phase as pair units (two warps per block of 32 sites, so that the
-// resident grid covers a 16^4 parity in one round); FP64 (bound by the FP64 pipe) keeps the
-// four-warp split unit.
+// Shape of the persistent kernel.  FP32 / FP16 iterations run each phase as pair units (two warps
+// per block of 32 sites, so that the resident grid covers a 16^4 parity in one round), two pairs
+// per 128-thread block; FP64 (bound by the FP64 pipe) runs four-warp split units.  Four blocks per
+// SM either way.  (One 512-thread block of eight pairs per SM made the grid barrier cheaper, 1.6
+// against 2.2 us at 16^4, but the sum of the per-block partials slower, 4.6 against 2.5 us.)
 template <int P>
-struct PcSmem {
+struct PcShape {
   static constexpr bool PAIR = P != 64;
+  static constexpr int THREADS = 128;
+  static constexpr int MIN_BLOCKS = 4;
+  static constexpr int PAIRS = THREADS / 64;
   static constexpr int PAIR_STAGE = PairStage<P == 64 ? 32 : P, EPI_XPAY_CG>::U4;  // per warp
-  static constexpr int STAGE = PAIR ? 4 * PAIR_STAGE : Stage<P, EPI_XPAY_CG>::U4;
+  // pair units: the pairs' exchange areas and the warps' staging rows, in dynamic shared memory
+  static constexpr size_t DYN = PAIR ? sizeof(PairXch<float>) * 2 * PAIRS + sizeof(uint4) * (THREADS / 32) * PAIR_STAGE
+                                     : 0;
 };
 
 // one phase over the site blocks this block owns; returns the thread's share of the phase's sum
@@ -123,16 +195,18 @@ __device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Rea
                                             PairXch<float> (*xch)[2], uint4* stage, double alpha) {
   const int nsb = (A.g.Vh + 31) / 32;
   double v = 0.0;
-  if constexpr (PcSmem<P>::PAIR) {
+  if constexpr (PcShape<P>::PAIR) {
+    constexpr int NP = PcShape<P>::PAIRS;
     const int w = threadIdx.x >> 5, q = w >> 1, d = w & 1;
     int slot = 0;
-    for (int sb = blockIdx.x * 2 + q; sb < nsb; sb += gridDim.x * 2) {
+    // site block sb goes to block sb mod grid, pair sb / grid: every SM gets a share of the phase
+    for (int sb = q * gridDim.x + blockIdx.x; sb < nsb; sb += NP * gridDim.x) {
       int hh;
       bool valid;
       Site s;
       split_prologue(A, sb, hh, valid, s);
       v += pair_unit<P, RECON, EPI, LDM>(A, hh, valid, s, d, q, true, alpha, &xch[q][slot],
-                                         stage + w * PcSmem<P>::PAIR_STAGE);
+                                         stage + w * PcShape<P>::PAIR_STAGE);
       slot ^= 1;
     }
   } else {
@@ -148,14 +222,19 @@ __device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Rea
 }
 
 template <int P, int RECON>
-__global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs Q) {
+__global__ void __launch_bounds__(PcShape<P>::THREADS, PcShape<P>::MIN_BLOCKS)
+    cg_persistent_kernel(PersistentCGArgs Q) {
   using R = typename Real<P>::T;
   constexpr int PR = P == 64 ? 64 : 32;
   using RR = typename Real<PR>::T;
-  constexpr bool PAIR = PcSmem<P>::PAIR;
-  __shared__ cx<R> part[PAIR ? 1 : 4][12][32];         // split unit: the four warps' partial sums
-  __shared__ PairXch<float> xch[PAIR ? 2 : 1][2];       // pair units: per pair, two alternating areas
-  __shared__ uint4 stage[PcSmem<P>::STAGE];            // the largest staging of the three epilogues
+  constexpr bool PAIR = PcShape<P>::PAIR;
+  constexpr int BLOCK = PcShape<P>::THREADS;
+  __shared__ cx<R> part[PAIR ? 1 : 4][12][32];                            // split unit: partial sums
+  __shared__ uint4 split_stage[PAIR ? 1 : Stage<P, EPI_XPAY_CG>::U4];     // split unit: staging
+  extern __shared__ __align__(16) unsigned char pc_dyn[];                  // pair units (PcShape::DYN)
+  PairXch<float>(*xch)[2] = reinterpret_cast<PairXch<float>(*)[2]>(pc_dyn);
+  uint4* stage = PAIR ? reinterpret_cast<uint4*>(pc_dyn + sizeof(PairXch<float>) * 2 * PcShape<P>::PAIRS)
+                      : split_stage;
   const CGState st0 = *Q.cg;
   // an earlier launch of the batch whose barrier gave up leaves *bar_err set: do nothing
   if (!st0.active || Q.ctl->halt || st0.iters >= Q.iter_limit || *reinterpret_cast<volatile int*>(Q.bar_err)) {
@@ -201,11 +280,10 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
       a.out = Q.y;
       a.out_norm = Q.y_n;
       a.do_norm = 1;
-      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY>(a, part, xch, stage, 0.0));
-      if (threadIdx.x == 0) Q.part_pap[blockIdx.x] = v;
+      const double v = block_sum<BLOCK>(run_phase<P, RECON, EPI_XPAY>(a, part, xch, stage, 0.0));
+      if (!grid_barrier_sum<BLOCK>(Q.bar_count, Q.bar_flag, bar_target, Q.bar_err, Q.part_pap, Q.totals, v, &pAp))
+        return;
     }
-    if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
-    pAp = grid_total(Q.part_pap);
     if (!(pAp > 0.0) || !isfinite(pAp)) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         Q.ctl->nan = 1;
@@ -222,6 +300,7 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
     run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, xch, stage, 0.0);
     if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     // phase 4
+    double rr_new;
     {
       DslashArgs a = a2;
       a.x = Q.y;
@@ -232,11 +311,11 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
       a.cg_r = Q.r;
       a.cg_p = Q.p;
       a.cg_p_norm = Q.p_n;
-      const double v = block_sum128(run_phase<P, RECON, EPI_XPAY_CG>(a, part, xch, stage, alpha));
-      if (threadIdx.x == 0) Q.part_rr[blockIdx.x] = v;
+      const double v = block_sum<BLOCK>(run_phase<P, RECON, EPI_XPAY_CG>(a, part, xch, stage, alpha));
+      if (!grid_barrier_sum<BLOCK>(Q.bar_count, Q.bar_flag, bar_target, Q.bar_err, Q.part_rr, Q.totals + 1, v,
+                                   &rr_new))
+        return;
     }
-    if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
-    const double rr_new = grid_total(Q.part_rr);
     if (!isfinite(rr_new)) {
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         Q.ctl->nan = 1;
@@ -253,7 +332,7 @@ __global__ void __launch_bounds__(128, 4) cg_persistent_kernel(PersistentCGArgs 
     const bool want = rr_new <= st0.tol2 || since >= every || rr_new < delta2 * st0.rr_reliable;
     if (!want) {
       // phase 5
-      for (int h = blockIdx.x * 128 + threadIdx.x; h < Vh; h += gridDim.x * 128) {
+      for (int h = blockIdx.x * BLOCK + threadIdx.x; h < Vh; h += gridDim.x * BLOCK) {
         cx<RR> rs[12];
         cx<R> ps[12], out[12];
         SpinorIO<PR>::template load<LDM>(Q.r, nullptr, Vh, 0, h, rs);
@@ -321,8 +400,12 @@ cudaError_t launch_pc(const PersistentCGArgs& q, cudaStream_t st) {
     if (s.per_sm < 0) {
       int n = 0, k = 0;
       if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, cg_persistent_kernel<P, RECON>, 128, 0)) !=
-          cudaSuccess)
+      if (PcShape<P>::DYN > 0 &&
+          (e = cudaFuncSetAttribute(cg_persistent_kernel<P, RECON>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)PcShape<P>::DYN)) != cudaSuccess)
+        return e;
+      if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, cg_persistent_kernel<P, RECON>, PcShape<P>::THREADS,
+                                                             PcShape<P>::DYN)) != cudaSuccess)
         return e;
       s.sms = n;
       s.per_sm = k < 1 ? 0 : k;
@@ -333,12 +416,13 @@ cudaError_t launch_pc(const PersistentCGArgs& q, cudaStream_t st) {
   if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
   const int nsb = (q.g.Vh + 31) / 32;
   int grid = per_sm * sms;
-  if (grid > nsb) grid = nsb;
+  const int units_per_block = PcShape<P>::PAIR ? PcShape<P>::PAIRS : 1;
+  if (grid > (nsb + units_per_block - 1) / units_per_block) grid = (nsb + units_per_block - 1) / units_per_block;
   if (grid > q.slots) grid = q.slots;
   PersistentCGArgs a = q;
   void* args[] = {&a};
-  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(cg_persistent_kernel<P, RECON>), dim3(grid), dim3(128),
-                                     args, 0, st);
+  return cudaLaunchCooperativeKernel(reinterpret_cast<void*>(cg_persistent_kernel<P, RECON>), dim3(grid),
+                                     dim3(PcShape<P>::THREADS), args, PcShape<P>::DYN, st);
 }
 
 }  // namespace

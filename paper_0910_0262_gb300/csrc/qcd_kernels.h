@@ -25,6 +25,8 @@ struct PersistentCGArgs {
   double *part_pap, *part_rr;  // one slot per block
   int slots;                   // slots in each; the grid never exceeds it
   unsigned* bar_count;         // barrier arrivals, zeroed before the launch
+  unsigned* bar_flag;          // release word of the summing barriers, zeroed before the launch
+  double* totals;              // [2]: the grid totals the summing barriers publish (pAp, |r|^2)
   int* bar_err;                // set when a barrier wait gave up
   int iter_limit;              // total iterations of the RHS (over all launches) at which to stop
   int* round_out;              // non-null: 2 x iterations this launch ran, + 1 if it raised a reliable
