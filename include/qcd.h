@@ -60,7 +60,8 @@ typedef enum {
   QCD_ERR_NOT_POSDEF = 5,    /* a clover block is not positive definite */
   QCD_ERR_NOT_CONVERGED = 6, /* CG hit max_iter; best x and stats are still written */
   QCD_ERR_NAN = 7,           /* non-finite input or a non-finite reduction */
-  QCD_ERR_TIMEOUT = 8        /* a bounded device-side wait (grid barrier of the persistent CG kernel) gave up */
+  QCD_ERR_TIMEOUT = 8,       /* a bounded device-side wait (grid barrier of the persistent CG kernel) gave up */
+  QCD_ERR_COMM = 9           /* a halo-exchange or sum callback of a t-slab call reported a failure */
 } qcd_status;
 
 /* qcd_load_gauge flags */
@@ -310,6 +311,65 @@ qcd_status qcd_selftest_barrier_timeout(qcd_ctx* ctx);
  * (0 on success); needs no GPU and no context.
  */
 long long qcd_selftest_fastdiv(void);
+
+/*
+ * Time decomposition over several GPUs (one process per GPU).  The paper runs its application as MPI
+ * processes that each hold part of the lattice and exchange boundary data between kernels (Sec. 4);
+ * here the global lattice X x Y x Z x T is cut into slabs of consecutive time slices, one per rank.
+ * A hopping pass needs, at the sites of its first and last local slice, the spinors one slice beyond
+ * the slab; only their spin projections enter the time hops, so each pass exchanges six complex
+ * numbers per face site (X Y Z / 2 sites of the input's parity) in each direction, and every CG
+ * reduction is summed over the ranks.  Both are done by the caller's callbacks (NCCL, MPI, or copies
+ * between contexts of one process), so the library itself holds no communicator.
+ *
+ * qcd_create_slab: a context for the slab t_offset <= t < t_offset + t_local of the global lattice
+ *   dims = {X, Y, Z, T} (t_offset and t_local even, t_local >= 2, t_offset + t_local <= T); fields of
+ *   the slab are the global even/odd-site fields restricted to its time slices, in the canonical
+ *   order of a lattice X x Y x Z x t_local (a contiguous range of the global field: half indices
+ *   t_offset XYZ/2 .. (t_offset + t_local) XYZ/2).  t_bc applies at global time T-1.
+ * qcd_load_gauge on a slab context takes the links of global times t_offset-2 .. t_offset+t_local+1
+ *   (taken mod T), [t_local+4][Z][Y][X][4][3][3] complex128: the slab and two slices on each side,
+ *   which the clover term of its boundary slices needs.  qcd_clover_build, qcd_clover_logdet (the
+ *   slab's sites only) and qcd_profile work as on any context.  qcd_dslash and qcd_cg_solve need
+ *   t_local = T (a slab that is the whole lattice); the force, molecular-dynamics, measurement and
+ *   allocation-free calls are not available on slab contexts (QCD_ERR_STATE).
+ * qcd_slab_halo_bytes: bytes each of the four halo buffers needs for nrhs fields at precision.
+ * qcd_slab_dslash: qcd_dslash's operators on the slab's fields (DSLASH_EO/OE: one exchange; MHAT:
+ *   two; MDAGM: four; CLOVER, CLOVER_INV: none).
+ * qcd_slab_cg_solve: qcd_cg_solve on the slab decomposition, every rank calling it with its slab of
+ *   x and b: the same iteration (FP64, or FP32 / FP16 inner with FP64 reliable updates), each hopping
+ *   pass preceded by an exchange and each reduction summed through comm->allreduce; stats as in
+ *   qcd_cg_solve (true residual of the whole lattice).  The callbacks are called from the calling
+ *   thread; a rank's call returns after its stream is synchronised.
+ *
+ * qcd_slab_comm: send_lo/send_hi/recv_lo/recv_hi are device buffers of at least qcd_slab_halo_bytes
+ * bytes, owned by the caller.  exchange(user, bytes) is called after the library has enqueued, on the
+ * context's stream, the kernels that fill the first `bytes` of send_lo and send_hi; before kernels the
+ * library enqueues after it returns, it must have copied the slab above's send_lo into this rank's
+ * recv_hi and the slab below's send_hi into its recv_lo (neighbours taken periodically in t; a single
+ * slab of the whole lattice is its own neighbour), in that stream's order.  allreduce(user, values, n)
+ * replaces n doubles in device memory by their sums over the ranks, likewise in stream order.  A
+ * nonzero return from either makes the call fail with QCD_ERR_COMM.
+ */
+typedef int (*qcd_halo_exchange_fn)(void* user, size_t bytes);
+typedef int (*qcd_allreduce_fn)(void* user, double* values, int n);
+typedef struct {
+  void* send_lo;
+  void* send_hi;
+  void* recv_lo;
+  void* recv_hi;
+  qcd_halo_exchange_fn exchange;
+  qcd_allreduce_fn allreduce;
+  void* user;
+} qcd_slab_comm;
+
+qcd_status qcd_create_slab(qcd_ctx** ctx, const int dims[4], int t_offset, int t_local, double t_bc,
+                           void* cuda_stream);
+qcd_status qcd_slab_halo_bytes(const qcd_ctx* ctx, int precision, int nrhs, size_t* bytes);
+qcd_status qcd_slab_dslash(qcd_ctx* ctx, double* out, const double* in, int op, int dagger, int precision, int nrhs,
+                           const qcd_slab_comm* comm);
+qcd_status qcd_slab_cg_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs, const qcd_solver_params* params,
+                             qcd_solver_stats* stats, const qcd_slab_comm* comm);
 
 /*
  * Device-limit probes for the kernels' rooflines (the paper has no counterpart; it quotes the Cell's

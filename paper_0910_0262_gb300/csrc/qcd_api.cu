@@ -179,6 +179,15 @@ struct qcd_ctx {
     double bytes_per_iter, flops_per_iter;
   };
   std::vector<PcPending> pc_pending;
+  // t-slab of a larger lattice (qcd_create_slab): the extended links (two slices on each side) and the
+  // FP64 packed links and clover term of that extended lattice, from which the slab's part is copied
+  bool slab = false;
+  Geom ge{};
+  double2* U_ext = nullptr;
+  void* ext_g64 = nullptr;
+  void *ext_A64 = nullptr, *ext_Ainv64 = nullptr, *ext_A32 = nullptr, *ext_Ainv32 = nullptr, *ext_A16 = nullptr,
+       *ext_Ainv16 = nullptr;
+  double* ext_logdet = nullptr;
 };
 
 namespace {
@@ -428,6 +437,7 @@ struct CtxView {
   const void* Ainv_odd64;
   double kappa;
   bool have_gauge, have_clover;
+  bool slab;
 };
 
 bool ctx_view(const qcd_ctx* c, CtxView* v) {
@@ -441,11 +451,23 @@ bool ctx_view(const qcd_ctx* c, CtxView* v) {
   v->kappa = c->kappa;
   v->have_gauge = c->have_gauge;
   v->have_clover = c->have_clover;
+  v->slab = c->slab;
   return true;
 }
 
 qcd_status set_error(qcd_status s, const char* msg) { return fail(s, "%s", msg); }
 }  // namespace qcd
+
+namespace {
+qcd_status slab_clover_build(qcd_ctx* c, double kappa, double csw, void* work);
+// calls that need an ordinary lattice (or a slab that is the whole lattice) refuse a t-slab
+qcd_status slab_refuse(const qcd_ctx* c, const char* what, bool whole_ok) {
+  if (!c || !c->slab) return QCD_OK;
+  if (whole_ok && c->g.T == c->g.Tg) return QCD_OK;
+  return fail(QCD_ERR_STATE, "%s is not available on a t-slab context%s", what,
+              whole_ok ? " (use the qcd_slab_* calls)" : "");
+}
+}  // namespace
 
 // ===================================================================== ABI ==
 extern "C" {
@@ -490,6 +512,8 @@ static qcd_status create_ctx(qcd_ctx** out, const int dims[4], double t_bc, void
   c->g.dX = make_fastdiv(dims[0]);
   c->g.dY = make_fastdiv(dims[1]);
   c->g.dZ = make_fastdiv(dims[2]);
+  c->g.t0 = 0;
+  c->g.Tg = dims[3];
   // partial sums of one reduction: nrhs x (blocks of the launch); the hopping kernel covers 32
   // (site, RHS) pairs per block, the fewest of all reducing kernels, so nrhs <= MAX_RHS needs
   // at most MAX_RHS * ceil(Vh * MAX_RHS / 32) slots
@@ -554,7 +578,9 @@ qcd_status qcd_destroy(qcd_ctx* c) {
   else cudaDeviceSynchronize();
   void* dev[] = {c->g64, c->g32, c->g16, c->A64, c->Ainv64, c->A32, c->Ainv32, c->A16, c->Ainv16, c->logdet, c->flags,
                  c->pc_part, c->pc_bar, c->pc_rounds,
-                 c->partials, c->counter, c->results, c->cg, c->ctl};
+                 c->partials, c->counter, c->results, c->cg, c->ctl,
+                 c->U_ext, c->ext_g64, c->ext_A64, c->ext_Ainv64, c->ext_A32, c->ext_Ainv32, c->ext_A16, c->ext_Ainv16,
+                 c->ext_logdet};
   for (void* p : dev)
     if (p) cudaFree(p);
   for (auto& b : c->ws)
@@ -591,16 +617,26 @@ qcd_status qcd_load_gauge(qcd_ctx* c, const double* U, int on_device, int flags)
     CUDA_TRY(cudaMalloc(&c->g32, n_links * 9 * sizeof(float2)));
     CUDA_TRY(cudaMalloc(&c->g16, n_links * 9 * sizeof(uint32_t)));
   }
+  // a t-slab keeps the whole extended field (its clover build reads it); the slab's own links start
+  // two time slices in
+  const size_t in_links = c->slab ? (size_t)c->ge.Vh * 2 * 4 : n_links;
+  const size_t in_bytes = in_links * 9 * sizeof(double2);
   const double2* src = reinterpret_cast<const double2*>(U);
-  if (!on_device) {
+  if (c->slab) {
+    if (!c->U_ext) CUDA_TRY(cudaMalloc(&c->U_ext, in_bytes));
+    CUDA_TRY(cudaMemcpyAsync(c->U_ext, U, in_bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->st));
+    src = c->U_ext;
+  } else if (!on_device) {
     void* stage;
     if ((s = ws_get(c, S_CANON, canon_bytes, &stage))) return s;
     CUDA_TRY(cudaMemcpyAsync(stage, U, canon_bytes, cudaMemcpyHostToDevice, c->st));
     src = static_cast<const double2*>(stage);
   }
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->st));
-  launch_check_finite(reinterpret_cast<const double*>(src), n_links * 18, c->flags + 1, c->st);
-  launch_pack_gauge(g, src, c->g64, c->g32, c->recon, c->g16, c->recon, c->st);
+  launch_check_finite(reinterpret_cast<const double*>(src), in_links * 18, c->flags + 1, c->st);
+  launch_pack_gauge(g, src + (c->slab ? (size_t)2 * g.XYZ * 4 * 9 : 0), c->g64, c->g32, c->recon, c->g16, c->recon,
+                    c->st);
   CUDA_TRY(cudaMemcpyAsync(c->h_flags, c->flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->st));
   if ((s = sync_and_check(c, "load_gauge"))) return s;
   c->have_clover = false;
@@ -628,9 +664,11 @@ qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
     CUDA_TRY(cudaMalloc(&c->logdet, (size_t)2 * 2 * g.Vh * sizeof(double)));
   }
   void* work;
-  if ((s = ws_get(c, S_F_CL, force_clover_bytes(g), &work))) return s;
+  if ((s = ws_get(c, S_F_CL, force_clover_bytes(c->slab ? c->ge : g), &work))) return s;
   CUDA_TRY(cudaMemsetAsync(c->flags, 0, 4 * sizeof(int), c->st));
-  {
+  if (c->slab) {
+    if ((s = slab_clover_build(c, kappa, csw, work))) return s;
+  } else {
     // 6 planes x 10 products of 3x3 complex matrices per site (two leaves share a product), plus
     // the two inversions
     ProfScope ps(c, "clover_build", 0, 2.0 * g.Vh * (60 * 216.0 + 2 * 1000.0));
@@ -652,6 +690,7 @@ qcd_status qcd_clover_build(qcd_ctx* c, double kappa, double csw) {
 
 qcd_status qcd_dslash(qcd_ctx* c, double* out, const double* in, int op, int dagger, int prec, int nrhs) {
   QCD_API_ENTER("qcd_dslash", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_dslash", true)) return rs;
   qcd_status s = QCD_OK;
   if (!out || !in) return fail(QCD_ERR_ARG, "null field pointer");
   if (op < QCD_OP_DSLASH_EO || op > QCD_OP_CLOVER_INV) return fail(QCD_ERR_ARG, "unknown op %d", op);
@@ -1243,6 +1282,7 @@ extern "C" {
 qcd_status qcd_cg_solve(qcd_ctx* c, double* x, const double* b, int nrhs, const qcd_solver_params* prm,
                         qcd_solver_stats* stats) {
   QCD_API_ENTER("qcd_cg_solve", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_cg_solve", true)) return rs;
   qcd_status s = QCD_OK;
   if (!x || !b) return fail(QCD_ERR_ARG, "null field pointer");
   if (nrhs < 1) return fail(QCD_ERR_ARG, "nrhs must be >= 1");
@@ -1269,6 +1309,7 @@ qcd_status qcd_cg_solve(qcd_ctx* c, double* x, const double* b, int nrhs, const 
 qcd_status qcd_fermion_force(qcd_ctx* c, double* F, const double* phi_or_x, int nrhs, int flags,
                              const qcd_solver_params* prm, qcd_solver_stats* stats) {
   QCD_API_ENTER("qcd_fermion_force", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_fermion_force", false)) return rs;
   qcd_status s = QCD_OK;
   const bool det = (flags & QCD_FORCE_CLOVER_DET) != 0;
   if (!F || (!phi_or_x && nrhs > 0)) return fail(QCD_ERR_ARG, "null pointer");
@@ -1413,6 +1454,7 @@ static qcd_status eo_check(qcd_ctx* c, const void* out, const void* in1, const v
 
 qcd_status qcd_prepare_source(qcd_ctx* c, double* bhat_e, const double* b_e, const double* b_o, int nrhs) {
   QCD_API_ENTER("qcd_prepare_source", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_prepare_source", false)) return rs;
   qcd_status s = eo_check(c, bhat_e, b_e, b_o, nrhs);
   if (s) return s;
   const Geom& g = c->g;
@@ -1446,6 +1488,7 @@ qcd_status qcd_prepare_source(qcd_ctx* c, double* bhat_e, const double* b_e, con
 
 qcd_status qcd_reconstruct_odd(qcd_ctx* c, double* x_o, const double* x_e, const double* b_o, int nrhs) {
   QCD_API_ENTER("qcd_reconstruct_odd", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_reconstruct_odd", false)) return rs;
   qcd_status s = eo_check(c, x_o, x_e, b_o, nrhs);
   if (s) return s;
   const Geom& g = c->g;
@@ -1484,6 +1527,7 @@ qcd_status qcd_reconstruct_odd(qcd_ctx* c, double* x_o, const double* x_e, const
 
 qcd_status qcd_gauge_force(qcd_ctx* c, double* F, double beta, int flags) {
   QCD_API_ENTER("qcd_gauge_force", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_gauge_force", false)) return rs;
   qcd_status s = QCD_OK;
   if (!F) return fail(QCD_ERR_ARG, "null pointer");
   if (flags & ~(QCD_FORCE_GRADIENT | QCD_FORCE_ACCUMULATE)) return fail(QCD_ERR_ARG, "unknown gauge force flags");
@@ -1502,6 +1546,7 @@ qcd_status qcd_gauge_force(qcd_ctx* c, double* F, double beta, int flags) {
 
 qcd_status qcd_plaquette(qcd_ctx* c, double* mean) {
   QCD_API_ENTER("qcd_plaquette", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_plaquette", false)) return rs;
   qcd_status s = QCD_OK;
   if (!mean) return fail(QCD_ERR_ARG, "null pointer");
   if (!c->have_gauge) return fail(QCD_ERR_STATE, "plaquette before load_gauge");
@@ -1514,6 +1559,7 @@ qcd_status qcd_plaquette(qcd_ctx* c, double* mean) {
 
 qcd_status qcd_kinetic_energy(qcd_ctx* c, const double* P, double* K) {
   QCD_API_ENTER("qcd_kinetic_energy", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_kinetic_energy", false)) return rs;
   qcd_status s = QCD_OK;
   if (!P || !K) return fail(QCD_ERR_ARG, "null pointer");
   launch_flat_norm2((size_t)c->g.Vh * 2 * 4 * 9, reinterpret_cast<const double2*>(P), reduce_args(c, FIN_STORE),
@@ -1526,6 +1572,7 @@ qcd_status qcd_kinetic_energy(qcd_ctx* c, const double* P, double* K) {
 
 qcd_status qcd_update_links(qcd_ctx* c, double* U, const double* P, double eps) {
   QCD_API_ENTER("qcd_update_links", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_update_links", false)) return rs;
   qcd_status s = QCD_OK;
   if (!U || !P) return fail(QCD_ERR_ARG, "null pointer");
   const size_t nlinks = (size_t)c->g.Vh * 2 * 4;
@@ -1544,6 +1591,7 @@ qcd_status qcd_update_links(qcd_ctx* c, double* U, const double* P, double eps) 
 qcd_status qcd_r_step(qcd_ctx* c, double* U, double* P, const double* eta, int nrhs, double eps, double beta,
                       int flags, const qcd_solver_params* prm, qcd_solver_stats* stats) {
   QCD_API_ENTER("qcd_r_step", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_r_step", false)) return rs;
   qcd_status s = QCD_OK;
   if (!U || !P || (!eta && nrhs > 0)) return fail(QCD_ERR_ARG, "null pointer");
   if (nrhs < 0) return fail(QCD_ERR_ARG, "nrhs must be >= 0");
@@ -1583,6 +1631,7 @@ qcd_status qcd_r_step(qcd_ctx* c, double* U, double* P, const double* eta, int n
 
 qcd_status qcd_polyakov(qcd_ctx* c, double out[2]) {
   QCD_API_ENTER("qcd_polyakov", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_polyakov", false)) return rs;
   qcd_status s = QCD_OK;
   if (!out) return fail(QCD_ERR_ARG, "null pointer");
   if (!c->have_gauge) return fail(QCD_ERR_STATE, "polyakov before load_gauge");
@@ -1597,6 +1646,7 @@ qcd_status qcd_polyakov(qcd_ctx* c, double out[2]) {
 qcd_status qcd_pbp(qcd_ctx* c, const double* eta_e, const double* eta_o, int nrhs, double* out,
                    const qcd_solver_params* prm, qcd_solver_stats* stats) {
   QCD_API_ENTER("qcd_pbp", c);
+  if (qcd_status rs = slab_refuse(c, "qcd_pbp", false)) return rs;
   qcd_status s = QCD_OK;
   if (!eta_e || !eta_o || !out) return fail(QCD_ERR_ARG, "null pointer");
   if (nrhs < 1 || nrhs > MAX_RHS) return fail(QCD_ERR_ARG, "nrhs must be in 1..%d", MAX_RHS);
@@ -1710,3 +1760,5 @@ qcd_status qcd_profile_read(qcd_ctx* c, qcd_kernel_stat* out, int max_entries, i
 }
 
 }  // extern "C"
+
+#include "qcd_api_slab.cuh"

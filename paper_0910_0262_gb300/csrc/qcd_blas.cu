@@ -134,6 +134,56 @@ __global__ void gate_clear_kernel(int* gate) { *gate = 0; }
 
 dim3 grid2(const Geom& g, int nrhs) { return dim3((g.Vh + BB - 1) / BB, nrhs); }
 
+// x_lo += alpha p, r_lo -= alpha Ap with alpha from the CG state, |r_lo|^2 -> reduction (the update the
+// fused EPI_XPAY_CG epilogue performs, as a separate pass for the t-slab solve)
+template <int PR, int PP>
+__global__ void __launch_bounds__(BB) xr_update_kernel(Geom g, int nrhs, void* x_lo, void* r_lo, const void* p,
+                                                       const float* pn, const void* ap, const float* apn,
+                                                       const CGState* cg, ReduceArgs red) {
+  using RR = typename Real<PR>::T;
+  using RP = typename Real<PP>::T;
+  const int k = blockIdx.y;
+  const int h = blockIdx.x * BB + threadIdx.x;
+  double v = 0.0;
+  if (h < g.Vh && cg[k].active) {
+    const RR al = RR(cg[k].alpha);
+    cx<RR> xs[12], rs[12];
+    cx<RP> ps[12], as[12];
+    SpinorIO<PR>::load(x_lo, nullptr, g.Vh, k, h, xs);
+    SpinorIO<PR>::load(r_lo, nullptr, g.Vh, k, h, rs);
+    SpinorIO<PP>::load(p, pn, g.Vh, k, h, ps);
+    SpinorIO<PP>::load(ap, apn, g.Vh, k, h, as);
+    RR n = RR(0);
+#pragma unroll
+    for (int c = 0; c < 12; c++) {
+      xs[c].re = fma(al, RR(ps[c].re), xs[c].re);
+      xs[c].im = fma(al, RR(ps[c].im), xs[c].im);
+      rs[c].re = fma(-al, RR(as[c].re), rs[c].re);
+      rs[c].im = fma(-al, RR(as[c].im), rs[c].im);
+      n = fma(rs[c].re, rs[c].re, n);
+      n = fma(rs[c].im, rs[c].im, n);
+    }
+    v = double(n);
+    SpinorIO<PR>::store(x_lo, nullptr, g.Vh, k, h, xs);
+    SpinorIO<PR>::store(r_lo, nullptr, g.Vh, k, h, rs);
+  }
+  block_partial<BB>(v, k, blockIdx.x, gridDim.x, red);
+  grid_finish<BB>(nrhs, (long long)gridDim.x * gridDim.y, gridDim.x, red);
+}
+
+// the finalisation a reducing kernel's last block performs, run on totals summed elsewhere (over the
+// slabs of a time decomposition): finalize_total for each RHS, then, after a true residual, the halt
+// word as grid_finish leaves it
+__global__ void finalize_kernel(ReduceArgs red, const double* totals, int nrhs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int r = 0; r < nrhs; r++) finalize_total(red, r, totals[r]);
+  if (red.mode == FIN_CG_TRUE) {
+    int any = 0;
+    for (int r = 0; r < nrhs; r++) any |= red.cg[r].active;
+    red.ctl->halt = (any && !red.ctl->nan) ? 0 : 1;
+  }
+}
+
 }  // namespace
 
 void launch_p_update(int prec_r, int prec_p, const Geom& g, int nrhs, const void* r, const float* rn, void* p,
@@ -182,6 +232,24 @@ void launch_redot(const Geom& g, int nrhs, const double2* a, const double2* b, c
                   cudaStream_t st) {
   g_kernel_launches += 1;
   redot_kernel<<<grid2(g, nrhs), BB, 0, st>>>(g, nrhs, a, b, red);
+}
+
+void launch_xr_update(int prec_r, int prec_p, const Geom& g, int nrhs, void* x_lo, void* r_lo, const void* p,
+                      const float* pn, const void* ap, const float* apn, const CGState* cg, const ReduceArgs& red,
+                      cudaStream_t st) {
+  g_kernel_launches += 1;
+  const dim3 grid((g.Vh + BB - 1) / BB, nrhs);
+  if (prec_r == 64)
+    xr_update_kernel<64, 64><<<grid, BB, 0, st>>>(g, nrhs, x_lo, r_lo, p, pn, ap, apn, cg, red);
+  else if (prec_p == 32)
+    xr_update_kernel<32, 32><<<grid, BB, 0, st>>>(g, nrhs, x_lo, r_lo, p, pn, ap, apn, cg, red);
+  else
+    xr_update_kernel<32, 16><<<grid, BB, 0, st>>>(g, nrhs, x_lo, r_lo, p, pn, ap, apn, cg, red);
+}
+
+void launch_finalize(const ReduceArgs& red, const double* totals, int nrhs, cudaStream_t st) {
+  g_kernel_launches += 1;
+  finalize_kernel<<<1, 32, 0, st>>>(red, totals, nrhs);
 }
 
 }  // namespace qcd

@@ -82,7 +82,38 @@ void launch_prec(int epi, const DslashArgs& a, cudaStream_t st) {
   }
 }
 
+// the split kernel with t-slab halos (no fused CG epilogue)
+template <int P, int RECON>
+void launch_halo(int epi, const DslashArgs& a, cudaStream_t st) {
+  const int nb = (a.g.Vh + 31) / 32;
+  if constexpr (P == 16) {
+    switch (epi) {
+      case EPI_NONE: dslash_split_fp16_kernel<RECON, EPI_NONE, true><<<nb, 128, 0, st>>>(a); break;
+      case EPI_CLOVER_INV: dslash_split_fp16_kernel<RECON, EPI_CLOVER_INV, true><<<nb, 128, 0, st>>>(a); break;
+      default: dslash_split_fp16_kernel<RECON, EPI_XPAY, true><<<nb, 128, 0, st>>>(a); break;
+    }
+  } else {
+    switch (epi) {
+      case EPI_NONE: dslash_split_kernel<P, RECON, EPI_NONE, true><<<nb, 128, 0, st>>>(a); break;
+      case EPI_CLOVER_INV: dslash_split_kernel<P, RECON, EPI_CLOVER_INV, true><<<nb, 128, 0, st>>>(a); break;
+      default: dslash_split_kernel<P, RECON, EPI_XPAY, true><<<nb, 128, 0, st>>>(a); break;
+    }
+  }
+}
+
 }  // namespace
+
+void launch_dslash_halo(int prec, int recon, int epi, const DslashArgs& a, cudaStream_t st) {
+  g_kernel_launches += 1;
+  if (prec == 64) launch_halo<64, 18>(epi, a, st);
+  else if (prec == 32) {
+    if (recon == 12) launch_halo<32, 12>(epi, a, st);
+    else launch_halo<32, 18>(epi, a, st);
+  } else {
+    if (recon == 12) launch_halo<16, 12>(epi, a, st);
+    else launch_halo<16, 18>(epi, a, st);
+  }
+}
 
 void launch_dslash(int prec, int recon, int epi, const DslashArgs& a, cudaStream_t st) {
   g_kernel_launches += 1;

@@ -48,6 +48,54 @@ struct DslashArgs {
   void* cg_r;
   const void* cg_p;
   const float* cg_p_norm;
+  // t-slab halos (hopping kernels instantiated with HALO): the neighbouring slabs' contributions to
+  // the time hops that leave this slab, one entry per site of a t-face (XYZ/2 per parity), layout of
+  // HaloIO.  halo_hi: (1 - g_t) psi of the upper slab's t = 0 sites, multiplied here by U_t(x);
+  // halo_lo: U_t(x - t)^dag (1 + g_t) psi of the lower slab's last time slice, already multiplied
+  // and signed by the slab that sent it.
+  const void* halo_lo;
+  const void* halo_hi;
+};
+
+// Halo entries: six complex numbers (a projected half spinor) per face site and RHS, FP64 as
+// [rhs][6][F] double2, FP32 and FP16 operators as [rhs][3][F] float4 (F = XYZ/2 face sites).
+template <int P>
+struct HaloIO {
+  static constexpr int ROWS = P == 64 ? 6 : 3;
+  static constexpr int BYTES = P == 64 ? 96 : 48;  // per face site and RHS
+  template <typename R>
+  __device__ static void load(const void* base, int F, int r, int f, cx<R> h[6]) {
+    if (P == 64) {
+      const double2* q = static_cast<const double2*>(base) + (size_t)r * 6 * F + f;
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        const double2 v = __ldg(q + (size_t)k * F);
+        h[k] = cmk(R(v.x), R(v.y));
+      }
+    } else {
+      const float4* q = static_cast<const float4*>(base) + (size_t)r * 3 * F + f;
+#pragma unroll
+      for (int k = 0; k < 3; k++) {
+        const float4 v = __ldg(q + (size_t)k * F);
+        h[2 * k] = cmk(R(v.x), R(v.y));
+        h[2 * k + 1] = cmk(R(v.z), R(v.w));
+      }
+    }
+  }
+  template <typename R>
+  __device__ static void store(void* base, int F, int r, int f, const cx<R> h[6]) {
+    if (P == 64) {
+      double2* q = static_cast<double2*>(base) + (size_t)r * 6 * F + f;
+#pragma unroll
+      for (int k = 0; k < 6; k++) q[(size_t)k * F] = make_double2(double(h[k].re), double(h[k].im));
+    } else {
+      float4* q = static_cast<float4*>(base) + (size_t)r * 3 * F + f;
+#pragma unroll
+      for (int k = 0; k < 3; k++)
+        q[(size_t)k * F] = make_float4(float(h[2 * k].re), float(h[2 * k].im), float(h[2 * k + 1].re),
+                                       float(h[2 * k + 1].im));
+    }
+  }
 };
 
 // Spin projection (1 + sgn g_mu) psi -> half spinor h (spin rows 0 and 1).
@@ -186,16 +234,22 @@ struct DirLinks {
   cx<R> uf[9], ub[9];  // U_mu(x), U_mu(x - mu)
   int nbf, nbb;        // half indices of x + mu, x - mu
   R sf, sb;            // boundary factors of the two hops
+  int hf, hb;          // HALO, mu = t: face index of a hop that leaves the slab forwards / backwards, else -1
 };
 
-// neighbours and boundary factors along mu
+// neighbours and boundary factors along mu (the factor t_bc belongs to the link at global time Tg-1)
 template <int MU, typename R>
 __device__ __forceinline__ void dir_index(const Geom& g, const Site& s, DirLinks<R>& L) {
   L.nbf = neighbor_fwd(g, s, MU) >> 1;
   L.nbb = neighbor_bwd(g, s, MU) >> 1;
-  L.sf = (MU == 3 && s.t == g.T - 1) ? R(g.t_bc) : R(1);
-  L.sb = (MU == 3 && s.t == 0) ? R(g.t_bc) : R(1);
+  const int tg = s.t + g.t0;
+  L.sf = (MU == 3 && tg == g.Tg - 1) ? R(g.t_bc) : R(1);
+  L.sb = (MU == 3 && tg == 0) ? R(g.t_bc) : R(1);
+  L.hf = L.hb = -1;
 }
+
+// the t-face index of a site (its half index within its time slice)
+__device__ __forceinline__ int face_index(const Geom& g, const Site& s) { return (s.i - s.t * g.XYZ) >> 1; }
 
 template <int P, int RECON, int MU>
 __device__ __forceinline__ void dir_links(const DslashArgs& A, const Site& s, DirLinks<typename Real<P>::T>& L) {
@@ -203,10 +257,18 @@ __device__ __forceinline__ void dir_links(const DslashArgs& A, const Site& s, Di
   GaugeIO<P, RECON>::load(A.gauge, A.g.Vh, 1 - A.p, MU, L.nbb, L.ub);
 }
 
-template <int P, int RECON, int MU>
+template <int P, int RECON, int MU, bool HALO = false>
 __device__ __forceinline__ void load_dir(const DslashArgs& A, const Site& s, DirLinks<typename Real<P>::T>& L) {
   dir_index<MU>(A.g, s, L);
-  dir_links<P, RECON, MU>(A, s, L);
+  if (HALO && MU == 3) {
+    // hops that leave the slab read the halos; U_t(x - t) of the backward one stays with the sender
+    if (s.t == A.g.T - 1) L.hf = face_index(A.g, s);
+    if (s.t == 0) L.hb = face_index(A.g, s);
+    GaugeIO<P, RECON>::load(A.gauge, A.g.Vh, A.p, MU, s.i >> 1, L.uf);
+    if (L.hb < 0) GaugeIO<P, RECON>::load(A.gauge, A.g.Vh, 1 - A.p, MU, L.nbb, L.ub);
+  } else {
+    dir_links<P, RECON, MU>(A, s, L);
+  }
 }
 
 // psi_r at half index nb; returns the factor still to be applied (the FP16 per-site scale, which
@@ -222,19 +284,33 @@ __device__ __forceinline__ typename Real<P>::T load_neighbor(const DslashArgs& A
   return R(1);
 }
 
-// acc += (1 - g_mu) U_mu(x) psi_r(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi_r(x-mu)  (FIRST: acc =)
-template <int P, int MU, int COH = LD_NC, bool FIRST = false>
+// acc += (1 - g_mu) U_mu(x) psi_r(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi_r(x-mu)  (FIRST: acc =).
+// HALO (mu = t): a hop that leaves the slab takes the neighbour's projected half spinor (forward) or
+// its finished contribution (backward) from the halos instead of the field.
+template <int P, int MU, int COH = LD_NC, bool FIRST = false, bool HALO = false>
 __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<typename Real<P>::T>& L, int r,
                                         cx<typename Real<P>::T> acc[12]) {
   using R = typename Real<P>::T;
+  constexpr bool H = HALO && MU == 3;
   cx<R> sp[12], h[6], w[6];
-  R f = load_neighbor<P, COH>(A, r, L.nbf, sp);
-  if (A.in_g5) apply_g5(sp);
-  project<MU, -1>(sp, h);
+  R f;
+  if (H && L.hf >= 0) {
+    HaloIO<P>::load(A.halo_hi, A.g.XYZ / 2, r, L.hf, h);
+    f = R(1);
+  } else {
+    f = load_neighbor<P, COH>(A, r, L.nbf, sp);
+    if (A.in_g5) apply_g5(sp);
+    project<MU, -1>(sp, h);
+  }
   su3_mul(L.uf, h, w);
   if (MU == 3) f *= L.sf;
   if (MU == 3 || P == 16) accumulate_scaled<MU, -1, FIRST>(w, f, acc);
   else accumulate<MU, -1, FIRST>(w, acc);
+  if (H && L.hb >= 0) {
+    HaloIO<P>::load(A.halo_lo, A.g.XYZ / 2, r, L.hb, w);
+    accumulate<MU, +1>(w, acc);
+    return;
+  }
   f = load_neighbor<P, COH>(A, r, L.nbb, sp);
   if (A.in_g5) apply_g5(sp);
   project<MU, +1>(sp, h);
@@ -245,11 +321,11 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
 }
 
 // acc = the two hops along mu of one output site and RHS r, links loaded here.
-template <int P, int RECON, int MU, int COH>
+template <int P, int RECON, int MU, int COH, bool HALO = false>
 __device__ __forceinline__ void dir_unit(const DslashArgs& A, const Site& s, int r, cx<typename Real<P>::T> acc[12]) {
   DirLinks<typename Real<P>::T> L;
-  load_dir<P, RECON, MU>(A, s, L);
-  hop_dir<P, MU, COH, true>(A, L, r, acc);
+  load_dir<P, RECON, MU, HALO>(A, s, L);
+  hop_dir<P, MU, COH, true, HALO>(A, L, r, acc);
 }
 
 template <int P>
@@ -321,7 +397,7 @@ __device__ __forceinline__ void stage_spinor(uint4* dst, const void* base, const
 // stage (Stage<P, EPI>); the clover pair only when fetch_clover (it is kept from an earlier call on
 // the same sites otherwise).  All threads must call it; it synchronises the block and leaves part
 // and stage free for the next call.
-template <int P, int RECON, int EPI, int COH>
+template <int P, int RECON, int EPI, int COH, bool HALO = false>
 __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool valid, const Site& s, int r,
                                              bool cg_active, double cg_alpha, cx<typename Real<P>::T> (*part)[12][32],
                                              uint4* stage, bool fetch_clover) {
@@ -346,7 +422,7 @@ __device__ __forceinline__ double split_unit(const DslashArgs& A, int hh, bool v
         case 0: dir_unit<P, RECON, 0, COH>(A, s, r, acc); break;
         case 1: dir_unit<P, RECON, 1, COH>(A, s, r, acc); break;
         case 2: dir_unit<P, RECON, 2, COH>(A, s, r, acc); break;
-        default: dir_unit<P, RECON, 3, COH>(A, s, r, acc); break;
+        default: dir_unit<P, RECON, 3, COH, HALO>(A, s, r, acc); break;
       }
     } else {
 #pragma unroll
@@ -732,8 +808,8 @@ __device__ __forceinline__ void split_prologue(const DslashArgs& A, int sb, int&
 }
 
 // Hopping kernel: one block per 32 output sites, looping over the right-hand sides (used for one
-// RHS, and for several in FP64).
-template <int P, int RECON, int EPI>
+// RHS, and for several in FP64; with HALO, for the sites of a t-slab).
+template <int P, int RECON, int EPI, bool HALO = false>
 __device__ __forceinline__ void dslash_split_body(const DslashArgs& A) {
   using R = typename Real<P>::T;
   __shared__ cx<R> part[4][12][32];
@@ -752,15 +828,15 @@ __device__ __forceinline__ void dslash_split_body(const DslashArgs& A) {
       al = A.red.cg[r].alpha;
     }
     const double nrm =
-        split_unit<P, RECON, EPI, LD_NC>(A, hh, valid, s, r, act, al, part, stage, r == 0);
+        split_unit<P, RECON, EPI, LD_NC, HALO>(A, hh, valid, s, r, act, al, part, stage, r == 0);
     if (reduce) block_partial<128>(nrm, r, blockIdx.x, gridDim.x, A.red);
   }
   if (reduce) grid_finish<128>(A.nrhs, gridDim.x, gridDim.x, A.red);
 }
 
-template <int P, int RECON, int EPI>
+template <int P, int RECON, int EPI, bool HALO = false>
 __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
-  dslash_split_body<P, RECON, EPI>(A);
+  dslash_split_body<P, RECON, EPI, HALO>(A);
 }
 
 // y = C x for chiral block b of a clover pair decoded to FP32 in shared memory (value m of block b of
@@ -992,9 +1068,9 @@ __global__ void __launch_bounds__(128, 5) dslash_site_fp16_kernel(DslashArgs A) 
 
 // The single-RHS FP16 operator is bound by latency: it is held to 64 registers, so that 8 blocks
 // (32 warps) share an SM.
-template <int RECON, int EPI>
+template <int RECON, int EPI, bool HALO = false>
 __global__ void __launch_bounds__(128, 8) dslash_split_fp16_kernel(DslashArgs A) {
-  dslash_split_body<16, RECON, EPI>(A);
+  dslash_split_body<16, RECON, EPI, HALO>(A);
 }
 
 }  // namespace qcd

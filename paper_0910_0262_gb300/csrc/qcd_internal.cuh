@@ -51,8 +51,10 @@ struct Geom {
   int X, Y, Z, T;
   int Vh;                // sites of one parity
   int XY, XYZ;           // lexicographic strides
-  double t_bc;           // factor on U_t(x) at t = T-1 in the hopping term
+  double t_bc;           // factor on U_t(x) at global time Tg-1 in the hopping term
   FastDiv dX, dY, dZ;    // division by X, Y, Z
+  int t0, Tg;            // global time of local t = 0 and the global time extent (a t-slab of a larger
+                         // lattice; 0 and T otherwise)
 };
 
 // (x, y, z, t) of the lexicographic index i = x + X (y + Y (z + Z t))

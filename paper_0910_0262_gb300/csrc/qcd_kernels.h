@@ -59,6 +59,15 @@ void launch_clover_apply(int prec, const Geom& g, const void* clover, const void
 // ---- hopping term (qcd_dslash.cu)
 struct DslashArgs;
 void launch_dslash(int prec, int recon, int epi, const DslashArgs& a, cudaStream_t st);
+// the same operators on the sites of a t-slab, time hops that leave the slab taken from a.halo_lo /
+// a.halo_hi (epi: EPI_NONE, EPI_CLOVER_INV or EPI_XPAY)
+void launch_dslash_halo(int prec, int recon, int epi, const DslashArgs& a, cudaStream_t st);
+// t-faces of a field of parity q (precision prec, nrhs RHS, native layout) for the neighbouring slabs:
+// send_lo[f] = (1 - g_t) (g5) psi at the face site f of local time 0; send_hi[f] = U_t(x)^dag (1 + g_t)
+// (g5) psi at the face site f of the last local time slice, times t_bc if that slice is the global
+// time Tg - 1 (HaloIO layout; gauge of the operator's precision)
+void launch_halo_pack(int prec, int recon, const Geom& g, const void* gauge, const void* in, const float* in_norm,
+                      int q, int in_g5, void* send_lo, void* send_hi, int nrhs, cudaStream_t st);
 
 // ---- BLAS-1 and CG steps (qcd_blas.cu); 2-D grids (sites x RHS)
 // gate (these three): non-null, the kernel returns at once unless *gate != 0 (the reliable-update
@@ -74,6 +83,12 @@ void launch_true_residual(int prec_r, const Geom& g, int nrhs, const double2* b,
                           float* r_lon, const ReduceArgs& red, cudaStream_t st, const int* gate = nullptr);
 // *gate = 0
 void launch_gate_clear(int* gate, cudaStream_t st);
+// x_lo += alpha p, r_lo -= alpha Ap (alpha from cg), |r_lo|^2 -> reduction (nrhs RHS; prec_r 64: all FP64)
+void launch_xr_update(int prec_r, int prec_p, const Geom& g, int nrhs, void* x_lo, void* r_lo, const void* p,
+                      const float* pn, const void* ap, const float* apn, const CGState* cg, const ReduceArgs& red,
+                      cudaStream_t st);
+// finalize_total(red, r, totals[r]) for r < nrhs on the device (totals summed over the slabs)
+void launch_finalize(const ReduceArgs& red, const double* totals, int nrhs, cudaStream_t st);
 // |v|^2 (FP64 native) -> reduction
 void launch_norm2(const Geom& g, int nrhs, const double2* v, const ReduceArgs& red, cudaStream_t st);
 // ---- molecular dynamics (qcd_md.cu); canonical link fields [V][4][3][3] complex128

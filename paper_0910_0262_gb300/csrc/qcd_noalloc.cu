@@ -45,6 +45,7 @@ struct CtxView {
   const void* Ainv_odd64;
   double kappa;
   bool have_gauge, have_clover;
+  bool slab;
 };
 bool ctx_view(const qcd_ctx* c, CtxView* v);
 }  // namespace qcd
@@ -90,6 +91,7 @@ extern "C" qcd_status qcd_mhat_static(qcd_ctx* ctx, double* out, const double* i
   }
   if (v.device < 0 || v.device >= kMaxDevices) return set_error(QCD_ERR_ARG, "device index out of range");
   if (!v.have_gauge || !v.have_clover) return set_error(QCD_ERR_STATE, "qcd_mhat_static needs load_gauge and clover_build");
+  if (v.slab) return set_error(QCD_ERR_STATE, "qcd_mhat_static is not available on a t-slab context");
   if ((const char*)out < (const char*)in + field && (const char*)in < (const char*)out + field)
     return set_error(QCD_ERR_ARG, "in and out overlap");
   void* base = nullptr;

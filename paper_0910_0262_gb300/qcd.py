@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "libqcd.so")
 
 QCD_OK = 0
 STATUS = {0: "QCD_OK", 1: "QCD_ERR_ARG", 2: "QCD_ERR_CUDA", 3: "QCD_ERR_NOMEM", 4: "QCD_ERR_STATE",
-          5: "QCD_ERR_NOT_POSDEF", 6: "QCD_ERR_NOT_CONVERGED", 7: "QCD_ERR_NAN", 8: "QCD_ERR_TIMEOUT"}
+          5: "QCD_ERR_NOT_POSDEF", 6: "QCD_ERR_NOT_CONVERGED", 7: "QCD_ERR_NAN", 8: "QCD_ERR_TIMEOUT",
+          9: "QCD_ERR_COMM"}
 
 QCD_GAUGE_RECON12 = 1
 QCD_OP_DSLASH_EO, QCD_OP_DSLASH_OE, QCD_OP_MHAT, QCD_OP_MDAGM, QCD_OP_CLOVER, QCD_OP_CLOVER_INV = range(6)
@@ -48,6 +49,17 @@ class SolverStats(ctypes.Structure):
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double),
                 ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+# callbacks of a t-slab call (include/qcd.h): the halo exchange and the sum over the ranks
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t)
+ALLREDUCE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int)
+
+
+class SlabComm(ctypes.Structure):
+    _fields_ = [("send_lo", ctypes.c_void_p), ("send_hi", ctypes.c_void_p), ("recv_lo", ctypes.c_void_p),
+                ("recv_hi", ctypes.c_void_p), ("exchange", EXCHANGE_FN), ("allreduce", ALLREDUCE_FN),
+                ("user", ctypes.c_void_p)]
 
 
 class QCDError(RuntimeError):
@@ -88,6 +100,13 @@ _SIGNATURES = {
                                ctypes.POINTER(SolverParams), ctypes.POINTER(SolverStats)]),
     "qcd_probe_fma_peak": (ctypes.c_int, [ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
     "qcd_probe_copy_bandwidth": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, _P, ctypes.POINTER(ctypes.c_double)]),
+    "qcd_create_slab": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, _P]),
+    "qcd_slab_halo_bytes": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]),
+    "qcd_slab_dslash": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(SlabComm)]),
+    "qcd_slab_cg_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(SolverParams),
+                                         ctypes.POINTER(SolverStats), ctypes.POINTER(SlabComm)]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -249,6 +268,31 @@ def qcd_probe_copy_bandwidth(nbytes, reps=20, stream=None):
     v = ctypes.c_double()
     _check(lib().qcd_probe_copy_bandwidth(int(nbytes), int(reps), stream, ctypes.byref(v)))
     return v.value
+
+
+def qcd_create_slab(dims, t_offset, t_local, t_bc=-1.0, stream=None):
+    ctx = _P()
+    d = (ctypes.c_int * 4)(*dims)
+    _check(lib().qcd_create_slab(ctypes.byref(ctx), d, int(t_offset), int(t_local), float(t_bc), stream))
+    return ctx
+
+
+def qcd_slab_halo_bytes(ctx, precision, nrhs):
+    n = ctypes.c_size_t()
+    _check(lib().qcd_slab_halo_bytes(ctx, int(precision), int(nrhs), ctypes.byref(n)))
+    return n.value
+
+
+def qcd_slab_dslash(ctx, out_ptr, in_ptr, op, dagger, precision, nrhs, comm):
+    return _check(lib().qcd_slab_dslash(ctx, out_ptr, in_ptr, int(op), int(bool(dagger)), int(precision), int(nrhs),
+                                        ctypes.byref(comm)))
+
+
+def qcd_slab_cg_solve(ctx, x_ptr, b_ptr, nrhs, params, stats, comm):
+    s = lib().qcd_slab_cg_solve(ctx, x_ptr, b_ptr, int(nrhs), ctypes.byref(params), stats, ctypes.byref(comm))
+    if s not in (QCD_OK, 6):
+        _check(s)
+    return s
 
 
 def qcd_last_error():
