@@ -839,16 +839,47 @@ __global__ void __launch_bounds__(128) dslash_split_kernel(DslashArgs A) {
   dslash_split_body<P, RECON, EPI, HALO>(A);
 }
 
-// y = C x for chiral block b of a clover pair decoded to FP32 in shared memory (value m of block b of
-// the site in lane at scl[(36 b + m) * 32 + lane]: 6 diagonal reals, then 15 strictly-lower complex)
+// Staged copies of the site kernel: per site, the 8 links (2 mu, 2 mu + 1: forward, backward) as 10
+// complex numbers each (9 and a pad, so that every link starts on 16 bytes) and the clover pair's 72
+// values, each site's run padded by 16 bytes so that the 16-byte reads of eight consecutive lanes hit
+// distinct banks.
+constexpr int STG_LINK_STRIDE = 8 * 20 + 4;  // floats per site of the staged links
+constexpr int STG_CLOVER_STRIDE = 72 + 4;     // floats per site of the staged clover pair
+
+// link j (= 2 mu for U_mu(x), 2 mu + 1 for U_mu(x - mu)) of the site in `lane`
+template <typename R>
+__device__ __forceinline__ void staged_link(const float* sl, int lane, int j, cx<R> u[9]) {
+  const float4* q = reinterpret_cast<const float4*>(sl + lane * STG_LINK_STRIDE + 20 * j);
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const float4 v = q[k];
+    u[2 * k] = cmk(R(v.x), R(v.y));
+    u[2 * k + 1] = cmk(R(v.z), R(v.w));
+  }
+  const float2 v = *reinterpret_cast<const float2*>(q + 4);
+  u[8] = cmk(R(v.x), R(v.y));
+}
+
+// y = C x for chiral block b of a staged clover pair (values 36 b .. 36 b + 35 of the site's run: 6
+// diagonal reals, then 15 strictly-lower complex)
 template <typename R>
 __device__ __forceinline__ void clover_apply_smem(const float* scl, int lane, int b, const cx<R> x[6], cx<R> y[6]) {
+  const float4* q = reinterpret_cast<const float4*>(scl + lane * STG_CLOVER_STRIDE + 36 * b);
+  float f[36];
+#pragma unroll
+  for (int k = 0; k < 9; k++) {
+    const float4 v = q[k];
+    f[4 * k] = v.x;
+    f[4 * k + 1] = v.y;
+    f[4 * k + 2] = v.z;
+    f[4 * k + 3] = v.w;
+  }
   R d[6];
   cx<R> L[15];
 #pragma unroll
-  for (int i = 0; i < 6; i++) d[i] = scl[(36 * b + i) * 32 + lane];
+  for (int i = 0; i < 6; i++) d[i] = R(f[i]);
 #pragma unroll
-  for (int k = 0; k < 15; k++) L[k] = cmk(R(scl[(36 * b + 6 + 2 * k) * 32 + lane]), R(scl[(36 * b + 7 + 2 * k) * 32 + lane]));
+  for (int k = 0; k < 15; k++) L[k] = cmk(R(f[6 + 2 * k]), R(f[7 + 2 * k]));
   hermitian6_accumulate(d, L, x, y);
 }
 
@@ -867,8 +898,9 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
   using RR = typename Real<PR>::T;
   // (staging the clover pair as well as the links: 8 RHS FP32 on 32^3 x 64 757 -> 707 us)
   constexpr bool SCL = STAGED && EPI != EPI_NONE;
-  __shared__ cx<R> sl[STAGED ? 8 * 9 * 32 : 1];  // [link 2 mu + bwd][element][site]
-  __shared__ float scl[SCL ? 72 * 32 : 1];       // [clover value][site]
+  static_assert(!STAGED || P != 64, "staging holds FP32 values");
+  __shared__ __align__(16) float sl[STAGED ? 32 * STG_LINK_STRIDE : 4];    // [site][link][10 complex]
+  __shared__ __align__(16) float scl[SCL ? 32 * STG_CLOVER_STRIDE : 4];     // [site][72 values]
   if ((A.halt && *A.halt) || (A.gate && !*A.gate)) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int G = STAGED ? 1 : (A.nrhs == 1 ? 4 : (A.nrhs == 2 ? 2 : 1)), W = 4 / G;
@@ -884,8 +916,11 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
         cx<R> u[9];
         if ((j & 1) == 0) GaugeIO<P, RECON>::load(A.gauge, Vh, A.p, mu, ss.i >> 1, u);
         else GaugeIO<P, RECON>::load(A.gauge, Vh, 1 - A.p, mu, neighbor_bwd(A.g, ss, mu) >> 1, u);
+        float4* q = reinterpret_cast<float4*>(sl + l * STG_LINK_STRIDE + 20 * j);
 #pragma unroll
-        for (int e = 0; e < 9; e++) sl[(j * 9 + e) * 32 + l] = u[e];
+        for (int e = 0; e < 4; e++)
+          q[e] = make_float4(float(u[2 * e].re), float(u[2 * e].im), float(u[2 * e + 1].re), float(u[2 * e + 1].im));
+        *reinterpret_cast<float2*>(q + 4) = make_float2(float(u[8].re), float(u[8].im));
       }
     }
     if (SCL) {
@@ -894,14 +929,8 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
         const float4* q = static_cast<const float4*>(A.clover);
         for (int it = threadIdx.x; it < 18 * 32; it += 128) {
           const int v = it >> 5, l = it & 31;  // float4 v = 9 b + k of the pair
-          if (hs0 + l < Vh) {
-            const float4 f = __ldg(q + (size_t)v * Vh + hs0 + l);
-            const int m = 36 * (v / 9) + 4 * (v % 9);
-            scl[(m + 0) * 32 + l] = f.x;
-            scl[(m + 1) * 32 + l] = f.y;
-            scl[(m + 2) * 32 + l] = f.z;
-            scl[(m + 3) * 32 + l] = f.w;
-          }
+          if (hs0 + l < Vh)  // float4 v holds values 4 v .. 4 v + 3 of the pair (block v / 9)
+            *reinterpret_cast<float4*>(scl + l * STG_CLOVER_STRIDE + 4 * v) = __ldg(q + (size_t)v * Vh + hs0 + l);
         }
       } else {
         const uint4* q = static_cast<const uint4*>(A.clover);
@@ -910,15 +939,9 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
           if (hs0 + l < Vh) {
             const uint4 f = __ldg(q + (size_t)v * Vh + hs0 + l);
             const float2 a = h2f(f.x), b = h2f(f.y), c = h2f(f.z), d = h2f(f.w);
-            const int m = 8 * v;
-            scl[(m + 0) * 32 + l] = a.x;
-            scl[(m + 1) * 32 + l] = a.y;
-            scl[(m + 2) * 32 + l] = b.x;
-            scl[(m + 3) * 32 + l] = b.y;
-            scl[(m + 4) * 32 + l] = c.x;
-            scl[(m + 5) * 32 + l] = c.y;
-            scl[(m + 6) * 32 + l] = d.x;
-            scl[(m + 7) * 32 + l] = d.y;
+            float4* o = reinterpret_cast<float4*>(scl + l * STG_CLOVER_STRIDE + 8 * v);
+            o[0] = make_float4(a.x, a.y, b.x, b.y);
+            o[1] = make_float4(c.x, c.y, d.x, d.y);
           }
         }
       }
@@ -948,11 +971,8 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
           constexpr int MU = decltype(mu_c)::value;
           if (STAGED) {
             dir_index<MU>(A.g, s, L);
-#pragma unroll
-            for (int e = 0; e < 9; e++) {
-              L.uf[e] = sl[((2 * MU) * 9 + e) * 32 + lane];
-              L.ub[e] = sl[((2 * MU + 1) * 9 + e) * 32 + lane];
-            }
+            staged_link(sl, lane, 2 * MU, L.uf);
+            staged_link(sl, lane, 2 * MU + 1, L.ub);
           } else {
             load_dir<P, RECON, MU>(A, s, L);
           }
