@@ -48,7 +48,7 @@ WORKLOAD = "c1_16^4"
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernel, with the summary
 # that holds the command; a kernel changed since its capture has no entry (traffic null)
 NCU_TRAFFIC = {
-    "cg_persistent_p32": (41.2e6, "profiles/cg_persistent_16x16x16x16.md"),
+    "cg_persistent_p32": (41.4e6, "profiles/cg_persistent_16x16x16x16.md"),
 }
 
 
@@ -67,6 +67,7 @@ def parse():
                     help="skip the 32^3x64 8-RHS batched-mixed vs sequential-FP64 solve comparison")
     ap.add_argument("--no-md", action="store_true",
                     help="skip the clover-determinant, full-solve and R-algorithm sections")
+    ap.add_argument("--no-slab", action="store_true", help="skip the two-slab time decomposition section")
     ap.add_argument("--only", default=None, choices=[None, "dslash", "peaks"],
                     help="dslash: only apply Mhat^dag Mhat (FP32 and FP64) a few times, for profiler captures; "
                          "peaks: only measure the FP64 / FP32 FMA and L2 copy denominators")
@@ -365,6 +366,8 @@ def run_ours(args, world, rank, local):
     if not args.no_md:
         result["clover_det_and_full_solve"] = clover_det_section(op, x, b, stream)
         result["r_algorithm_step"] = r_step_section(op, U, w, stream)
+    if not args.no_slab and world == 1:
+        result["slab_decomposition"] = slab_section(w)
     if not args.no_hbm or not args.no_batched:
         result.update(large_volume(dev, hbm_peak, not args.no_hbm, not args.no_batched, jobs is not None))
     if not args.no_hbm:
@@ -613,6 +616,74 @@ def largest_volume(dev, hbm_peak, do_errors=False):
         res["errors"] = sampled_mhat_errors(op, U_np, b, dims, 0.12, 1.0, -1.0)
     op.close()
     return res
+
+
+def slab_section(w, reps=5):
+    """The time decomposition on one GPU: the step's lattice cut into two t-slabs, each a context of its
+    own on a stream of its own, driven by a host thread and exchanging halos through device copies
+    (LocalSlabGroup).  Times Mhat^dag Mhat in FP32 (four exchanges) and the mixed FP32 solve to 1e-8
+    against one context, with the halo bytes per exchange.  On one GPU every exchange synchronises both
+    slabs on the host, so this measures the halo path's overhead, not a multi-GPU speed."""
+    import torch
+    from paper_0910_0262_gb300 import synth, slab
+    from paper_0910_0262_gb300 import qcd as Q
+    dims = w["dims"]
+    U, b = synth.make_problem(dims, w["eps"], w["seed"], 1)
+    bounds = [slab.slab_bounds(dims[3], 2, r) for r in range(2)]
+    grp = slab.LocalSlabGroup(2)
+    ops = []
+    for r, (t0, tl) in enumerate(bounds):
+        st = torch.cuda.Stream()
+        op = slab.SlabCloverWilson(dims, t0, tl, grp.member(r), w["t_bc"], stream=st)
+        with torch.cuda.stream(st):
+            op.load_gauge(torch.from_numpy(slab.extended_links(U, t0, tl)).cuda(), recon12=True)
+        op.clover_build(w["kappa"], w["csw"])
+        ops.append(op)
+    bd = torch.from_numpy(b).cuda()
+    kw = dict(tol=1e-8, inner_prec=32, reliable_every=50, reliable_delta=0.1, max_iter=20000)
+
+    def on_slabs(fn):
+        def job(r):
+            op = ops[r]
+            a, c = slab.slab_rows(dims, op.t_offset, op.t_local)
+            with torch.cuda.stream(op.stream):
+                out = fn(op, bd[:, a:c].contiguous())
+                op.stream.synchronize()
+            return out
+        t0 = time.perf_counter()
+        res = grp.run([lambda r=r: job(r) for r in range(2)])
+        return res, 1e3 * (time.perf_counter() - t0)
+
+    t_mdagm, t_solve, iters = [], [], None
+    for k in range(reps + 1):
+        _, t = on_slabs(lambda op, v: op.dslash(v, Q.QCD_OP_MDAGM, precision=32))
+        res, ts = on_slabs(lambda op, v: op.cg_solve(v, **kw))
+        if k:
+            t_mdagm.append(t)
+            t_solve.append(ts)
+        iters = res[0][1][0]["iters"]
+        ok = all(r[2] for r in res)
+    one = Q.CloverWilson(dims, w["t_bc"])
+    one.load_gauge(torch.from_numpy(U).cuda(), recon12=True)
+    one.clover_build(w["kappa"], w["csw"])
+    t1 = []
+    for k in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, st1, ok1 = one.cg_solve(bd, **kw)
+        torch.cuda.synchronize()
+        if k:
+            t1.append(1e3 * (time.perf_counter() - t0))
+    one.close()
+    halo = Q.qcd_slab_halo_bytes(ops[0].ctx, 32, 1)
+    for op in ops:
+        op.close()
+    return {"dims": list(dims), "slabs": [list(s) for s in bounds], "gpus": 1,
+            "mdagm_fp32_ms_two_slabs": float(np.median(t_mdagm)),
+            "mixed_solve_ms_two_slabs": float(np.median(t_solve)), "mixed_solve_ms_one_context": float(np.median(t1)),
+            "iters_two_slabs": iters, "iters_one_context": st1[0]["iters"], "converged": bool(ok and ok1),
+            "halo_bytes_per_exchange_fp32": halo, "exchanges_per_mdagm": 4,
+            "timing": f"median of {reps} after one, host wall clock (each exchange synchronises both slabs)"}
 
 
 def run_e2e(op, U_np, b_np, w, stream, dev):
