@@ -18,6 +18,17 @@ void launch_split(int epi, const DslashArgs& a, cudaStream_t st) {
   }
 }
 
+// FP64 passes without the fused CG update on pair units (one wave of 64-thread blocks at 16^4)
+template <int RECON>
+void launch_pair64(int epi, const DslashArgs& a, cudaStream_t st) {
+  const int nb = (a.g.Vh + 31) / 32;
+  switch (epi) {
+    case EPI_NONE: dslash_pair64_kernel<RECON, EPI_NONE><<<nb, 64, 0, st>>>(a); break;
+    case EPI_CLOVER_INV: dslash_pair64_kernel<RECON, EPI_CLOVER_INV><<<nb, 64, 0, st>>>(a); break;
+    default: dslash_pair64_kernel<RECON, EPI_XPAY><<<nb, 64, 0, st>>>(a); break;
+  }
+}
+
 template <int RECON>
 void launch_split_fp16(int epi, const DslashArgs& a, cudaStream_t st) {
   const int nb = (a.g.Vh + 31) / 32;
@@ -73,8 +84,11 @@ const int SITE_KERNEL_MIN_VH = QCD_SITE_KERNEL_MIN_VH;
 template <int P, int RECON>
 void launch_prec(int epi, const DslashArgs& a, cudaStream_t st) {
   if constexpr (P == 64) {
-    // (one thread per site measured within 7% either way: 16^4 90 vs 85 us, 32^3 x 64 2260 vs 2293 us)
-    launch_split<P, RECON>(epi, a, st);
+    // pair units against the four-warp split kernel, M^dag M passes: 16^4 83.3 vs 84.0 us, 32^3 x 64
+    // 2222 vs 2292 us, 8 RHS 17.7 vs 18.7 ms (one thread per site was within 7% of the split kernel
+    // either way); the fused CG update stays on the split kernel
+    if (epi == EPI_XPAY_CG) launch_split<P, RECON>(epi, a, st);
+    else launch_pair64<RECON>(epi, a, st);
   } else {
     if (a.nrhs > 1 || a.g.Vh >= SITE_KERNEL_MIN_VH) launch_site<P, RECON>(epi, a, st);
     else if constexpr (P == 16) launch_split_fp16<RECON>(epi, a, st);

@@ -800,6 +800,91 @@ __device__ __forceinline__ float pair_unit(const DslashArgs& A, int hh, bool val
   return pair_unit_b<P, RECON, EPI, COH, 1>(A, hh, valid, s, q, cg_active, cg_alpha, xch, stage);
 }
 
+// FP64 pair unit: the hopping operator for one block of 32 output sites on a 64-thread block, warp B
+// computing the four hops along mu = 2B, 2B+1 of RHS r and finishing chiral block B (epilogue and
+// stores) after the two warps swap half of their partial sums.  Used by the standalone FP64 hopping
+// kernel (the reliable updates' passes): with two threads per site and 64-thread blocks, 8 blocks per
+// SM hold the 1024 site blocks of a 16^4 parity in one wave, where 128-thread blocks of four warps at 4
+// per SM needed 1.7 (the FP64 pipe idled through the second wave's partly filled SMs).
+template <int RECON, int EPI, int B>
+__device__ __forceinline__ double pair_unit64_b(const DslashArgs& A, int hh, bool valid, const Site& s, int r,
+                                                cx<double> (*xch)[6][32]) {
+  constexpr int b = B;
+  const int lane = threadIdx.x & 31;
+  const int Vh = A.g.Vh;
+  cx<double> acc[12];
+  if (valid) {
+    DirLinks<double> L;
+    load_dir<64, RECON, 2 * B>(A, s, L);
+    hop_dir<64, 2 * B, LD_NC, true>(A, L, r, acc);
+    load_dir<64, RECON, 2 * B + 1>(A, s, L);
+    hop_dir<64, 2 * B + 1, LD_NC>(A, L, r, acc);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 12; c++) acc[c] = cmk(0.0, 0.0);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; k++) xch[1 - b][k][lane] = acc[6 * (1 - b) + k];
+  __syncthreads();
+  double nrm = 0.0;
+  if (valid) {
+    cx<double> v[6], res[6];
+#pragma unroll
+    for (int k = 0; k < 6; k++) v[k] = acc[6 * b + k] + xch[b][k][lane];
+    if (EPI == EPI_NONE) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = v[k];
+    } else if (EPI == EPI_CLOVER_INV) {
+      CloverIO<64>::apply(A.clover, Vh, hh, b, v, res);
+    } else {
+      cx<double> xs[6], cxs[6];
+      SpinorIO<64>::load_block(A.x, nullptr, Vh, r, hh, b, xs);
+      if (A.x_g5 && b == 1) {
+#pragma unroll
+        for (int k = 0; k < 6; k++) xs[k] = -xs[k];
+      }
+      CloverIO<64>::apply(A.clover, Vh, hh, b, xs, cxs);
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        res[k].re = fma(A.a, v[k].re, cxs[k].re);
+        res[k].im = fma(A.a, v[k].im, cxs[k].im);
+      }
+    }
+    if (A.out_g5 && b == 1) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) res[k] = -res[k];
+    }
+    if (A.do_norm) {
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        nrm = fma(res[k].re, res[k].re, nrm);
+        nrm = fma(res[k].im, res[k].im, nrm);
+      }
+    }
+    SpinorIO<64>::store_block(A.out, nullptr, Vh, r, hh, b, res);
+  }
+  __syncthreads();  // the exchange area is rewritten by the next RHS
+  return nrm;
+}
+
+// Standalone FP64 hopping kernel on pair units (epilogues EPI_NONE, EPI_CLOVER_INV, EPI_XPAY), looping
+// over the RHS; one 64-thread block per 32 output sites.
+template <int RECON, int EPI>
+__global__ void __launch_bounds__(64, 8) dslash_pair64_kernel(DslashArgs A) {
+  __shared__ cx<double> xch[2][6][32];
+  if ((A.halt && *A.halt) || (A.gate && !*A.gate)) return;
+  const int hh = blockIdx.x * 32 + (threadIdx.x & 31);
+  const bool valid = hh < A.g.Vh;
+  Site s;
+  if (valid) s = site_of(A.g, A.p, hh);
+  for (int r = 0; r < A.nrhs; r++) {
+    const double nrm = (threadIdx.x >> 5) == 0 ? pair_unit64_b<RECON, EPI, 0>(A, hh, valid, s, r, xch)
+                                                : pair_unit64_b<RECON, EPI, 1>(A, hh, valid, s, r, xch);
+    if (A.do_norm) block_partial<64>(nrm, r, blockIdx.x, gridDim.x, A.red);
+  }
+  if (A.do_norm) grid_finish<64>(A.nrhs, gridDim.x, gridDim.x, A.red);
+}
+
 // Site of a lane in the block of 32 sites starting at 32 * sb.
 __device__ __forceinline__ void split_prologue(const DslashArgs& A, int sb, int& hh, bool& valid, Site& s) {
   hh = sb * 32 + (threadIdx.x & 31);
