@@ -205,6 +205,22 @@ __device__ __forceinline__ void su3_mul(const cx<R> u[9], const cx<R> v[6], cx<R
   }
 }
 
+// out_a = init_a + sum_b conj(U_ba) v_b (the products chained onto init)
+template <typename R>
+__device__ __forceinline__ void su3_adj_mul_onto(const cx<R> u[9], const cx<R> v[6], const cx<R> init[6], cx<R> w[6]) {
+#pragma unroll
+  for (int s = 0; s < 2; s++) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<R> acc = init[3 * s + a];
+      acc = cfmac(u[a], v[3 * s], acc);
+      acc = cfmac(u[3 + a], v[3 * s + 1], acc);
+      acc = cfmac(u[6 + a], v[3 * s + 2], acc);
+      w[3 * s + a] = acc;
+    }
+  }
+}
+
 // out_a = sum_b conj(U_ba) v_b
 template <typename R>
 __device__ __forceinline__ void su3_adj_mul(const cx<R> u[9], const cx<R> v[6], cx<R> w[6]) {
@@ -293,6 +309,42 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
   using R = typename Real<P>::T;
   constexpr bool H = HALO && MU == 3;
   cx<R> sp[12], h[6], w[6];
+  if constexpr (P == 64 && MU != 3) {
+    // FP64, unsigned hops (bound by the FP64 pipe, so every instruction counts): the two hops along mu
+    // expand to rows 0, 1: wf + wb and rows 2, 3: L(wf) - L(wb) = L(wf - wb), with L the fixed +-1 / +-i
+    // map of the forward projector.  wb is chained onto wf (s = wf + wb, no separate adds) and
+    // d = 2 wf - s, which saves 12 of the 48 additions of two separate expansions.
+    load_neighbor<P, COH>(A, r, L.nbf, sp);
+    if (A.in_g5) apply_g5(sp);
+    project<MU, -1>(sp, h);
+    cx<R> wf[6];
+    su3_mul(L.uf, h, wf);
+    load_neighbor<P, COH>(A, r, L.nbb, sp);
+    if (A.in_g5) apply_g5(sp);
+    project<MU, +1>(sp, h);
+    su3_adj_mul_onto(L.ub, h, wf, w);  // w = wf + wb
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<R> d0, d1, lo, hi;
+      d0.re = fma(R(2), wf[a].re, -w[a].re);
+      d0.im = fma(R(2), wf[a].im, -w[a].im);
+      d1.re = fma(R(2), wf[3 + a].re, -w[3 + a].re);
+      d1.im = fma(R(2), wf[3 + a].im, -w[3 + a].im);
+      expand_rows<MU, -1>(d0, d1, lo, hi);
+      if (FIRST) {
+        acc[a] = w[a];
+        acc[3 + a] = w[3 + a];
+        acc[6 + a] = lo;
+        acc[9 + a] = hi;
+      } else {
+        acc[a] = acc[a] + w[a];
+        acc[3 + a] = acc[3 + a] + w[3 + a];
+        acc[6 + a] = acc[6 + a] + lo;
+        acc[9 + a] = acc[9 + a] + hi;
+      }
+    }
+    return;
+  }
   R f;
   if (H && L.hf >= 0) {
     HaloIO<P>::load(A.halo_hi, A.g.XYZ / 2, r, L.hf, h);
