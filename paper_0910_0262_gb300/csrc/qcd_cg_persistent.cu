@@ -190,7 +190,7 @@ struct PcShape {
 };
 
 // one phase over the site blocks this block owns; returns the thread's share of the phase's sum
-template <int P, int RECON, int EPI>
+template <int P, int RECON, int EPI, bool LAZY = false>
 __device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Real<P>::T> (*part)[12][32],
                                             PairXch<float> (*xch)[2], uint4* stage, double alpha) {
   const int nsb = (A.g.Vh + 31) / 32;
@@ -205,8 +205,8 @@ __device__ __forceinline__ double run_phase(const DslashArgs& A, cx<typename Rea
       bool valid;
       Site s;
       split_prologue(A, sb, hh, valid, s);
-      v += pair_unit<P, RECON, EPI, LDM>(A, hh, valid, s, d, q, true, alpha, &xch[q][slot],
-                                         stage + w * PcShape<P>::PAIR_STAGE);
+      v += pair_unit<P, RECON, EPI, LDM, LAZY>(A, hh, valid, s, d, q, true, alpha, &xch[q][slot],
+                                               stage + w * PcShape<P>::PAIR_STAGE);
       slot ^= 1;
     }
   } else {
@@ -263,6 +263,11 @@ __global__ void __launch_bounds__(PcShape<P>::THREADS, PcShape<P>::MIN_BLOCKS)
   a2.in = Q.t;
   a2.in_norm = Q.t_n;
 
+  // FP32: the p update p = r + beta p of iteration k is formed where p is read in phases 1 and 2 of
+  // iteration k+1 (phase 2 writes it back), so phase 5 and its grid barrier are not needed; the first
+  // iteration of a launch finds p already updated (coefficients 0, 1)
+  constexpr bool LAZY = P == 32;
+  bool first = true;
   double alpha = 0.0, beta = 0.0, pAp = 0.0;
   unsigned bar_target = 0;
   while (true) {
@@ -270,7 +275,10 @@ __global__ void __launch_bounds__(PcShape<P>::THREADS, PcShape<P>::MIN_BLOCKS)
     a1.in = Q.p;
     a1.in_norm = Q.p_n;
     a1.in_g5 = 0;
-    run_phase<P, RECON, EPI_CLOVER_INV>(a1, part, xch, stage, 0.0);
+    a1.lz_r = Q.r;
+    a1.lz_a = first ? 0.f : 1.f;
+    a1.lz_b = first ? 1.f : float(beta);
+    run_phase<P, RECON, EPI_CLOVER_INV, LAZY>(a1, part, xch, stage, 0.0);
     if (!grid_barrier(Q.bar_count, bar_target, Q.bar_err)) return;
     // phase 2
     {
@@ -280,7 +288,10 @@ __global__ void __launch_bounds__(PcShape<P>::THREADS, PcShape<P>::MIN_BLOCKS)
       a.out = Q.y;
       a.out_norm = Q.y_n;
       a.do_norm = 1;
-      const double v = block_sum<BLOCK>(run_phase<P, RECON, EPI_XPAY>(a, part, xch, stage, 0.0));
+      a.lz_r = a1.lz_r;
+      a.lz_a = a1.lz_a;
+      a.lz_b = a1.lz_b;
+      const double v = block_sum<BLOCK>(run_phase<P, RECON, EPI_XPAY, LAZY>(a, part, xch, stage, 0.0));
       if (!grid_barrier_sum<BLOCK>(Q.bar_count, Q.bar_flag, bar_target, Q.bar_err, Q.part_pap, Q.totals, v, &pAp))
         return;
     }
@@ -330,7 +341,10 @@ __global__ void __launch_bounds__(PcShape<P>::THREADS, PcShape<P>::MIN_BLOCKS)
     iters += 1;
     since += 1;
     const bool want = rr_new <= st0.tol2 || since >= every || rr_new < delta2 * st0.rr_reliable;
-    if (!want) {
+    first = false;
+    // phase 5 (with LAZY only when the launch ends without a reliable update, so that the next launch
+    // finds p updated; at a reliable update the update's own p = r + beta p follows)
+    if (!want && (!LAZY || iters >= Q.iter_limit)) {
       // phase 5
       for (int h = blockIdx.x * BLOCK + threadIdx.x; h < Vh; h += gridDim.x * BLOCK) {
         cx<RR> rs[12];

@@ -55,6 +55,10 @@ struct DslashArgs {
   // and signed by the slab that sent it.
   const void* halo_lo;
   const void* halo_hi;
+  // LAZY loads (the persistent FP32 iteration): the input is p' = lz_b p + lz_a r, formed where it is
+  // read (p = in, r = lz_r, both FP32), so that the p update needs no pass of its own
+  const void* lz_r;
+  float lz_a, lz_b;
 };
 
 // Halo entries: six complex numbers (a projected half spinor) per face site and RHS, FP64 as
@@ -289,10 +293,22 @@ __device__ __forceinline__ void load_dir(const DslashArgs& A, const Site& s, Dir
 
 // psi_r at half index nb; returns the factor still to be applied (the FP16 per-site scale, which
 // commutes with the spin projection and the link multiply, so it is applied once to the result)
-template <int P, int COH>
+template <int P, int COH, bool LAZY = false>
 __device__ __forceinline__ typename Real<P>::T load_neighbor(const DslashArgs& A, int r, int nb,
                                                              cx<typename Real<P>::T> sp[12]) {
   using R = typename Real<P>::T;
+  if constexpr (LAZY) {
+    static_assert(P == 32, "lazy p updates serve the FP32 iteration");
+    cx<float> rs[12];
+    SpinorIO<32>::template load<COH>(A.in, nullptr, A.g.Vh, r, nb, sp);
+    SpinorIO<32>::template load<COH>(A.lz_r, nullptr, A.g.Vh, r, nb, rs);
+#pragma unroll
+    for (int c = 0; c < 12; c++) {  // the p update's own expression: fma(beta, p, r)
+      sp[c].re = fmaf(A.lz_b, sp[c].re, A.lz_a * rs[c].re);
+      sp[c].im = fmaf(A.lz_b, sp[c].im, A.lz_a * rs[c].im);
+    }
+    return R(1);
+  }
   if (P == 16)
     return SpinorIO<16>::template load_unscaled<COH>(A.in, A.in_norm, A.g.Vh, r, nb,
                                                      reinterpret_cast<cx<float>*>(sp));
@@ -303,23 +319,26 @@ __device__ __forceinline__ typename Real<P>::T load_neighbor(const DslashArgs& A
 // acc += (1 - g_mu) U_mu(x) psi_r(x+mu) + (1 + g_mu) U_mu(x-mu)^dag psi_r(x-mu)  (FIRST: acc =).
 // HALO (mu = t): a hop that leaves the slab takes the neighbour's projected half spinor (forward) or
 // its finished contribution (backward) from the halos instead of the field.
-template <int P, int MU, int COH = LD_NC, bool FIRST = false, bool HALO = false>
+template <int P, int MU, int COH = LD_NC, bool FIRST = false, bool HALO = false, bool FOLD = true,
+          bool LAZY = false>
 __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<typename Real<P>::T>& L, int r,
                                         cx<typename Real<P>::T> acc[12]) {
   using R = typename Real<P>::T;
   constexpr bool H = HALO && MU == 3;
   cx<R> sp[12], h[6], w[6];
-  if constexpr (P == 64 && MU != 3) {
-    // FP64, unsigned hops (bound by the FP64 pipe, so every instruction counts): the two hops along mu
-    // expand to rows 0, 1: wf + wb and rows 2, 3: L(wf) - L(wb) = L(wf - wb), with L the fixed +-1 / +-i
-    // map of the forward projector.  wb is chained onto wf (s = wf + wb, no separate adds) and
-    // d = 2 wf - s, which saves 12 of the 48 additions of two separate expansions.
-    load_neighbor<P, COH>(A, r, L.nbf, sp);
+  if constexpr (P != 16 && MU != 3 && FOLD) {
+    // Unsigned, unscaled hops: the two hops along mu expand to rows 0, 1: wf + wb and rows 2, 3:
+    // L(wf) - L(wb) = L(wf - wb), with L the fixed +-1 / +-i map of the forward projector.  wb is
+    // chained onto wf (s = wf + wb, no separate adds) and d = 2 wf - s, which saves 12 of the 48
+    // additions of two separate expansions (FP64 M^dag M pass at 16^4: 83.6 -> 81.6 us; the FP32
+    // single-RHS passes 161 -> 159 us at 32^3 x 64; the staged multi-RHS kernel, where the extra live
+    // registers cost a block per SM, keeps the separate expansions: FOLD = false).
+    load_neighbor<P, COH, LAZY>(A, r, L.nbf, sp);
     if (A.in_g5) apply_g5(sp);
     project<MU, -1>(sp, h);
     cx<R> wf[6];
     su3_mul(L.uf, h, wf);
-    load_neighbor<P, COH>(A, r, L.nbb, sp);
+    load_neighbor<P, COH, LAZY>(A, r, L.nbb, sp);
     if (A.in_g5) apply_g5(sp);
     project<MU, +1>(sp, h);
     su3_adj_mul_onto(L.ub, h, wf, w);  // w = wf + wb
@@ -350,7 +369,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
     HaloIO<P>::load(A.halo_hi, A.g.XYZ / 2, r, L.hf, h);
     f = R(1);
   } else {
-    f = load_neighbor<P, COH>(A, r, L.nbf, sp);
+    f = load_neighbor<P, COH, LAZY>(A, r, L.nbf, sp);
     if (A.in_g5) apply_g5(sp);
     project<MU, -1>(sp, h);
   }
@@ -363,7 +382,7 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
     accumulate<MU, +1>(w, acc);
     return;
   }
-  f = load_neighbor<P, COH>(A, r, L.nbb, sp);
+  f = load_neighbor<P, COH, LAZY>(A, r, L.nbb, sp);
   if (A.in_g5) apply_g5(sp);
   project<MU, +1>(sp, h);
   su3_adj_mul(L.ub, h, w);
@@ -373,11 +392,11 @@ __device__ __forceinline__ void hop_dir(const DslashArgs& A, const DirLinks<type
 }
 
 // acc = the two hops along mu of one output site and RHS r, links loaded here.
-template <int P, int RECON, int MU, int COH, bool HALO = false>
+template <int P, int RECON, int MU, int COH, bool HALO = false, bool LAZY = false>
 __device__ __forceinline__ void dir_unit(const DslashArgs& A, const Site& s, int r, cx<typename Real<P>::T> acc[12]) {
   DirLinks<typename Real<P>::T> L;
   load_dir<P, RECON, MU, HALO>(A, s, L);
-  hop_dir<P, MU, COH, true, HALO>(A, L, r, acc);
+  hop_dir<P, MU, COH, true, HALO, true, LAZY>(A, L, r, acc);
 }
 
 template <int P>
@@ -704,21 +723,26 @@ __device__ __forceinline__ void staged_clover_block(const uint4* st, int lane, i
 }
 
 // the hops along mu = 2B and 2B + 1 of one output site (acc = their sum)
-template <int P, int RECON, int COH, int B>
+template <int P, int RECON, int COH, int B, bool LAZY = false>
 __device__ __forceinline__ void pair_hops(const DslashArgs& A, const Site& s, cx<typename Real<P>::T> acc[12]) {
   using R = typename Real<P>::T;
   DirLinks<R> L;
-  dir_unit<P, RECON, 2 * B, COH>(A, s, 0, acc);
+  dir_unit<P, RECON, 2 * B, COH, false, LAZY>(A, s, 0, acc);
   load_dir<P, RECON, 2 * B + 1>(A, s, L);
-  hop_dir<P, 2 * B + 1, COH>(A, L, 0, acc);
+  hop_dir<P, 2 * B + 1, COH, false, false, true, LAZY>(A, L, 0, acc);
 }
 
 // The pair unit on warp B of its pair (B is the chiral block the warp finishes; a compile-time
 // constant, so that the partial sums stay in registers).
-template <int P, int RECON, int EPI, int COH, int B>
+// LAZY (FP32): with EPI_CLOVER_INV the input p' = lz_b p + lz_a r is formed at every neighbour; with
+// EPI_XPAY the local term x = p is replaced by p' (formed from the staged p and r blocks) and p' is
+// written back over p, which completes the p update of the iteration.
+template <int P, int RECON, int EPI, int COH, int B, bool LAZY = false>
 __device__ __forceinline__ float pair_unit_b(const DslashArgs& A, int hh, bool valid, const Site& s, int q,
                                              bool cg_active, double cg_alpha, PairXch<float>* xch, uint4* stage) {
   static_assert(P == 32 || P == 16, "the pair unit serves the FP32 and FP16 inner iteration");
+  static_assert(!LAZY || (P == 32 && (EPI == EPI_CLOVER_INV || EPI == EPI_XPAY)), "lazy p: FP32 phases 1, 2");
+  constexpr bool LZ_HOPS = LAZY && EPI == EPI_CLOVER_INV, LZ_X = LAZY && EPI == EPI_XPAY;
   using ST = PairStage<P, EPI>;
   constexpr int b = B;
   const int lane = threadIdx.x & 31;
@@ -737,11 +761,13 @@ __device__ __forceinline__ float pair_unit_b(const DslashArgs& A, int hh, bool v
     }
     if (ST::XR) stage_spinor_block<P>(stage + ST::OFF_X, A.x, A.x_norm, Vh, hh0, b, lane, n);
     if (ST::CG && cg_active) stage_spinor_block<P>(stage + ST::OFF_P, A.cg_p, A.cg_p_norm, Vh, hh0, b, lane, n);
+    // (the warp's rows are sized for EPI_XPAY_CG, whose p rows follow x: r takes their place here)
+    if (LZ_X) stage_spinor_block<32>(stage + ST::OFF_X + ST::SPBN, A.lz_r, nullptr, Vh, hh0, b, lane, n);
     cp_async_commit();
   }
   cx<float> acc[12];
   if (valid) {
-    pair_hops<P, RECON, COH, B>(A, s, acc);
+    pair_hops<P, RECON, COH, B, LZ_HOPS>(A, s, acc);
   } else {
 #pragma unroll
     for (int c = 0; c < 12; c++) acc[c] = cmk(0.f, 0.f);
@@ -764,6 +790,16 @@ __device__ __forceinline__ float pair_unit_b(const DslashArgs& A, int hh, bool v
     } else {  // EPI_XPAY, EPI_XPAY_CG
       cx<float> xs[6], cxs[6];
       staged_spinor_block<P>(stage + ST::OFF_X, lane, b, xs);
+      if (LZ_X) {
+        cx<float> rs[6];
+        staged_spinor_block<32>(stage + ST::OFF_X + ST::SPBN, lane, b, rs);
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+          xs[k].re = fmaf(A.lz_b, xs[k].re, A.lz_a * rs[k].re);
+          xs[k].im = fmaf(A.lz_b, xs[k].im, A.lz_a * rs[k].im);
+        }
+        SpinorIO<32>::store_block(const_cast<void*>(A.x), nullptr, Vh, 0, hh, b, xs);
+      }
       if (A.x_g5 && b == 1) {
 #pragma unroll
         for (int k = 0; k < 6; k++) xs[k] = -xs[k];
@@ -845,11 +881,12 @@ __device__ __forceinline__ float pair_unit_b(const DslashArgs& A, int hh, bool v
 // |r|^2 (EPI_XPAY_CG, with cg_alpha applied when cg_active), summed in FP32 over the site's
 // components.  xch: the pair's exchange area for this unit (alternate two per pair between units, so
 // that one barrier per unit suffices); stage: the warp's PairStage<P, EPI> rows.  P is 32 or 16.
-template <int P, int RECON, int EPI, int COH>
+template <int P, int RECON, int EPI, int COH, bool LAZY = false>
 __device__ __forceinline__ float pair_unit(const DslashArgs& A, int hh, bool valid, const Site& s, int d, int q,
                                            bool cg_active, double cg_alpha, PairXch<float>* xch, uint4* stage) {
-  if (d == 0) return pair_unit_b<P, RECON, EPI, COH, 0>(A, hh, valid, s, q, cg_active, cg_alpha, xch, stage);
-  return pair_unit_b<P, RECON, EPI, COH, 1>(A, hh, valid, s, q, cg_active, cg_alpha, xch, stage);
+  if (d == 0)
+    return pair_unit_b<P, RECON, EPI, COH, 0, LAZY>(A, hh, valid, s, q, cg_active, cg_alpha, xch, stage);
+  return pair_unit_b<P, RECON, EPI, COH, 1, LAZY>(A, hh, valid, s, q, cg_active, cg_alpha, xch, stage);
 }
 
 // FP64 pair unit: the hopping operator for one block of 32 output sites on a 64-thread block, warp B
@@ -1115,11 +1152,11 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
           }
         };
         links(std::integral_constant<int, 0>());
-        hop_dir<P, 0, LD_NC, true>(A, L, r, acc);
+        hop_dir<P, 0, LD_NC, true, false, !STAGED>(A, L, r, acc);
         links(std::integral_constant<int, 1>());
-        hop_dir<P, 1, LD_NC>(A, L, r, acc);
+        hop_dir<P, 1, LD_NC, false, false, !STAGED>(A, L, r, acc);
         links(std::integral_constant<int, 2>());
-        hop_dir<P, 2, LD_NC>(A, L, r, acc);
+        hop_dir<P, 2, LD_NC, false, false, !STAGED>(A, L, r, acc);
         links(std::integral_constant<int, 3>());
         hop_dir<P, 3, LD_NC>(A, L, r, acc);
       }
