@@ -49,6 +49,8 @@ WORKLOAD = "c1_16^4"
 # that holds the command; a kernel changed since its capture has no entry (traffic null)
 NCU_TRAFFIC = {
     "cg_persistent_p32": (41.4e6, "profiles/cg_persistent_16x16x16x16.md"),
+    # mean of the clover-inverse (63.3 MB) and xpay (70.2 MB) passes over a step's mix of the two
+    "dslash_p64": (66.7e6, "profiles/dslash_pair64_16x16x16x16.md"),
 }
 
 
