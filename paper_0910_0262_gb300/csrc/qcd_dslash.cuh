@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "qcd_internal.cuh"
+#include "qcd_spinpair.cuh"
 
 namespace qcd {
 
@@ -1057,6 +1058,47 @@ __device__ __forceinline__ void clover_apply_smem(const float* scl, int lane, in
   hermitian6_accumulate(d, L, x, y);
 }
 
+// The eight hops of FP16 site s and RHS r on spin-paired registers (qcd_spinpair.cuh); STAGED: the
+// block's links staged as broadcast pairs at lks (the site's run), else loaded here.
+template <int RECON, bool STAGED>
+__device__ __forceinline__ void hops_fp16_sp(const DslashArgs& A, const Site& s, int r, const float4* lks,
+                                             cx<float> acc[12]) {
+  const float g = A.in_g5 ? -1.f : 1.f;
+  const float2 SG[4] = {make_float2(g, g), make_float2(g, -g), make_float2(-g, g), make_float2(-g, -g)};
+  const float2 M1 = make_float2(-1.f, -1.f);
+  const int Vh = A.g.Vh;
+  SpAcc sa;
+  auto dir = [&](auto mu_c, auto f01_c, auto f23_c) {
+    constexpr int MU = decltype(mu_c)::value;
+    constexpr bool F01 = decltype(f01_c)::value, F23 = decltype(f23_c)::value;
+    DirLinks<float> L;
+    dir_index<MU>(A.g, s, L);
+    SpinorIO<16>::Raw qf, qb;
+    load_nb_sp(A.in, A.in_norm, Vh, r, L.nbf, qf);
+    load_nb_sp(A.in, A.in_norm, Vh, r, L.nbb, qb);
+    if constexpr (STAGED) {
+      hop_sp<MU, -1, F01, F23>(qf, StagedLinkSp{lks + 18 * MU}, L.sf, SG, M1, sa);
+      hop_sp<MU, +1, false, false>(qb, StagedLinkSp{lks + 18 * MU + 9}, L.sb, SG, M1, sa);
+    } else {
+      GaugeIO<16, RECON>::load(A.gauge, Vh, A.p, MU, s.i >> 1, L.uf);
+      GaugeIO<16, RECON>::load(A.gauge, Vh, 1 - A.p, MU, L.nbb, L.ub);
+      hop_sp<MU, -1, F01, F23>(qf, RegLinkSp{L.uf}, L.sf, SG, M1, sa);
+      hop_sp<MU, +1, false, false>(qb, RegLinkSp{L.ub}, L.sb, SG, M1, sa);
+    }
+  };
+  using I0 = std::integral_constant<int, 0>;
+  using I1 = std::integral_constant<int, 1>;
+  using I2 = std::integral_constant<int, 2>;
+  using I3 = std::integral_constant<int, 3>;
+  using BT = std::true_type;
+  using BF = std::false_type;
+  dir(I0(), BT(), BF());
+  dir(I1(), BF(), BF());
+  dir(I2(), BF(), BT());
+  dir(I3(), BF(), BF());
+  sp_unpack(sa, acc);
+}
+
 // Hopping kernel with one thread per (site, RHS).  A block of four warps covers 32 sites (64 when
 // nrhs = 2: two site groups of two warps; 128 when nrhs = 1: four groups of one warp); warp k of a
 // site group takes RHS k, k + W, ... (W warps per group) and computes all eight hops and the
@@ -1073,7 +1115,9 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
   // (staging the clover pair as well as the links: 8 RHS FP32 on 32^3 x 64 757 -> 707 us)
   constexpr bool SCL = STAGED && EPI != EPI_NONE;
   static_assert(!STAGED || P != 64, "staging holds FP32 values");
-  __shared__ __align__(16) float sl[STAGED ? 32 * STG_LINK_STRIDE : 4];    // [site][link][10 complex]
+  // [site][link][10 complex]; FP16: [site][link][9 entries as (re, re, im, im)] (spin-paired hops)
+  constexpr int LSTRIDE = P == 16 ? SP_LINK_STRIDE : STG_LINK_STRIDE;
+  __shared__ __align__(16) float sl[STAGED ? 32 * LSTRIDE : 4];
   __shared__ __align__(16) float scl[SCL ? 32 * STG_CLOVER_STRIDE : 4];     // [site][72 values]
   if ((A.halt && *A.halt) || (A.gate && !*A.gate)) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1090,11 +1134,18 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
         cx<R> u[9];
         if ((j & 1) == 0) GaugeIO<P, RECON>::load(A.gauge, Vh, A.p, mu, ss.i >> 1, u);
         else GaugeIO<P, RECON>::load(A.gauge, Vh, 1 - A.p, mu, neighbor_bwd(A.g, ss, mu) >> 1, u);
-        float4* q = reinterpret_cast<float4*>(sl + l * STG_LINK_STRIDE + 20 * j);
+        if (P == 16) {
+          float4* q = reinterpret_cast<float4*>(sl + l * LSTRIDE + 36 * j);
 #pragma unroll
-        for (int e = 0; e < 4; e++)
-          q[e] = make_float4(float(u[2 * e].re), float(u[2 * e].im), float(u[2 * e + 1].re), float(u[2 * e + 1].im));
-        *reinterpret_cast<float2*>(q + 4) = make_float2(float(u[8].re), float(u[8].im));
+          for (int e = 0; e < 9; e++)
+            q[e] = make_float4(float(u[e].re), float(u[e].re), float(u[e].im), float(u[e].im));
+        } else {
+          float4* q = reinterpret_cast<float4*>(sl + l * LSTRIDE + 20 * j);
+#pragma unroll
+          for (int e = 0; e < 4; e++)
+            q[e] = make_float4(float(u[2 * e].re), float(u[2 * e].im), float(u[2 * e + 1].re), float(u[2 * e + 1].im));
+          *reinterpret_cast<float2*>(q + 4) = make_float2(float(u[8].re), float(u[8].im));
+        }
       }
     }
     if (SCL) {
@@ -1139,7 +1190,10 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
     double nrm = 0.0;
     if (valid) {
       cx<R> acc[12];
-      {
+      if constexpr (P == 16) {
+        hops_fp16_sp<RECON, STAGED>(A, s, r, reinterpret_cast<const float4*>(sl + lane * LSTRIDE),
+                                    reinterpret_cast<cx<float>*>(acc));
+      } else {
         DirLinks<R> L;
         auto links = [&](auto mu_c) {
           constexpr int MU = decltype(mu_c)::value;
@@ -1254,9 +1308,12 @@ __global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
   dslash_site_body<P, RECON, EPI, STAGED>(A);
 }
 
-// FP16: held to 102 registers, 5 blocks per SM (the compiler's own choice of 124-128 leaves 4)
+// FP16: held to 96 registers, 5 blocks per SM (the compiler's own choice of 124-128 leaves 4);
+// staged, the 47 KB of shared memory (links as broadcast pairs, clover pair) leave room for 4 blocks
+// of up to 128 registers (5 blocks of 96 registers with the clover read through L1 instead: 32^3 x
+// 64, 8 RHS 631 -> 658 us)
 template <int RECON, int EPI, bool STAGED>
-__global__ void __launch_bounds__(128, 5) dslash_site_fp16_kernel(DslashArgs A) {
+__global__ void __launch_bounds__(128, STAGED ? 4 : 5) dslash_site_fp16_kernel(DslashArgs A) {
   dslash_site_body<16, RECON, EPI, STAGED>(A);
 }
 
