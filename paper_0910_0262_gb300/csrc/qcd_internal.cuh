@@ -719,10 +719,20 @@ __device__ __forceinline__ void grid_finish(int nrhs, long long blk_total, int n
   if (!is_last) return;
   __threadfence();
   for (int r = 0; r < nrhs; r++) {
+    // thread t adds partials t, t + BLOCK, t + 2 BLOCK, ... in that order; the loads of U terms are
+    // issued together (a grid of 32768 blocks leaves 256 partials per thread of a 128-thread block)
+    constexpr int U = 16;
     double s = 0.0;
-    for (int j = threadIdx.x; j < nblk; j += BLOCK) {
-      const long long slot = (long long)r * nblk + j;
-      if (slot < ra.capacity) s += __ldcg(ra.partials + slot);
+    for (int j0 = threadIdx.x; j0 < nblk; j0 += U * BLOCK) {
+      double v[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int j = j0 + u * BLOCK;
+        const long long slot = (long long)r * nblk + j;
+        v[u] = (j < nblk && slot < ra.capacity) ? __ldcg(ra.partials + slot) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < U; u++) s += v[u];
     }
     for (int off = 16; off >= 1; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     __syncthreads();
