@@ -1092,6 +1092,45 @@ __device__ __forceinline__ void hops_fp16_sp(const DslashArgs& A, const Site& s,
   using I3 = std::integral_constant<int, 3>;
   using BT = std::true_type;
   using BF = std::false_type;
+  if constexpr (!STAGED) {
+    // links and neighbours of two directions in flight: those of mu + 1 are fetched before the
+    // arithmetic of mu (32^3 x 64, 1 RHS: 107 -> 103 us at 4 blocks of 128 registers per SM; at 5
+    // blocks of 96 registers 105 us, without the prefetch 107 us)
+    using GIO = GaugeIO<16, RECON>;
+    struct DirRaw {
+      SpinorIO<16>::Raw qf, qb;
+      typename GIO::Raw lf, lb;
+    };
+    DirLinks<float> L[4];
+    auto fetch = [&](auto mu_c, DirRaw& d) {
+      constexpr int MU = decltype(mu_c)::value;
+      dir_index<MU>(A.g, s, L[MU]);
+      load_nb_sp(A.in, A.in_norm, Vh, r, L[MU].nbf, d.qf);
+      load_nb_sp(A.in, A.in_norm, Vh, r, L[MU].nbb, d.qb);
+      GIO::load_raw(A.gauge, Vh, A.p, MU, s.i >> 1, d.lf);
+      GIO::load_raw(A.gauge, Vh, 1 - A.p, MU, L[MU].nbb, d.lb);
+    };
+    auto compute = [&](auto mu_c, auto f01_c, auto f23_c, const DirRaw& d) {
+      constexpr int MU = decltype(mu_c)::value;
+      constexpr bool F01 = decltype(f01_c)::value, F23 = decltype(f23_c)::value;
+      cx<float> u[9];
+      GIO::decode(d.lf, u);
+      hop_sp<MU, -1, F01, F23>(d.qf, RegLinkSp{u}, L[MU].sf, SG, M1, sa);
+      GIO::decode(d.lb, u);
+      hop_sp<MU, +1, false, false>(d.qb, RegLinkSp{u}, L[MU].sb, SG, M1, sa);
+    };
+    DirRaw d0, d1;
+    fetch(I0(), d0);
+    fetch(I1(), d1);
+    compute(I0(), BT(), BF(), d0);
+    fetch(I2(), d0);
+    compute(I1(), BF(), BF(), d1);
+    fetch(I3(), d1);
+    compute(I2(), BF(), BT(), d0);
+    compute(I3(), BF(), BF(), d1);
+    sp_unpack(sa, acc);
+    return;
+  }
   dir(I0(), BT(), BF());
   dir(I1(), BF(), BF());
   dir(I2(), BF(), BT());
@@ -1303,17 +1342,21 @@ __device__ __forceinline__ void dslash_site_body(const DslashArgs& A) {
   if (reduce) grid_finish<128>(A.nrhs, gridDim.x, gridDim.x * G, A.red);
 }
 
+// FP32: 6 blocks per SM (80 registers).  32^3 x 64 against the compiler's own choice (96 registers
+// unstaged, 5 blocks): 1 RHS 159 -> 153.5 us, 4 RHS 418 -> 413 us, 8 RHS 698 -> 688 us; 48^3 x 96,
+// 1 RHS 782 -> 744 us.  7 blocks spill (1 RHS 170 us), 5 staged blocks are slower (8 RHS 715 us).
 template <int P, int RECON, int EPI, bool STAGED>
-__global__ void __launch_bounds__(128) dslash_site_kernel(DslashArgs A) {
+__global__ void __launch_bounds__(128, 6) dslash_site_kernel(DslashArgs A) {
   dslash_site_body<P, RECON, EPI, STAGED>(A);
 }
 
-// FP16: held to 96 registers, 5 blocks per SM (the compiler's own choice of 124-128 leaves 4);
-// staged, the 47 KB of shared memory (links as broadcast pairs, clover pair) leave room for 4 blocks
-// of up to 128 registers (5 blocks of 96 registers with the clover read through L1 instead: 32^3 x
-// 64, 8 RHS 631 -> 658 us)
+// FP16: 4 blocks per SM of up to 128 registers.  Unstaged, the registers hold the links and
+// neighbours of two directions at once (5 blocks of 96 registers: 105 us against 103 us at 32^3 x 64,
+// 1 RHS; 6 of 80: 108 us); staged, the 47 KB of shared memory (links as broadcast pairs, clover pair)
+// allow 4 blocks (5 blocks of 96 registers with the clover read through L1 instead: 32^3 x 64, 8 RHS
+// 631 -> 658 us)
 template <int RECON, int EPI, bool STAGED>
-__global__ void __launch_bounds__(128, STAGED ? 4 : 5) dslash_site_fp16_kernel(DslashArgs A) {
+__global__ void __launch_bounds__(128, 4) dslash_site_fp16_kernel(DslashArgs A) {
   dslash_site_body<16, RECON, EPI, STAGED>(A);
 }
 

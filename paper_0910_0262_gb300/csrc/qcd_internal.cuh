@@ -419,32 +419,57 @@ struct GaugeIO<32, 12> {
   }
 };
 
+// FP16 links: load_raw fetches the stored halves (so that loads can be issued ahead of their use),
+// decode converts them (and reconstructs row 2 of 12-real storage)
 template <>
 struct GaugeIO<16, 18> {
   static constexpr int NVEC = 9;
-  __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+  struct Raw {
+    uint32_t v[9];
+  };
+  __device__ static void load_raw(const void* g, int Vh, int p, int mu, int h, Raw& w) {
     const uint32_t* q = static_cast<const uint32_t*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
 #pragma unroll
+    for (int k = 0; k < 9; k++) w.v[k] = __ldg(q + (size_t)k * Vh);
+  }
+  __device__ static void decode(const Raw& w, cx<float> u[9]) {
+#pragma unroll
     for (int k = 0; k < 9; k++) {
-      float2 v = h2f(__ldg(q + (size_t)k * Vh));
+      float2 v = h2f(w.v[k]);
       u[k] = cmk(v.x, v.y);
     }
+  }
+  __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+    Raw w;
+    load_raw(g, Vh, p, mu, h, w);
+    decode(w, u);
   }
 };
 
 template <>
 struct GaugeIO<16, 12> {
   static constexpr int NVEC = 3;
-  __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+  struct Raw {
+    uint2 v[3];
+  };
+  __device__ static void load_raw(const void* g, int Vh, int p, int mu, int h, Raw& w) {
     const uint2* q = static_cast<const uint2*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
 #pragma unroll
+    for (int k = 0; k < 3; k++) w.v[k] = __ldg(q + (size_t)k * Vh);
+  }
+  __device__ static void decode(const Raw& w, cx<float> u[9]) {
+#pragma unroll
     for (int k = 0; k < 3; k++) {
-      uint2 v = __ldg(q + (size_t)k * Vh);
-      float2 a = h2f(v.x), b = h2f(v.y);
+      float2 a = h2f(w.v[k].x), b = h2f(w.v[k].y);
       u[2 * k] = cmk(a.x, a.y);
       u[2 * k + 1] = cmk(b.x, b.y);
     }
     reconstruct_row2(u);
+  }
+  __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+    Raw w;
+    load_raw(g, Vh, p, mu, h, w);
+    decode(w, u);
   }
 };
 
