@@ -3,8 +3,8 @@
 // On small lattices the inner CG iteration is bound by kernel launch latency and ramp-up, not by
 // memory bandwidth: its five launches (four hopping passes, the p update) each touch a working set
 // that fits in L2.  This cooperative kernel keeps every block resident and runs the iteration's
-// five phases back to back, separated by grid barriers, until a reliable-update or convergence
-// trigger (or an iteration cap) -- the same arithmetic, in the same order, as the graph of launches.
+// phases back to back, separated by grid barriers, until a reliable-update or convergence trigger (or
+// an iteration cap) -- the same arithmetic as the graph of launches.
 // At a reliable-update trigger it raises the update's gate (ctl->rel_go), so that the update's
 // launches, enqueued behind it before the trigger is known, run; a launch that finds the RHS
 // converged or halted returns at once.
@@ -15,8 +15,11 @@
 //   phase 4  Ap = g5 (A_ee g5 y - kappa^2 D_eo t), x += alpha p, r -= alpha Ap, |r|^2 -> beta
 //   phase 5  p  = r + beta p
 //
-// Sums are formed per block over a fixed set of site blocks and then, after the barrier, added in
-// block order by every block, so all blocks hold the same alpha and beta.  Fields written inside
+// FP32 forms phase 5 where phases 1 and 2 of the next iteration read p (p = r + beta p from the
+// previous iteration's r, p and beta), so its iteration has four phases; phase 5 runs as a phase only
+// when a launch stops at its iteration cap.  Sums are formed per block over a fixed set of site blocks;
+// the barrier that closes a sum has the last-arriving block add the per-block partials in block order
+// and publish the total, so all blocks hold the same alpha and beta.  Fields written inside
 // the kernel are read with ordinary loads after the barrier.  Every barrier wait is bounded: a
 // block that has waited too long sets an error word and all blocks return (the host reports
 // QCD_ERR_TIMEOUT).
