@@ -304,6 +304,29 @@ qcd_status qcd_mhat_static(qcd_ctx* ctx, double* out, const double* in, int dagg
 qcd_status qcd_selftest_barrier_timeout(qcd_ctx* ctx);
 
 /*
+ * Index checks of the debug build.  libqcd_debug.so (built with QCD_DEBUG=1 by
+ * `python -m paper_0910_0262_gb300.build --debug`) checks, in every kernel, the indices handed to the
+ * field accessors: the site (0 <= h < V/2, a face index against its face), the RHS (>= 0), the link's
+ * parity and direction, the clover block.  A failed check records a bit in a device word of the
+ * kernel's translation unit and skips the access (a load returns zeros, a store writes nothing), so
+ * an indexing fault is reported instead of reading or writing out of range.
+ * qcd_debug_violations: *violations = the OR of the bits recorded since the previous call
+ * (QCD_DBG_SPINOR, QCD_DBG_LINK, QCD_DBG_CLOVER, QCD_DBG_HALO; ~0u if a word could not be read),
+ * which it clears; *is_debug (may be null) = 1 in the debug build, 0 in the release build, whose
+ * checks are compiled away (*violations is then 0).  Synchronises the context's stream.
+ * qcd_selftest_debug_index: launches one thread that loads the FP64 spinor at site index V/2 (one
+ * past the last site) from a scratch buffer of 13 V/2 complex doubles it allocates and frees, so
+ * that the load stays inside the buffer even where it is not checked; the debug build records
+ * QCD_DBG_SPINOR for it.  Synchronises the context's stream.
+ */
+#define QCD_DBG_SPINOR 1u
+#define QCD_DBG_LINK 2u
+#define QCD_DBG_CLOVER 4u
+#define QCD_DBG_HALO 8u
+qcd_status qcd_debug_violations(qcd_ctx* ctx, unsigned* violations, int* is_debug);
+qcd_status qcd_selftest_debug_index(qcd_ctx* ctx);
+
+/*
  * Host-only self-test of the multiply-and-shift division by a lattice extent that the kernels use
  * to turn a site index into coordinates (the same expression, evaluated on the host): checks every
  * even extent 2..1024 against integer division on the numerators 0..65535, near each multiple of

@@ -7,6 +7,7 @@ changed.
 
     python -m paper_0910_0262_gb300.build          # build if needed
     python -m paper_0910_0262_gb300.build --force  # rebuild
+    python -m paper_0910_0262_gb300.build --debug  # libqcd_debug.so: index checks in every kernel
 """
 
 import hashlib
@@ -21,6 +22,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqcd.so")
+# the debug build (index checks in every field accessor, reported by qcd_debug_violations)
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libqcd_debug.so")
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -33,7 +37,7 @@ def sources():
     return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stamp():
+def _stamp(extra=()):
     h = hashlib.sha256()
     for d, names in ((CSRC, sorted(os.listdir(CSRC))), (INCLUDE, sorted(os.listdir(INCLUDE)))):
         for n in names:
@@ -42,7 +46,7 @@ def _stamp():
                 h.update(n.encode())
                 with open(p, "rb") as f:
                     h.update(f.read())
-    h.update(" ".join(FLAGS + LINK).encode())
+    h.update(" ".join(FLAGS + list(extra) + LINK).encode())
     h.update(os.uname().machine.encode())
     return h.hexdigest()
 
@@ -52,21 +56,25 @@ def _run(cmd):
     return r.returncode, r.stdout
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    """Compile every .cu under csrc/ and link libqcd.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp_file = os.path.join(BUILD, "stamp")
-    stamp = _stamp()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp_file):
+def build(force=False, verbose=False, extra_flags=(), debug=False):
+    """Compile every .cu under csrc/ and link libqcd.so (debug: libqcd_debug.so, with QCD_DEBUG=1);
+    returns the library path."""
+    build_dir = BUILD_DEBUG if debug else BUILD
+    lib_path = LIB_DEBUG if debug else LIB
+    extra = list(extra_flags) + (["-DQCD_DEBUG=1"] if debug else [])
+    os.makedirs(build_dir, exist_ok=True)
+    stamp_file = os.path.join(build_dir, "stamp")
+    stamp = _stamp(extra)
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp_file):
         with open(stamp_file) as f:
             if f.read().strip() == stamp:
-                return LIB
+                return lib_path
     objs = []
     cmds = []
     for src in sources():
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmds.append([NVCC] + FLAGS + list(extra_flags) + ["-c", os.path.join(CSRC, src), "-o", obj])
+        cmds.append([NVCC] + FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", obj])
     with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 4)) as ex:
         results = list(ex.map(_run, cmds))
     for cmd, (rc, out) in zip(cmds, results):
@@ -74,16 +82,16 @@ def build(force=False, verbose=False, extra_flags=()):
             sys.stderr.write(" ".join(cmd) + "\n" + out)
         if rc:
             raise RuntimeError("nvcc failed for " + cmd[-3])
-    tmp = LIB + ".tmp"
+    tmp = lib_path + ".tmp"
     rc, out = _run([NVCC] + LINK + objs + ["-o", tmp])
     if rc:
         sys.stderr.write(out)
-        raise RuntimeError("link of libqcd.so failed")
-    os.replace(tmp, LIB)
+        raise RuntimeError("link of " + os.path.basename(lib_path) + " failed")
+    os.replace(tmp, lib_path)
     with open(stamp_file, "w") as f:
         f.write(stamp)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -1427,6 +1427,43 @@ qcd_status qcd_selftest_barrier_timeout(qcd_ctx* c) {
   return QCD_OK;
 }
 
+static_assert(QCD_DBG_SPINOR == DBG_SPINOR && QCD_DBG_LINK == DBG_LINK && QCD_DBG_CLOVER == DBG_CLOVER &&
+                  QCD_DBG_HALO == DBG_HALO,
+              "debug bits of the header and the kernels");
+
+qcd_status qcd_debug_violations(qcd_ctx* c, unsigned* violations, int* is_debug) {
+  QCD_API_ENTER("qcd_debug_violations", c);
+  qcd_status s = QCD_OK;
+  if (!violations) return fail(QCD_ERR_ARG, "null pointer");
+  if ((s = sync_and_check(c, "debug_violations"))) return s;
+  *violations = debug_take_blas() | debug_take_cg_persistent() | debug_take_clover() | debug_take_dslash() |
+                debug_take_force() | debug_take_halo() | debug_take_layout() | debug_take_md() |
+                debug_take_probe();
+  if (is_debug) *is_debug = QCD_DEBUG;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(QCD_ERR_CUDA, "debug_violations: %s", cudaGetErrorString(e));
+  return QCD_OK;
+}
+
+qcd_status qcd_selftest_debug_index(qcd_ctx* c) {
+  QCD_API_ENTER("qcd_selftest_debug_index", c);
+  qcd_status s = QCD_OK;
+  double2* buf = nullptr;
+  double* out = nullptr;
+  const size_t n = (size_t)13 * c->g.Vh;
+  if (cudaMalloc(&buf, n * sizeof(double2)) != cudaSuccess || cudaMalloc(&out, sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(buf);
+    return fail(QCD_ERR_NOMEM, "debug index self-test: allocation failed");
+  }
+  cudaError_t e = cudaMemsetAsync(buf, 0, n * sizeof(double2), c->st);
+  if (e == cudaSuccess) launch_debug_index_probe(c->g, buf, out, c->st);
+  s = e == cudaSuccess ? sync_and_check(c, "debug index self-test") : fail(QCD_ERR_CUDA, "%s", cudaGetErrorString(e));
+  cudaFree(buf);
+  cudaFree(out);
+  return s;
+}
+
 qcd_status qcd_clover_logdet(qcd_ctx* c, double out[2]) {
   QCD_API_ENTER("qcd_clover_logdet", c);
   qcd_status s = QCD_OK;

@@ -9,6 +9,8 @@
 
 namespace qcd {
 
+QCD_DEBUG_TAKE(debug_take_blas)
+
 namespace {
 
 constexpr int BB = 256;  // block size of the BLAS kernels
@@ -81,6 +83,15 @@ __global__ void __launch_bounds__(BB) true_residual_kernel(Geom g, int nrhs, con
   }
   block_partial<BB>(v, k, blockIdx.x, gridDim.x, red);
   grid_finish<BB>(nrhs, (long long)gridDim.x * gridDim.y, gridDim.x, red);
+}
+
+__global__ void debug_index_probe_kernel(Geom g, const double2* buf, double* out) {
+  cx<double> s[12];
+  SpinorIO<64>::load(buf, nullptr, g.Vh, 0, g.Vh, s);
+  double t = 0.0;
+#pragma unroll
+  for (int c = 0; c < 12; c++) t += s[c].re + s[c].im;
+  *out = t;
 }
 
 __global__ void __launch_bounds__(BB) norm2_kernel(Geom g, int nrhs, const double2* a, ReduceArgs red) {
@@ -199,6 +210,11 @@ void launch_accumulate_x(int prec_r, const Geom& g, int nrhs, double2* x_hi, voi
   g_kernel_launches += 1;
   if (prec_r == 64) accumulate_x_kernel<64><<<grid2(g, nrhs), BB, 0, st>>>(g, x_hi, x_lo, x_lon, gate);
   else accumulate_x_kernel<32><<<grid2(g, nrhs), BB, 0, st>>>(g, x_hi, x_lo, x_lon, gate);
+}
+
+void launch_debug_index_probe(const Geom& g, const double2* buf, double* out, cudaStream_t st) {
+  g_kernel_launches += 1;
+  debug_index_probe_kernel<<<1, 1, 0, st>>>(g, buf, out);
 }
 
 void launch_true_residual(int prec_r, const Geom& g, int nrhs, const double2* b, const double2* Ap, void* r_lo,

@@ -30,6 +30,8 @@
 
 namespace qcd {
 
+QCD_DEBUG_TAKE(debug_take_cg_persistent)
+
 namespace {
 
 constexpr unsigned BARRIER_SPIN_LIMIT = 1u << 22;  // polls of an L2 word: about a second or more

@@ -16,6 +16,8 @@
 
 namespace qcd {
 
+QCD_DEBUG_TAKE(debug_take_clover)
+
 namespace {
 
 // traceless part of (Q - Q^dag) / (8 i), with Q = L1 + L2 + L3 + L4 the four-leaf sum in the

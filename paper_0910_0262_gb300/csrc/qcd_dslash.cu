@@ -5,6 +5,8 @@
 
 namespace qcd {
 
+QCD_DEBUG_TAKE(debug_take_dslash)
+
 namespace {
 
 template <int P, int RECON>

@@ -70,6 +70,10 @@ struct HaloIO {
   static constexpr int BYTES = P == 64 ? 96 : 48;  // per face site and RHS
   template <typename R>
   __device__ static void load(const void* base, int F, int r, int f, cx<R> h[6]) {
+    if (!dbg_check(f >= 0 && f < F && r >= 0, DBG_HALO)) {
+      for (int k = 0; k < 6; k++) h[k] = {};
+      return;
+    }
     if (P == 64) {
       const double2* q = static_cast<const double2*>(base) + (size_t)r * 6 * F + f;
 #pragma unroll
@@ -89,6 +93,7 @@ struct HaloIO {
   }
   template <typename R>
   __device__ static void store(void* base, int F, int r, int f, const cx<R> h[6]) {
+    if (!dbg_check(f >= 0 && f < F && r >= 0, DBG_HALO)) return;
     if (P == 64) {
       double2* q = static_cast<double2*>(base) + (size_t)r * 6 * F + f;
 #pragma unroll

@@ -33,6 +33,8 @@
 
 namespace qcd {
 
+QCD_DEBUG_TAKE(debug_take_force)
+
 namespace {
 
 constexpr int FB = 128;

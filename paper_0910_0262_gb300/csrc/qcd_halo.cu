@@ -12,6 +12,8 @@
 
 namespace qcd {
 
+QCD_DEBUG_TAKE(debug_take_halo)
+
 namespace {
 
 template <int P, int RECON>

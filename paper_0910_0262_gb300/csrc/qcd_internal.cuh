@@ -151,6 +151,51 @@ __device__ __forceinline__ int neighbor_bwd(const Geom& g, const Site& s, int mu
   }
 }
 
+// ------------------------------------------------------------ debug checks ----
+// Builds with QCD_DEBUG=1 (libqcd_debug.so) check the indices every field accessor below is given: the
+// site (0 <= h < Vh, or the face index against its face), the RHS (r >= 0), the link's parity and
+// direction and the clover block.  A failed check sets a bit of this translation unit's violation word
+// (DBG_SPINOR, DBG_LINK, DBG_CLOVER, DBG_HALO) and the access is skipped: a load returns zeros, a
+// store writes nothing.  The host collects the words with qcd_debug_violations.  Release builds
+// compile the checks away.
+enum : unsigned { DBG_SPINOR = 1u, DBG_LINK = 2u, DBG_CLOVER = 4u, DBG_HALO = 8u };
+#ifndef QCD_DEBUG
+#define QCD_DEBUG 0
+#endif
+#if QCD_DEBUG
+static __device__ unsigned qcd_dbg_word;
+#endif
+__device__ __forceinline__ bool dbg_check(bool ok, unsigned bit) {
+#if QCD_DEBUG
+  if (!ok) atomicOr(&qcd_dbg_word, bit);
+  return ok;
+#else
+  (void)bit;
+  return true;
+#endif
+}
+__device__ __forceinline__ bool dbg_spinor(int Vh, int r, int h) { return dbg_check(h >= 0 && h < Vh && r >= 0, DBG_SPINOR); }
+__device__ __forceinline__ bool dbg_link(int Vh, int p, int mu, int h) {
+  return dbg_check(h >= 0 && h < Vh && (p == 0 || p == 1) && mu >= 0 && mu < 4, DBG_LINK);
+}
+__device__ __forceinline__ bool dbg_clover(int Vh, int h, int b) {
+  return dbg_check(h >= 0 && h < Vh && (b == 0 || b == 1), DBG_CLOVER);
+}
+// A host function `unsigned name()` that returns and clears this translation unit's violation word
+// (0 in release builds); every translation unit with kernels defines one.
+#if QCD_DEBUG
+#define QCD_DEBUG_TAKE(name)                                                         \
+  unsigned name() {                                                                  \
+    unsigned v = 0, z = 0;                                                           \
+    if (cudaMemcpyFromSymbol(&v, qcd_dbg_word, sizeof v) != cudaSuccess) v = ~0u;    \
+    cudaMemcpyToSymbol(qcd_dbg_word, &z, sizeof z);                                  \
+    return v;                                                                        \
+  }
+#else
+#define QCD_DEBUG_TAKE(name) \
+  unsigned name() { return 0; }
+#endif
+
 // ------------------------------------------------------------ precision ----
 template <int P>
 struct Real;
@@ -190,6 +235,10 @@ struct SpinorIO<64> {
   static constexpr int NVEC = 12;  // double2 per site
   template <int LD = LD_NC>
   __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<double> s[12]) {
+    if (!dbg_spinor(Vh, r, h)) {
+      for (int c = 0; c < 12; c++) s[c] = {};
+      return;
+    }
     const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 12; c++) {
@@ -198,6 +247,7 @@ struct SpinorIO<64> {
     }
   }
   __device__ static void store(void* base, float*, int Vh, int r, int h, const cx<double> s[12]) {
+    if (!dbg_spinor(Vh, r, h)) return;
     double2* p = static_cast<double2*>(base);
 #pragma unroll
     for (int c = 0; c < 12; c++) p[sidx<NVEC>(c, Vh, r, h)] = make_double2(s[c].re, s[c].im);
@@ -206,6 +256,10 @@ struct SpinorIO<64> {
   template <int LD = LD_NC>
   __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b,
                                     cx<double> s[6]) {
+    if (!dbg_spinor(Vh, r, h)) {
+      for (int c = 0; c < 6; c++) s[c] = {};
+      return;
+    }
     const double2* p = static_cast<const double2*>(base);
 #pragma unroll
     for (int c = 0; c < 6; c++) {
@@ -215,6 +269,7 @@ struct SpinorIO<64> {
   }
   __device__ static void store_block(void* base, float*, int Vh, int r, int h, int b,
                                      const cx<double> s[6]) {
+    if (!dbg_spinor(Vh, r, h)) return;
     double2* p = static_cast<double2*>(base);
 #pragma unroll
     for (int c = 0; c < 6; c++) p[sidx<NVEC>(6 * b + c, Vh, r, h)] = make_double2(s[c].re, s[c].im);
@@ -226,6 +281,10 @@ struct SpinorIO<32> {
   static constexpr int NVEC = 6;  // float4 per site
   template <int LD = LD_NC>
   __device__ static void load(const void* base, const float*, int Vh, int r, int h, cx<float> s[12]) {
+    if (!dbg_spinor(Vh, r, h)) {
+      for (int c = 0; c < 12; c++) s[c] = {};
+      return;
+    }
     const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 6; k++) {
@@ -235,6 +294,7 @@ struct SpinorIO<32> {
     }
   }
   __device__ static void store(void* base, float*, int Vh, int r, int h, const cx<float> s[12]) {
+    if (!dbg_spinor(Vh, r, h)) return;
     float4* p = static_cast<float4*>(base);
 #pragma unroll
     for (int k = 0; k < 6; k++)
@@ -243,6 +303,10 @@ struct SpinorIO<32> {
   template <int LD = LD_NC>
   __device__ static void load_block(const void* base, const float*, int Vh, int r, int h, int b,
                                     cx<float> s[6]) {
+    if (!dbg_spinor(Vh, r, h)) {
+      for (int c = 0; c < 6; c++) s[c] = {};
+      return;
+    }
     const float4* p = static_cast<const float4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -253,6 +317,7 @@ struct SpinorIO<32> {
   }
   __device__ static void store_block(void* base, float*, int Vh, int r, int h, int b,
                                      const cx<float> s[6]) {
+    if (!dbg_spinor(Vh, r, h)) return;
     float4* p = static_cast<float4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++)
@@ -277,6 +342,10 @@ struct SpinorIO<16> {
   static constexpr int NVEC = 3;  // uint4 per site
   template <int LD = LD_NC>
   __device__ static void load(const void* base, const float* nrm, int Vh, int r, int h, cx<float> s[12]) {
+    if (!dbg_spinor(Vh, r, h)) {
+      for (int c = 0; c < 12; c++) s[c] = {};
+      return;
+    }
     const uint4* p = static_cast<const uint4*>(base);
     const float n = ldv<LD>(nrm + (size_t)r * Vh + h);
 #pragma unroll
@@ -297,6 +366,10 @@ struct SpinorIO<16> {
   };
   template <int LD = LD_NC>
   __device__ static void load_raw(const void* base, const float* nrm, int Vh, int r, int h, Raw& q) {
+    if (!dbg_spinor(Vh, r, h)) {
+      q = {};
+      return;
+    }
     const uint4* p = static_cast<const uint4*>(base);
 #pragma unroll
     for (int k = 0; k < 3; k++) q.v[k] = ldv<LD>(p + sidx<NVEC>(k, Vh, r, h));
@@ -321,6 +394,7 @@ struct SpinorIO<16> {
     return unpack_unscaled(q, s);
   }
   __device__ static void store(void* base, float* nrm, int Vh, int r, int h, const cx<float> s[12]) {
+    if (!dbg_spinor(Vh, r, h)) return;
     float m = 0.f;
 #pragma unroll
     for (int c = 0; c < 12; c++) m = fmaxf(m, fmaxf(fabsf(s[c].re), fabsf(s[c].im)));
@@ -341,6 +415,10 @@ struct SpinorIO<16> {
   template <int LD = LD_NC>
   __device__ static void load_block(const void* base, const float* nrm, int Vh, int r, int h, int b,
                                     cx<float> s[6]) {
+    if (!dbg_spinor(Vh, r, h)) {
+      for (int c = 0; c < 6; c++) s[c] = {};
+      return;
+    }
     const uint4* p = static_cast<const uint4*>(base);
     const float n = ldv<LD>(nrm + (size_t)r * Vh + h);
     const uint4 mid = ldv<LD>(p + sidx<NVEC>(1, Vh, r, h));
@@ -382,6 +460,10 @@ template <>
 struct GaugeIO<64, 18> {
   static constexpr int NVEC = 9;
   __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<double> u[9]) {
+    if (!dbg_link(Vh, p, mu, h)) {
+      for (int k = 0; k < 9; k++) u[k] = {};
+      return;
+    }
     const double2* q = static_cast<const double2*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
 #pragma unroll
     for (int k = 0; k < 9; k++) {
@@ -395,6 +477,10 @@ template <>
 struct GaugeIO<32, 18> {
   static constexpr int NVEC = 9;
   __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+    if (!dbg_link(Vh, p, mu, h)) {
+      for (int k = 0; k < 9; k++) u[k] = {};
+      return;
+    }
     const float2* q = static_cast<const float2*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
 #pragma unroll
     for (int k = 0; k < 9; k++) {
@@ -408,6 +494,10 @@ template <>
 struct GaugeIO<32, 12> {
   static constexpr int NVEC = 3;
   __device__ static void load(const void* g, int Vh, int p, int mu, int h, cx<float> u[9]) {
+    if (!dbg_link(Vh, p, mu, h)) {
+      for (int k = 0; k < 9; k++) u[k] = {};
+      return;
+    }
     const float4* q = static_cast<const float4*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -428,6 +518,10 @@ struct GaugeIO<16, 18> {
     uint32_t v[9];
   };
   __device__ static void load_raw(const void* g, int Vh, int p, int mu, int h, Raw& w) {
+    if (!dbg_link(Vh, p, mu, h)) {
+      w = {};
+      return;
+    }
     const uint32_t* q = static_cast<const uint32_t*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
 #pragma unroll
     for (int k = 0; k < 9; k++) w.v[k] = __ldg(q + (size_t)k * Vh);
@@ -453,6 +547,10 @@ struct GaugeIO<16, 12> {
     uint2 v[3];
   };
   __device__ static void load_raw(const void* g, int Vh, int p, int mu, int h, Raw& w) {
+    if (!dbg_link(Vh, p, mu, h)) {
+      w = {};
+      return;
+    }
     const uint2* q = static_cast<const uint2*>(g) + (size_t)(p * 4 + mu) * NVEC * Vh + h;
 #pragma unroll
     for (int k = 0; k < 3; k++) w.v[k] = __ldg(q + (size_t)k * Vh);
@@ -499,6 +597,10 @@ struct CloverIO<64> {
   static constexpr int NVEC = 36;  // double2 per site
   template <int LD = LD_NC>
   __device__ static void apply(const void* c, int Vh, int h, int b, const cx<double> x[6], cx<double> y[6]) {
+    if (!dbg_clover(Vh, h, b)) {
+      for (int k = 0; k < 6; k++) y[k] = {};
+      return;
+    }
     const double2* q = static_cast<const double2*>(c) + (size_t)(b * 18) * Vh + h;
     double d[6];
     cx<double> L[15];
@@ -522,6 +624,10 @@ struct CloverIO<32> {
   static constexpr int NVEC = 18;  // float4 per site
   template <int LD = LD_NC>
   __device__ static void apply(const void* c, int Vh, int h, int b, const cx<float> x[6], cx<float> y[6]) {
+    if (!dbg_clover(Vh, h, b)) {
+      for (int k = 0; k < 6; k++) y[k] = {};
+      return;
+    }
     const float4* q = static_cast<const float4*>(c) + (size_t)(b * 9) * Vh + h;
     float f[36];
 #pragma unroll
@@ -550,6 +656,10 @@ struct CloverIO<16> {
   // row of c holding uint4 4B (4B for a whole field; 0 for a copy of the block's five rows alone)
   template <int B, int LD = LD_NC, int ROW0 = 4 * B>
   __device__ static void apply_block(const void* c, int Vh, int h, const cx<float> x[6], cx<float> y[6]) {
+    if (!dbg_clover(Vh, h, B)) {
+      for (int k = 0; k < 6; k++) y[k] = {};
+      return;
+    }
     const uint4* q = static_cast<const uint4*>(c) + h;
     float f[40];
 #pragma unroll

@@ -56,6 +56,20 @@ void launch_clover_build(const Geom& g, const void* g64, double kappa, double cs
 void launch_clover_apply(int prec, const Geom& g, const void* clover, const void* in, const float* in_norm,
                          void* out, float* out_norm, int nrhs, cudaStream_t st);
 
+// ---- debug builds: each translation unit's index-violation word, returned and cleared (qcd_internal.cuh)
+unsigned debug_take_blas();
+unsigned debug_take_cg_persistent();
+unsigned debug_take_clover();
+unsigned debug_take_dslash();
+unsigned debug_take_force();
+unsigned debug_take_halo();
+unsigned debug_take_layout();
+unsigned debug_take_md();
+unsigned debug_take_probe();
+// one thread loads the FP64 spinor at site index Vh (one past the last site) of buf, which holds
+// 13 Vh double2, so that the load stays inside buf even unchecked; debug builds record DBG_SPINOR
+void launch_debug_index_probe(const Geom& g, const double2* buf, double* out, cudaStream_t st);
+
 // ---- hopping term (qcd_dslash.cu)
 struct DslashArgs;
 void launch_dslash(int prec, int recon, int epi, const DslashArgs& a, cudaStream_t st);

@@ -9,6 +9,8 @@
 
 namespace qcd {
 
+QCD_DEBUG_TAKE(debug_take_layout)
+
 long long g_kernel_launches = 0;
 
 namespace {

@@ -15,6 +15,8 @@
 
 namespace qcd {
 
+QCD_DEBUG_TAKE(debug_take_md)
+
 namespace {
 
 constexpr int MB = 128;

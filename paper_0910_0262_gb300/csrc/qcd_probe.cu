@@ -9,6 +9,8 @@
 #include "qcd_kernels.h"
 
 namespace qcd {
+
+QCD_DEBUG_TAKE(debug_take_probe)
 namespace {
 
 constexpr int FMA_CHAINS = 8;      // independent dependency chains per thread

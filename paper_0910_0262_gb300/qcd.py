@@ -17,7 +17,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libqcd.so")
+# the library the binding loads: the in-tree build, or the file named by QCD_LIB (for example the
+# debug build, libqcd_debug.so)
+LIB_PATH = os.environ.get("QCD_LIB") or os.path.join(_HERE, "libqcd.so")
 
 QCD_OK = 0
 STATUS = {0: "QCD_OK", 1: "QCD_ERR_ARG", 2: "QCD_ERR_CUDA", 3: "QCD_ERR_NOMEM", 4: "QCD_ERR_STATE",
@@ -107,6 +109,8 @@ _SIGNATURES = {
                                        ctypes.POINTER(SlabComm)]),
     "qcd_slab_cg_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, ctypes.POINTER(SolverParams),
                                          ctypes.POINTER(SolverStats), ctypes.POINTER(SlabComm)]),
+    "qcd_debug_violations": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int)]),
+    "qcd_selftest_debug_index": (ctypes.c_int, [_P]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -249,6 +253,20 @@ def qcd_mhat_static(ctx, out_ptr, in_ptr, dagger=0):
 def qcd_selftest_barrier_timeout(ctx):
     """Returns the status of the barrier self-test (QCD_ERR_TIMEOUT = 8 when the wait gave up)."""
     return lib().qcd_selftest_barrier_timeout(ctx)
+
+
+QCD_DBG_SPINOR, QCD_DBG_LINK, QCD_DBG_CLOVER, QCD_DBG_HALO = 1, 2, 4, 8
+
+
+def qcd_debug_violations(ctx):
+    """(violation bits recorded since the last call, 1 for the debug build else 0); clears the bits."""
+    v, d = ctypes.c_uint(0), ctypes.c_int(0)
+    _check(lib().qcd_debug_violations(ctx, ctypes.byref(v), ctypes.byref(d)))
+    return v.value, d.value
+
+
+def qcd_selftest_debug_index(ctx):
+    _check(lib().qcd_selftest_debug_index(ctx))
 
 
 def qcd_selftest_fastdiv():
