@@ -33,6 +33,21 @@ def test_header_declares_the_boundary():
         assert n in names
 
 
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
+def test_header_compiles_on_its_own(tmp_path, compiler, std):
+    """include/qcd.h is a plain C header: it compiles alone, as C99 and as C++, without warnings."""
+    import shutil
+    import subprocess
+    if shutil.which(compiler) is None:
+        pytest.skip(compiler + " not found")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "qcd.h"\nint main(void) { return qcd_last_error() == 0; }\n')
+    lang = ["-x", "c++"] if compiler == "g++" else []
+    r = subprocess.run([compiler, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I",
+                        os.path.join(ROOT, "include")] + lang + [str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_every_declared_symbol_is_exported(libqcd):
     for n in declared_functions():
         assert hasattr(libqcd, n), n
