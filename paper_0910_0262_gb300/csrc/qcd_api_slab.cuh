@@ -206,8 +206,9 @@ qcd_status slab_cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, con
   // r = b - A x_hi (x_lo = 0, so the reliable update's accumulation adds nothing), p = r
   if ((s = slab_reliable(c, f, nrhs, m))) return s;
   qcd_status result = QCD_OK;
+  bool stale = true;  // the host copy of the state predates the last reliable update
   while (true) {
-    if ((s = read_state(c, nrhs))) return s;
+    if (stale && (s = read_state(c, nrhs))) return s;
     if (c->h_ctl->overflow) return fail(QCD_ERR_CUDA, "reduction buffer too small (internal sizing error)");
     if (c->h_ctl->nan) {
       result = fail(QCD_ERR_NAN, "non-finite value or breakdown in CG");
@@ -241,8 +242,11 @@ qcd_status slab_cg_batch(qcd_ctx* c, double2* x, const double2* b, int nrhs, con
     if (c->h_ctl->halt) {
       // a reliable update (or the convergence check) is due for some RHS: it is made for all
       if ((s = slab_reliable(c, f, nrhs, m))) return s;
+      stale = true;
     } else {
+      // the p update leaves the state read above as it is
       launch_p_update(f.pr, f.pp, g, nrhs, f.r_lo, f.r_lo_n, f.p, f.p_n, c->cg, nullptr, c->st);
+      stale = false;
     }
   }
   launch_accumulate_x(f.pr, g, nrhs, f.x_hi, f.x_lo, f.x_lo_n, c->st);
