@@ -52,6 +52,12 @@ NCU_TRAFFIC = {
     # mean of the clover-inverse (63.3 MB) and xpay (70.2 MB) passes over a step's mix of the two
     "dslash_p64": (66.7e6, "profiles/dslash_pair64_16x16x16x16.md"),
 }
+# FP64 pipe activity (% of active cycles) from the same captures, for the kernels bound by it: the
+# counted flops of a launch leave out that spin projection and reconstruction are additions, each
+# taking an FMA slot of the pipe
+NCU_FP64_PIPE = {
+    "dslash_p64": (84.3, "profiles/dslash_pair64_16x16x16x16.md"),
+}
 
 
 def parse():
@@ -365,6 +371,9 @@ def run_ours(args, world, rank, local):
         result["roofline"] = dict(common, bound="alu", achieved=dk["gflops"] / 1e3, peak=p64, unit="TFLOP/s",
                                   frac=dk["gflops"] / 1e3 / p64,
                                   peak_source="FP64 FMA probe measured in this run (of measured)")
+        if dominant in NCU_FP64_PIPE:
+            result["roofline"]["fp64_pipe_active_pct_ncu"] = NCU_FP64_PIPE[dominant][0]
+            result["roofline"]["fp64_pipe_source"] = NCU_FP64_PIPE[dominant][1]
     if not args.no_md:
         result["clover_det_and_full_solve"] = clover_det_section(op, x, b, stream)
         result["r_algorithm_step"] = r_step_section(op, U, w, stream)
