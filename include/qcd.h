@@ -312,7 +312,8 @@ qcd_status qcd_selftest_barrier_timeout(qcd_ctx* ctx);
  * an indexing fault is reported instead of reading or writing out of range.
  * qcd_debug_violations: *violations = the OR of the bits recorded since the previous call
  * (QCD_DBG_SPINOR, QCD_DBG_LINK, QCD_DBG_CLOVER, QCD_DBG_HALO; ~0u if a word could not be read),
- * which it clears; *is_debug (may be null) = 1 in the debug build, 0 in the release build, whose
+ * which it clears.  The words belong to the process on the context's device, not to the context: the
+ * kernels of every context on that device record into them; *is_debug (may be null) = 1 in the debug build, 0 in the release build, whose
  * checks are compiled away (*violations is then 0).  Synchronises the context's stream.
  * qcd_selftest_debug_index: launches one thread that loads the FP64 spinor at site index V/2 (one
  * past the last site) from a scratch buffer of 13 V/2 complex doubles it allocates and frees, so
