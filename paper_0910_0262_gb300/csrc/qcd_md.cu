@@ -178,8 +178,12 @@ __global__ void __launch_bounds__(MB) flat_redot_kernel(size_t n, int nrhs, cons
 
 // exp(M) for a 3x3 complex M: scaling by 2^-s until the Frobenius norm r is <= 1/4, the Taylor
 // series to the lowest order n with r^(n+1)/(n+1)! <= 1e-17 (at most 12 at r = 1/4; about 8 for the
-// eps |P| of a molecular-dynamics step) in Horner form, then s squarings (Moler and Van Loan,
-// "Nineteen dubious ways to compute the exponential of a matrix", 2003)
+// eps |P| of a molecular-dynamics step), then s squarings (Moler and Van Loan, "Nineteen dubious ways
+// to compute the exponential of a matrix", 2003).  The truncated series is summed in the basis
+// I, M, M^2: by the Cayley-Hamilton theorem M^3 = tr(M) M^2 - c M + det(M) I with
+// c = (tr(M)^2 - tr(M^2)) / 2, so M^k / k! = a_k I + b_k M + c_k M^2 with
+//   (a, b, c)_{k+1} = (c_k det M, a_k - c_k c, b_k + c_k tr M) / (k + 1),
+// the same sum as the matrix series, for one matrix product (M^2) instead of one per term.
 __device__ M3 expm3(M3 m) {
   double nrm = 0.0;
 #pragma unroll
@@ -198,20 +202,30 @@ __device__ M3 expm3(M3 m) {
     t *= nrm / (order + 1);  // r^(order+1) / (order+1)!
     if (t <= 1e-17) break;
   }
-  // E = I + m (I + m/2 (I + m/3 (... (I + m/order))))
+  const M3 m2 = mul(m, m);
+  const C tr1 = m.e[0] + m.e[4] + m.e[8];
+  const C tr2 = m2.e[0] + m2.e[4] + m2.e[8];
+  const C cc = 0.5 * (tr1 * tr1 - tr2);
+  const C det = m.e[0] * (m.e[4] * m.e[8] - m.e[5] * m.e[7]) - m.e[1] * (m.e[3] * m.e[8] - m.e[5] * m.e[6]) +
+                m.e[2] * (m.e[3] * m.e[7] - m.e[4] * m.e[6]);
+  C a = cmk(1.0, 0.0), b = cmk(0.0, 0.0), c = cmk(0.0, 0.0);  // M^k / k! in the basis I, M, M^2
+  C sa = a, sb = b, scm = c;                                    // their sums over k <= order
+  for (int k = 0; k < order; k++) {
+    const double f = 1.0 / (k + 1);
+    const C na = f * (c * det), nb = f * (a - c * cc), nc = f * (b + c * tr1);
+    a = na;
+    b = nb;
+    c = nc;
+    sa = sa + a;
+    sb = sb + b;
+    scm = scm + c;
+  }
   M3 e;
 #pragma unroll
-  for (int k = 0; k < 9; k++) e.e[k] = cmk(0.0, 0.0);
-  e.e[0] = e.e[4] = e.e[8] = cmk(1.0, 0.0);
-  for (int n = order; n >= 1; n--) {
-    M3 t = mul(m, e);
-    const double f = 1.0 / n;
-#pragma unroll
-    for (int k = 0; k < 9; k++) e.e[k] = cmk(f * t.e[k].re, f * t.e[k].im);
-    e.e[0].re += 1.0;
-    e.e[4].re += 1.0;
-    e.e[8].re += 1.0;
-  }
+  for (int k = 0; k < 9; k++) e.e[k] = sb * m.e[k] + scm * m2.e[k];
+  e.e[0] = e.e[0] + sa;
+  e.e[4] = e.e[4] + sa;
+  e.e[8] = e.e[8] + sa;
   for (int k = 0; k < s; k++) e = mul(e, e);
   return e;
 }
