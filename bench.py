@@ -631,49 +631,63 @@ def largest_volume(dev, hbm_peak, do_errors=False):
 
 def slab_section(w, reps=5):
     """The time decomposition on one GPU: the step's lattice cut into two t-slabs, each a context of its
-    own on a stream of its own, driven by a host thread and exchanging halos through device copies
-    (LocalSlabGroup).  Times Mhat^dag Mhat in FP32 (four exchanges) and the mixed FP32 solve to 1e-8
-    against one context, with the halo bytes per exchange.  On one GPU every exchange synchronises both
-    slabs on the host, so this measures the halo path's overhead, not a multi-GPU speed."""
+    own on a stream of its own, driven by a host thread.  The halos and sums go through the library's
+    in-process group (NativeSlabGroup: native callbacks, CUDA events between the slabs' streams, host
+    barriers only to publish them); the same solve through the Python group (LocalSlabGroup: torch
+    copies after host synchronisation) is given beside it.  Times Mhat^dag Mhat in FP32 (four
+    exchanges) and the mixed FP32 solve to 1e-8 against one context, with the halo bytes per exchange.
+    Both slabs share one GPU, so this measures the halo path's cost, not a multi-GPU speed."""
     import torch
     from paper_0910_0262_gb300 import synth, slab
     from paper_0910_0262_gb300 import qcd as Q
     dims = w["dims"]
     U, b = synth.make_problem(dims, w["eps"], w["seed"], 1)
     bounds = [slab.slab_bounds(dims[3], 2, r) for r in range(2)]
-    grp = slab.LocalSlabGroup(2)
-    ops = []
-    for r, (t0, tl) in enumerate(bounds):
-        st = torch.cuda.Stream()
-        op = slab.SlabCloverWilson(dims, t0, tl, grp.member(r), w["t_bc"], stream=st)
-        with torch.cuda.stream(st):
-            op.load_gauge(torch.from_numpy(slab.extended_links(U, t0, tl)).cuda(), recon12=True)
-        op.clover_build(w["kappa"], w["csw"])
-        ops.append(op)
     bd = torch.from_numpy(b).cuda()
     kw = dict(tol=1e-8, inner_prec=32, reliable_every=50, reliable_delta=0.1, max_iter=20000)
 
-    def on_slabs(fn):
-        def job(r):
-            op = ops[r]
-            a, c = slab.slab_rows(dims, op.t_offset, op.t_local)
-            with torch.cuda.stream(op.stream):
-                out = fn(op, bd[:, a:c].contiguous())
-                op.stream.synchronize()
-            return out
-        t0 = time.perf_counter()
-        res = grp.run([lambda r=r: job(r) for r in range(2)])
-        return res, 1e3 * (time.perf_counter() - t0)
+    def measure(grp, with_mdagm):
+        ops = []
+        for r, (t0, tl) in enumerate(bounds):
+            st = torch.cuda.Stream()
+            op = slab.SlabCloverWilson(dims, t0, tl, grp.member(r), w["t_bc"], stream=st)
+            with torch.cuda.stream(st):
+                op.load_gauge(torch.from_numpy(slab.extended_links(U, t0, tl)).cuda(), recon12=True)
+            op.clover_build(w["kappa"], w["csw"])
+            ops.append(op)
 
-    t_mdagm, t_solve, iters = [], [], None
-    for k in range(reps + 1):
-        _, t = on_slabs(lambda op, v: op.dslash(v, Q.QCD_OP_MDAGM, precision=32))
-        res, ts = on_slabs(lambda op, v: op.cg_solve(v, **kw))
-        if k:
-            t_mdagm.append(t)
-            t_solve.append(ts)
-        iters = res[0][1][0]["iters"]
-        ok = all(r[2] for r in res)
+        def on_slabs(fn):
+            def job(r):
+                op = ops[r]
+                a, c = slab.slab_rows(dims, op.t_offset, op.t_local)
+                with torch.cuda.stream(op.stream):
+                    out = fn(op, bd[:, a:c].contiguous())
+                    op.stream.synchronize()
+                return out
+            t0 = time.perf_counter()
+            res = grp.run([lambda r=r: job(r) for r in range(2)])
+            return res, 1e3 * (time.perf_counter() - t0)
+
+        t_mdagm, t_solve, iters, ok = [], [], None, True
+        for k in range(reps + 1):
+            if with_mdagm:
+                _, t = on_slabs(lambda op, v: op.dslash(v, Q.QCD_OP_MDAGM, precision=32))
+                if k:
+                    t_mdagm.append(t)
+            res, ts = on_slabs(lambda op, v: op.cg_solve(v, **kw))
+            if k:
+                t_solve.append(ts)
+            iters = res[0][1][0]["iters"]
+            ok = ok and all(r[2] for r in res)
+        halo = Q.qcd_slab_halo_bytes(ops[0].ctx, 32, 1)
+        for op in ops:
+            op.close()
+        if hasattr(grp, "close"):
+            grp.close()
+        return (float(np.median(t_mdagm)) if t_mdagm else None), float(np.median(t_solve)), iters, ok, halo
+
+    mdagm_n, solve_n, iters, ok_n, halo = measure(slab.NativeSlabGroup(2), True)
+    _, solve_p, _, ok_p, _ = measure(slab.LocalSlabGroup(2), False)
     one = Q.CloverWilson(dims, w["t_bc"])
     one.load_gauge(torch.from_numpy(U).cuda(), recon12=True)
     one.clover_build(w["kappa"], w["csw"])
@@ -686,15 +700,13 @@ def slab_section(w, reps=5):
         if k:
             t1.append(1e3 * (time.perf_counter() - t0))
     one.close()
-    halo = Q.qcd_slab_halo_bytes(ops[0].ctx, 32, 1)
-    for op in ops:
-        op.close()
     return {"dims": list(dims), "slabs": [list(s) for s in bounds], "gpus": 1,
-            "mdagm_fp32_ms_two_slabs": float(np.median(t_mdagm)),
-            "mixed_solve_ms_two_slabs": float(np.median(t_solve)), "mixed_solve_ms_one_context": float(np.median(t1)),
-            "iters_two_slabs": iters, "iters_one_context": st1[0]["iters"], "converged": bool(ok and ok1),
+            "mdagm_fp32_ms_two_slabs": mdagm_n, "mixed_solve_ms_two_slabs": solve_n,
+            "mixed_solve_ms_two_slabs_python_exchange": solve_p, "mixed_solve_ms_one_context": float(np.median(t1)),
+            "iters_two_slabs": iters, "iters_one_context": st1[0]["iters"], "converged": bool(ok_n and ok_p and ok1),
             "halo_bytes_per_exchange_fp32": halo, "exchanges_per_mdagm": 4,
-            "timing": f"median of {reps} after one, host wall clock (each exchange synchronises both slabs)"}
+            "exchange": "the library's in-process group (qcd_local_group_*); python_exchange: LocalSlabGroup",
+            "timing": f"median of {reps} after one, host wall clock around both slabs' calls"}
 
 
 def run_e2e(op, U_np, b_np, w, stream, dev):

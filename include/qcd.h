@@ -396,6 +396,28 @@ qcd_status qcd_slab_cg_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs,
                              qcd_solver_stats* stats, const qcd_slab_comm* comm);
 
 /*
+ * In-process slab group: the exchanges and sums for n slabs (1 <= n <= 16) of one lattice held by one
+ * process, for example all on one GPU, each slab's qcd_slab_* calls made from a host thread of its own.
+ * qcd_local_group_create: an empty group of n ranks.  qcd_local_group_join(grp, rank, ctx, comm):
+ * rank `rank` is the slab context ctx (rank r's slab lies above rank r-1's, periodically); the group
+ * allocates the rank's four halo buffers (qcd_slab_halo_bytes for FP64 and 8 RHS) on ctx's device and
+ * fills *comm with them and with the group's callbacks, which every later qcd_slab_* call of ctx takes.
+ * Every rank joins before any rank calls; a call that finds a rank missing waits for it at the
+ * group's host barrier for up to two minutes, then fails with QCD_ERR_COMM, as do all later calls of
+ * the group.  The callbacks do not wait for the GPU: a rank records CUDA events on its context's stream
+ * when its faces or partial sums are ready, the ranks meet at a host barrier to publish them, and the
+ * copies and the sums (in rank order, the same bits on every rank) wait for them on the reading
+ * rank's stream.  qcd_local_group_abort releases every rank waiting at the group's barrier and
+ * makes this and every later call of the group fail with QCD_ERR_COMM (for a rank that will not
+ * come).  qcd_local_group_destroy frees the buffers and the group (after the last call).
+ */
+typedef struct qcd_local_group qcd_local_group;
+qcd_status qcd_local_group_create(qcd_local_group** grp, int n);
+qcd_status qcd_local_group_join(qcd_local_group* grp, int rank, qcd_ctx* ctx, qcd_slab_comm* comm);
+qcd_status qcd_local_group_abort(qcd_local_group* grp);
+qcd_status qcd_local_group_destroy(qcd_local_group* grp);
+
+/*
  * Device-limit probes for the kernels' rooflines (the paper has no counterpart; it quotes the Cell's
  * peak rates, Sec. 2, and measures its DMA bandwidths, Sec. 3).  Both run on the current device,
  * ordered on cuda_stream (NULL: the legacy default stream), allocate their own buffers and

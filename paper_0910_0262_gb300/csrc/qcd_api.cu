@@ -426,19 +426,8 @@ int batch_of(int n) {
 }  // namespace
 
 // Read-only view of a context and the thread's error message, for entry points defined in other
-// translation units of the library.
+// translation units of the library (qcd_kernels.h).
 namespace qcd {
-struct CtxView {
-  Geom g;
-  cudaStream_t st;
-  int device;
-  const void* g64;
-  const void* A_even64;
-  const void* Ainv_odd64;
-  double kappa;
-  bool have_gauge, have_clover;
-  bool slab;
-};
 
 bool ctx_view(const qcd_ctx* c, CtxView* v) {
   if (!c) return false;

@@ -3,9 +3,25 @@
 
 #include <cuda_runtime.h>
 
+#include "qcd.h"
 #include "qcd_internal.cuh"
 
 namespace qcd {
+
+// Read-only view of a context, for entry points defined outside qcd_api.cu (filled by ctx_view;
+// false for a null context)
+struct CtxView {
+  Geom g;
+  cudaStream_t st;
+  int device;
+  const void* g64;
+  const void* A_even64;
+  const void* Ainv_odd64;
+  double kappa;
+  bool have_gauge, have_clover;
+  bool slab;
+};
+bool ctx_view(const qcd_ctx* c, CtxView* v);
 
 // kernels launched by the library since the last reset (profiling)
 extern long long g_kernel_launches;

@@ -35,20 +35,6 @@
 #include "qcd_dslash.cuh"
 #include "qcd_kernels.h"
 
-namespace qcd {
-struct CtxView {
-  Geom g;
-  cudaStream_t st;
-  int device;
-  const void* g64;
-  const void* A_even64;
-  const void* Ainv_odd64;
-  double kappa;
-  bool have_gauge, have_clover;
-  bool slab;
-};
-bool ctx_view(const qcd_ctx* c, CtxView* v);
-}  // namespace qcd
 
 using namespace qcd;
 

@@ -111,6 +111,10 @@ _SIGNATURES = {
                                          ctypes.POINTER(SolverStats), ctypes.POINTER(SlabComm)]),
     "qcd_debug_violations": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_int)]),
     "qcd_selftest_debug_index": (ctypes.c_int, [_P]),
+    "qcd_local_group_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int]),
+    "qcd_local_group_join": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.POINTER(SlabComm)]),
+    "qcd_local_group_abort": (ctypes.c_int, [_P]),
+    "qcd_local_group_destroy": (ctypes.c_int, [_P]),
     "qcd_last_error": (ctypes.c_char_p, []),
 }
 
@@ -253,6 +257,28 @@ def qcd_mhat_static(ctx, out_ptr, in_ptr, dagger=0):
 def qcd_selftest_barrier_timeout(ctx):
     """Returns the status of the barrier self-test (QCD_ERR_TIMEOUT = 8 when the wait gave up)."""
     return lib().qcd_selftest_barrier_timeout(ctx)
+
+
+def qcd_local_group_create(n):
+    """An in-process group of n slabs whose exchanges and sums the library makes (see include/qcd.h)."""
+    g = _P()
+    _check(lib().qcd_local_group_create(ctypes.byref(g), int(n)))
+    return g
+
+
+def qcd_local_group_join(grp, rank, ctx):
+    """Rank `rank` of the group is the slab context ctx; returns the SlabComm its calls take."""
+    comm = SlabComm()
+    _check(lib().qcd_local_group_join(grp, int(rank), ctx, ctypes.byref(comm)))
+    return comm
+
+
+def qcd_local_group_abort(grp):
+    _check(lib().qcd_local_group_abort(grp))
+
+
+def qcd_local_group_destroy(grp):
+    _check(lib().qcd_local_group_destroy(grp))
 
 
 QCD_DBG_SPINOR, QCD_DBG_LINK, QCD_DBG_CLOVER, QCD_DBG_HALO = 1, 2, 4, 8

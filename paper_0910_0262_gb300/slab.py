@@ -9,8 +9,11 @@ ranks; the library asks for both through callbacks, which this module provides:
 
 * ``TorchHaloComm`` -- torch.distributed (NCCL for CUDA tensors across processes, gloo for CPU
   tensors): paired sends and receives to the ranks below and above, and an all-reduce;
-* ``LocalSlabGroup`` -- several slabs of one lattice in one process (for example on one GPU), each
-  driven by a host thread of its own, exchanging through device copies between their buffers.
+* ``NativeSlabGroup`` -- several slabs of one lattice in one process (for example on one GPU), each
+  driven by a host thread of its own; the library's in-process group (qcd_local_group_*) makes the
+  exchanges and sums, ordered by CUDA events between the slabs' streams, with no Python in the loop;
+* ``LocalSlabGroup`` -- the same with the exchanges and sums written in Python (torch copies after
+  host synchronisation), a reference for the native group.
 
 ``SlabCloverWilson`` owns one slab context, its four halo buffers and the ctypes callbacks.  All
 arithmetic runs in the library's kernels; this module only moves buffers between ranks.
@@ -104,9 +107,10 @@ def device_doubles(ptr, n):
 
 class SlabCloverWilson:
     """Owns one slab context of a global lattice dims = (X, Y, Z, T) with its four halo buffers and the
-    callbacks the qcd_slab_* calls make.  exchange(send_lo, send_hi, recv_lo, recv_hi) (uint8 device
-    tensors of the bytes to move) and allreduce(values) (a float64 device tensor) come from the comm
-    object (TorchHaloComm, or a LocalSlabGroup member)."""
+    callbacks the qcd_slab_* calls make.  comm: a NativeSlabGroup member (the library's buffers and
+    callbacks), or an object with exchange(send_lo, send_hi, recv_lo, recv_hi) (uint8 device tensors of
+    the bytes to move) and allreduce(values) (a float64 device tensor): TorchHaloComm, or a
+    LocalSlabGroup member."""
 
     def __init__(self, dims, t_offset, t_local, comm, t_bc=-1.0, stream=None):
         if not torch.cuda.is_available():
@@ -120,9 +124,14 @@ class SlabCloverWilson:
         self.ctx = Q.qcd_create_slab(self.dims, self.t_offset, self.t_local, t_bc,
                                      ctypes.c_void_p(self.stream.cuda_stream))
         self.comm = comm
+        self._errors = []
+        if isinstance(comm, _NativeMember):
+            # the group's buffers and native callbacks
+            self.comm_struct = Q.qcd_local_group_join(comm.group.handle, comm.rank, self.ctx)
+            self.bufs, self._fns = None, None
+            return
         nbytes = Q.qcd_slab_halo_bytes(self.ctx, 64, 8)  # the largest: FP64 reliable updates of 8 RHS
         self.bufs = [torch.zeros(nbytes, dtype=torch.uint8, device="cuda") for _ in range(4)]
-        self._errors = []
 
         def exchange(user, nb):
             try:
@@ -192,6 +201,57 @@ class SlabCloverWilson:
         return x, [st[i].as_dict() for i in range(n)], s == Q.QCD_OK
 
 
+def _run_threads(n, fns, abort):
+    """Call fns[r]() on thread r; returns their results (re-raises the first error after abort())."""
+    out = [None] * n
+    errs = []
+
+    def body(r):
+        try:
+            out[r] = fns[r]()
+        except BaseException as e:
+            errs.append(e)
+            abort()
+
+    th = [threading.Thread(target=body, args=(r,)) for r in range(n)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    if errs:
+        raise errs[0]
+    return out
+
+
+class NativeSlabGroup:
+    """Several slabs of one lattice in this process (for example all on one GPU): member(r) is the comm
+    of slab r, whose exchanges and sums the library's in-process group makes (qcd_local_group_*: CUDA
+    events between the slabs' streams, host barriers only to publish them, sums in slab order).  Each
+    slab's calls must run on a host thread of their own (run()); ctypes releases the interpreter lock
+    during the calls, so the slabs' threads run side by side.  close() after the slabs' last call."""
+
+    def __init__(self, n):
+        self.n = n
+        self.handle = Q.qcd_local_group_create(n)
+
+    def member(self, rank):
+        return _NativeMember(self, rank)
+
+    def run(self, fns):
+        return _run_threads(self.n, fns, lambda: Q.qcd_local_group_abort(self.handle))
+
+    def close(self):
+        if self.handle is not None:
+            Q.qcd_local_group_destroy(self.handle)
+            self.handle = None
+
+
+class _NativeMember:
+    def __init__(self, group, rank):
+        self.group = group
+        self.rank = rank
+
+
 class LocalSlabGroup:
     """Several slabs of one lattice in this process (for example all on one GPU): member(r) is the comm
     object of slab r; each slab's calls must run on a host thread of their own (run()).  An exchange or a
@@ -210,24 +270,7 @@ class LocalSlabGroup:
 
     def run(self, fns):
         """Call fns[r]() on thread r for every slab; returns their results (re-raises the first error)."""
-        out = [None] * self.n
-        errs = []
-
-        def body(r):
-            try:
-                out[r] = fns[r]()
-            except BaseException as e:
-                errs.append(e)
-                self.barrier.abort()
-
-        th = [threading.Thread(target=body, args=(r,)) for r in range(self.n)]
-        for t in th:
-            t.start()
-        for t in th:
-            t.join()
-        if errs:
-            raise errs[0]
-        return out
+        return _run_threads(self.n, fns, self.barrier.abort)
 
 
 class _LocalMember:

@@ -1,5 +1,7 @@
 """The time decomposition on the GPU, through the C ABI: slabs of one lattice, each a context of its
-own driven by a host thread, exchanging their halos through device copies (LocalSlabGroup) on one GPU.
+own driven by a host thread, exchanging their halos on one GPU through the library's in-process group
+(NativeSlabGroup: native callbacks, CUDA events between the slabs' streams) or through device copies
+made in Python (LocalSlabGroup).
 
 * a single slab that is the whole lattice (its own neighbour) agrees with the ordinary context's
   operators;
@@ -7,7 +9,8 @@ own driven by a host thread, exchanging their halos through device copies (Local
   hopping blocks on the whole lattice within the parity tolerances (FP64 1e-13, FP32 1e-6, FP16 5e-3);
 * the CG solve on two slabs (FP64, and FP32 inner with FP64 reliable updates) reaches a true residual
   <= 1e-8 recomputed by the oracle on the gathered solution, in about the iterations of one context;
-* calls that need an ordinary lattice refuse a slab context, and a failing callback is reported.
+* calls that need an ordinary lattice refuse a slab context, and a failing callback is reported; an
+  aborted native group fails its calls at once.
 """
 
 import ctypes
@@ -25,9 +28,11 @@ KAPPA, CSW, TBC = 0.12, 1.0, -1.0
 TOL = {64: 1e-13, 32: 1e-6, 16: 5e-3}
 
 
-def _slabs(dims, U, bounds, recon12=True):
+def _slabs(dims, U, bounds, recon12=True, kind="python"):
+    """The slabs of `bounds`, exchanging through a LocalSlabGroup (kind "python") or the library's
+    in-process group (kind "native")."""
     from paper_0910_0262_gb300 import slab
-    grp = slab.LocalSlabGroup(len(bounds))
+    grp = slab.NativeSlabGroup(len(bounds)) if kind == "native" else slab.LocalSlabGroup(len(bounds))
     ops = []
     for r, (t0, tl) in enumerate(bounds):
         st = torch.cuda.Stream()
@@ -88,12 +93,20 @@ def test_whole_lattice_slab_matches_the_ordinary_context(lattice):
         op.close()
 
 
+def _close(grp, ops):
+    for op in ops:
+        op.close()
+    if hasattr(grp, "close"):
+        grp.close()
+
+
+@pytest.mark.parametrize("kind", ["python", "native"])
 @pytest.mark.parametrize("bounds", [[(0, 4), (4, 4)], [(0, 2), (2, 6)], [(0, 2), (2, 2), (4, 4)],
                                     [(0, 2), (2, 2), (4, 2), (6, 2)]])
-def test_split_lattice_matches_the_oracle(lattice, bounds):
+def test_split_lattice_matches_the_oracle(lattice, bounds, kind):
     from paper_0910_0262_gb300 import qcd as Q
     dims, U, b, ref = lattice
-    grp, ops = _slabs(dims, U, bounds)
+    grp, ops = _slabs(dims, U, bounds, kind=kind)
     rng = np.random.default_rng(11)
     ve = rand_eo(1, b.shape[1], rng)
     v = to_dev(ve)
@@ -106,18 +119,18 @@ def test_split_lattice_matches_the_oracle(lattice, bounds):
                "doe": _apply(grp, ops, dims, v, Q.QCD_OP_DSLASH_OE, False, prec)[0]}
         for k in want:
             err = rel_l2(got[k], want[k])
-            assert err <= TOL[prec], (bounds, prec, k, err)
-    for op in ops:
-        op.close()
+            assert err <= TOL[prec], (bounds, kind, prec, k, err)
+    _close(grp, ops)
 
 
+@pytest.mark.parametrize("kind", ["python", "native"])
 @pytest.mark.parametrize("inner", [64, 32])
-def test_split_lattice_cg_solve(lattice, inner):
+def test_split_lattice_cg_solve(lattice, inner, kind):
     from paper_0910_0262_gb300 import slab
     from paper_0910_0262_gb300.qcd import CloverWilson
     dims, U, b, ref = lattice
     bounds = [(0, 4), (4, 4)]
-    grp, ops = _slabs(dims, U, bounds)
+    grp, ops = _slabs(dims, U, bounds, kind=kind)
     bd = to_dev(b)
     kw = dict(tol=1e-8, inner_prec=inner, reliable_every=50, reliable_delta=0.1, max_iter=2000)
 
@@ -146,8 +159,25 @@ def test_split_lattice_cg_solve(lattice, inner):
     for k in range(b.shape[0]):
         assert abs(res[0][1][k]["iters"] - st1[k]["iters"]) <= 2
     plain.close()
+    _close(grp, ops)
+
+
+def test_native_group_abort_fails_the_calls(lattice):
+    """A native group released by qcd_local_group_abort (a rank that will not come) fails every call
+    with QCD_ERR_COMM at once, without waiting at its barrier; joining twice is refused."""
+    from paper_0910_0262_gb300 import qcd as Q
+    dims, U, b, ref = lattice
+    grp, ops = _slabs(dims, U, [(0, 4), (4, 4)], kind="native")
+    with pytest.raises(Q.QCDError) as e:
+        Q.qcd_local_group_join(grp.handle, 0, ops[0].ctx)
+    assert e.value.status == 4
+    Q.qcd_local_group_abort(grp.handle)
+    v = torch.zeros((1, ops[0].Vh, 4, 3), dtype=torch.complex128, device="cuda")
     for op in ops:
-        op.close()
+        with pytest.raises(Q.QCDError) as e:
+            op.dslash(v, Q.QCD_OP_DSLASH_OE, precision=64)
+        assert e.value.status == 9
+    _close(grp, ops)
 
 
 def test_slab_refusals_and_failed_callback(lattice):
