@@ -6,9 +6,9 @@
 // for its readers' events before it reuses its buffers.  No host thread waits for the GPU, and the
 // sums are added in slab order, so every slab gets the same bits.  (The paper's two MPI processes on
 // one Cell blade exchanged through shared memory, Sec. 4; this is the single-process analogue.)
+#include <atomic>
 #include <chrono>
-#include <condition_variable>
-#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "qcd.h"
@@ -59,32 +59,38 @@ struct Member {
 struct qcd_local_group {
   int n = 0;
   std::vector<Member> members;
-  std::mutex mu;
-  std::condition_variable cv;
-  int arrived = 0;
-  unsigned long long generation = 0;
-  bool broken = false;
+  std::atomic<int> arrived{0};
+  std::atomic<unsigned> generation{0};
+  std::atomic<bool> broken{false};
 };
 
 namespace {
 
-// all n slabs meet; false (for every later caller too) if one has not arrived within the timeout
+// All n slabs meet; false (for every later caller too) if one has not arrived within the timeout or
+// the group was aborted.  Each slab has a host thread of its own, so the waiting threads spin on the
+// generation word (yielding now and then) rather than sleep: a wake-up through the scheduler costs
+// tens of microseconds, several times per CG iteration.  The last arrival resets the count before it
+// advances the generation, so no thread enters the next barrier before the count is reset.
 bool group_barrier(qcd_local_group* g) {
-  std::unique_lock<std::mutex> lk(g->mu);
-  if (g->broken) return false;
-  const unsigned long long gen = g->generation;
-  if (++g->arrived == g->n) {
-    g->arrived = 0;
-    g->generation++;
-    g->cv.notify_all();
+  if (g->broken.load(std::memory_order_acquire)) return false;
+  const unsigned gen = g->generation.load(std::memory_order_acquire);
+  if (g->arrived.fetch_add(1, std::memory_order_acq_rel) + 1 == g->n) {
+    g->arrived.store(0, std::memory_order_relaxed);
+    g->generation.fetch_add(1, std::memory_order_release);
     return true;
   }
-  if (!g->cv.wait_for(lk, kBarrierTimeout, [&] { return g->generation != gen || g->broken; })) {
-    g->broken = true;
-    g->cv.notify_all();
-    return false;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (unsigned k = 1; g->generation.load(std::memory_order_acquire) == gen; k++) {
+    if (g->broken.load(std::memory_order_acquire)) return false;
+    if ((k & 1023) == 0) {
+      if (std::chrono::steady_clock::now() - t0 > kBarrierTimeout) {
+        g->broken.store(true, std::memory_order_release);
+        return false;
+      }
+      std::this_thread::yield();
+    }
   }
-  return !g->broken;
+  return !g->broken.load(std::memory_order_acquire);
 }
 
 int local_exchange(void* user, size_t bytes) {
@@ -207,9 +213,7 @@ qcd_status qcd_local_group_join(qcd_local_group* grp, int rank, qcd_ctx* ctx, qc
 
 qcd_status qcd_local_group_abort(qcd_local_group* grp) {
   if (!grp) return qcd::set_error(QCD_ERR_ARG, "null pointer");
-  std::lock_guard<std::mutex> lk(grp->mu);
-  grp->broken = true;
-  grp->cv.notify_all();
+  grp->broken.store(true, std::memory_order_release);
   return QCD_OK;
 }
 
