@@ -1,13 +1,15 @@
 // Fermion-force launchers (internal to libqcd).
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include "qcd_internal.cuh"
 
 namespace qcd {
 
-extern long long g_kernel_launches;
+extern std::atomic<long long> g_kernel_launches;
 
 // bytes of one per-site, per-plane 3x3 complex field over the full lattice (6 planes)
 size_t force_clover_bytes(const Geom& g);

@@ -1,6 +1,8 @@
 // Host-side launchers of the CUDA kernels (internal to libqcd; not part of the C ABI).
 #pragma once
 
+#include <atomic>
+
 #include <cuda_runtime.h>
 
 #include "qcd.h"
@@ -24,7 +26,7 @@ struct CtxView {
 bool ctx_view(const qcd_ctx* c, CtxView* v);
 
 // kernels launched by the library since the last reset (profiling)
-extern long long g_kernel_launches;
+extern std::atomic<long long> g_kernel_launches;
 
 // ---- persistent single-RHS CG iteration (qcd_cg_persistent.cu)
 struct PersistentCGArgs {

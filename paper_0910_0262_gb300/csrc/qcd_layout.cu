@@ -11,7 +11,7 @@ namespace qcd {
 
 QCD_DEBUG_TAKE(debug_take_layout)
 
-long long g_kernel_launches = 0;
+std::atomic<long long> g_kernel_launches{0};
 
 namespace {
 
