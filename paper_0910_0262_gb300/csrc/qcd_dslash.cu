@@ -52,13 +52,13 @@ void launch_site_k(int epi, const DslashArgs& a, int nb, cudaStream_t st) {
       case EPI_XPAY_CG: dslash_site_fp16_kernel<RECON, EPI_XPAY_CG, STAGED><<<nb, 128, 0, st>>>(a); break;
       default: dslash_site_fp16_kernel<RECON, EPI_XPAY, STAGED><<<nb, 128, 0, st>>>(a); break;
     }
-    return;
-  }
-  switch (epi) {
-    case EPI_NONE: dslash_site_kernel<P, RECON, EPI_NONE, STAGED><<<nb, 128, 0, st>>>(a); break;
-    case EPI_CLOVER_INV: dslash_site_kernel<P, RECON, EPI_CLOVER_INV, STAGED><<<nb, 128, 0, st>>>(a); break;
-    case EPI_XPAY_CG: dslash_site_kernel<P, RECON, EPI_XPAY_CG, STAGED><<<nb, 128, 0, st>>>(a); break;
-    default: dslash_site_kernel<P, RECON, EPI_XPAY, STAGED><<<nb, 128, 0, st>>>(a); break;
+  } else {
+    switch (epi) {
+      case EPI_NONE: dslash_site_kernel<P, RECON, EPI_NONE, STAGED><<<nb, 128, 0, st>>>(a); break;
+      case EPI_CLOVER_INV: dslash_site_kernel<P, RECON, EPI_CLOVER_INV, STAGED><<<nb, 128, 0, st>>>(a); break;
+      case EPI_XPAY_CG: dslash_site_kernel<P, RECON, EPI_XPAY_CG, STAGED><<<nb, 128, 0, st>>>(a); break;
+      default: dslash_site_kernel<P, RECON, EPI_XPAY, STAGED><<<nb, 128, 0, st>>>(a); break;
+    }
   }
 }
 
