@@ -369,11 +369,15 @@ long long qcd_selftest_fastdiv(void);
  * qcd_slab_comm: send_lo/send_hi/recv_lo/recv_hi are device buffers of at least qcd_slab_halo_bytes
  * bytes, owned by the caller.  exchange(user, bytes) is called after the library has enqueued, on the
  * context's stream, the kernels that fill the first `bytes` of send_lo and send_hi; before kernels the
- * library enqueues after it returns, it must have copied the slab above's send_lo into this rank's
- * recv_hi and the slab below's send_hi into its recv_lo (neighbours taken periodically in t; a single
- * slab of the whole lattice is its own neighbour), in that stream's order.  allreduce(user, values, n)
- * replaces n doubles in device memory by their sums over the ranks, likewise in stream order.  A
- * nonzero return from either makes the call fail with QCD_ERR_COMM.
+ * library enqueues after it returns, recv_hi must hold the slab above's send_lo faces and recv_lo the
+ * slab below's send_hi faces (neighbours taken periodically in t; a single slab of the whole lattice is
+ * its own neighbour), in that stream's order: copied there, or with recv_lo / recv_hi pointed at those
+ * buffers by the callback.  The library reads the four pointers from *comm at every pass (send_lo and
+ * send_hi before it packs, recv_lo and recv_hi after exchange returns), so the callback may rewrite
+ * them, for example to alternate between buffer sets; the struct passed to a call must then be the
+ * one the callback rewrites.  allreduce(user, values, n) replaces n doubles in device memory by their
+ * sums over the ranks, likewise in stream order.  A nonzero return from either makes the call fail
+ * with QCD_ERR_COMM.
  */
 typedef int (*qcd_halo_exchange_fn)(void* user, size_t bytes);
 typedef int (*qcd_allreduce_fn)(void* user, double* values, int n);
@@ -397,19 +401,22 @@ qcd_status qcd_slab_cg_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs,
 
 /*
  * In-process slab group: the exchanges and sums for n slabs (1 <= n <= 16) of one lattice held by one
- * process, for example all on one GPU, each slab's qcd_slab_* calls made from a host thread of its own.
+ * process on one GPU, each slab's qcd_slab_* calls made from a host thread of its own.
  * qcd_local_group_create: an empty group of n ranks.  qcd_local_group_join(grp, rank, ctx, comm):
- * rank `rank` is the slab context ctx (rank r's slab lies above rank r-1's, periodically); the group
- * allocates the rank's four halo buffers (qcd_slab_halo_bytes for FP64 and 8 RHS) on ctx's device and
- * fills *comm with them and with the group's callbacks, which every later qcd_slab_* call of ctx takes.
- * Every rank joins before any rank calls; a call that finds a rank missing waits for it at the
- * group's host barrier for up to two minutes, then fails with QCD_ERR_COMM, as do all later calls of
- * the group.  The callbacks do not wait for the GPU: a rank records CUDA events on its context's stream
- * when its faces or partial sums are ready, the ranks meet at a host barrier to publish them, and the
- * copies and the sums (in rank order, the same bits on every rank) wait for them on the reading
- * rank's stream.  qcd_local_group_abort releases every rank waiting at the group's barrier and
- * makes this and every later call of the group fail with QCD_ERR_COMM (for a rank that will not
- * come).  qcd_local_group_destroy frees the buffers and the group (after the last call).
+ * rank `rank` is the slab context ctx (rank r's slab lies above rank r-1's, periodically; every rank's
+ * context on the same device, else QCD_ERR_ARG); the group allocates the rank's two sets of send
+ * buffers (qcd_slab_halo_bytes for FP64 and 8 RHS each) on ctx's device and fills *comm with them and
+ * with the group's callbacks.  Every later qcd_slab_* call of ctx takes that same struct, which the
+ * exchanges rewrite: the receive pointers name the neighbours' send buffers of the pass (read in
+ * place), and the send pointers alternate between the two sets.  Every rank joins before any rank
+ * calls; a call that finds a rank missing waits for it at the group's host barrier for up to two
+ * minutes, then fails with QCD_ERR_COMM, as do all later calls of the group.  The callbacks do not
+ * wait for the GPU: a rank records a CUDA event on its context's stream when its faces or partial
+ * sums are ready, the ranks meet once per exchange or sum at a host barrier to publish them, and the
+ * halo kernels and the sums (in rank order, the same bits on every rank) wait for them on the reading
+ * rank's stream.  qcd_local_group_abort releases every rank waiting at the group's barrier and makes
+ * this and every later call of the group fail with QCD_ERR_COMM (for a rank that will not come).
+ * qcd_local_group_destroy frees the buffers and the group (after the last call).
  */
 typedef struct qcd_local_group qcd_local_group;
 qcd_status qcd_local_group_create(qcd_local_group** grp, int n);

@@ -1,13 +1,18 @@
 // In-process slab group: the halo exchanges and sums of the time decomposition for several slabs of
-// one lattice held by one process (for example all on one GPU), each slab driven by a host thread of
-// its own.  The callbacks run in the library: a slab records a CUDA event on its stream when its
-// faces (or its partial sums) are ready, the slabs meet at a host barrier only to publish those events,
-// and every copy or sum waits for them on the reading slab's stream; the writer's stream then waits
-// for its readers' events before it reuses its buffers.  No host thread waits for the GPU, and the
-// sums are added in slab order, so every slab gets the same bits.  (The paper's two MPI processes on
-// one Cell blade exchanged through shared memory, Sec. 4; this is the single-process analogue.)
+// one lattice held by one process on one GPU, each slab driven by a host thread of its own.  The
+// callbacks run in the library: a slab records a CUDA event on its stream when its faces (or its
+// partial sums) are ready, and the slabs meet once per exchange or sum at a host barrier, only to
+// publish those events.  A slab's halo kernel then reads its neighbours' send buffers in place (no
+// copy), after waiting for their events on its own stream; the send buffers alternate between two
+// sets from one pass to the next, so a slab packs the next pass's faces while its neighbours may
+// still read the last ones, and the wait at the next meeting orders its packing after their reads
+// of the set before.  Sums stage each slab's values in one of two alternating buffers and add them
+// in slab order, so every slab gets the same bits.  No host thread waits for the GPU.  (The paper's
+// two MPI processes on one Cell blade exchanged through shared memory, Sec. 4; this is the
+// single-process analogue.)
 #include <atomic>
 #include <chrono>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -48,10 +53,12 @@ struct Member {
   int rank = -1;
   int device = -1;
   cudaStream_t st = nullptr;
-  void* buf[4] = {nullptr, nullptr, nullptr, nullptr};  // send_lo, send_hi, recv_lo, recv_hi
+  void* buf[4] = {nullptr, nullptr, nullptr, nullptr};  // send sets: (lo, hi) = buf[2 s], buf[2 s + 1]
   size_t cap = 0;
-  double* stage = nullptr;
-  cudaEvent_t ready = nullptr, done = nullptr;
+  double* stage = nullptr;                              // two sets of kStageDoubles
+  cudaEvent_t ready = nullptr;
+  qcd_slab_comm* comm = nullptr;                        // the struct the slab's calls take
+  unsigned passes = 0, sums = 0;                        // calls so far: the current set of each
 };
 
 }  // namespace
@@ -59,6 +66,7 @@ struct Member {
 struct qcd_local_group {
   int n = 0;
   std::vector<Member> members;
+  std::mutex join_mu;
   std::atomic<int> arrived{0};
   std::atomic<unsigned> generation{0};
   std::atomic<bool> broken{false};
@@ -93,32 +101,36 @@ bool group_barrier(qcd_local_group* g) {
   return !g->broken.load(std::memory_order_acquire);
 }
 
+// After every slab's faces of this pass are packed (its event), the pass's receive buffers are the
+// neighbours' send buffers of the current set; the next pass packs into the other set.
 int local_exchange(void* user, size_t bytes) {
   Member* m = static_cast<Member*>(user);
   qcd_local_group* g = m->grp;
   if (bytes > m->cap) return 1;
+  const int s = m->passes & 1;
   if (cudaEventRecord(m->ready, m->st) != cudaSuccess) return 1;
   if (!group_barrier(g)) return 1;
   const Member& up = g->members[(m->rank + 1) % g->n];
   const Member& lo = g->members[(m->rank + g->n - 1) % g->n];
   cudaStreamWaitEvent(m->st, up.ready, 0);
   cudaStreamWaitEvent(m->st, lo.ready, 0);
-  cudaMemcpyAsync(m->buf[3], up.buf[0], bytes, cudaMemcpyDeviceToDevice, m->st);  // recv_hi <- upper send_lo
-  cudaMemcpyAsync(m->buf[2], lo.buf[1], bytes, cudaMemcpyDeviceToDevice, m->st);  // recv_lo <- lower send_hi
-  cudaEventRecord(m->done, m->st);
-  if (!group_barrier(g)) return 1;
-  // the next packing into this slab's send buffers follows its readers' copies
-  cudaStreamWaitEvent(m->st, up.done, 0);
-  cudaStreamWaitEvent(m->st, lo.done, 0);
+  m->comm->recv_hi = up.buf[2 * s];      // the slab above's lower face
+  m->comm->recv_lo = lo.buf[2 * s + 1];  // the slab below's upper face
+  m->passes++;
+  m->comm->send_lo = m->buf[2 * (1 - s)];
+  m->comm->send_hi = m->buf[2 * (1 - s) + 1];
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
+// values <- the sum over the slabs in slab order, from the staged copies of the current set
 int local_allreduce(void* user, double* values, int n) {
   Member* m = static_cast<Member*>(user);
   qcd_local_group* g = m->grp;
   if (n < 0 || n > kStageDoubles) return 1;
   if (n == 0) return 0;
-  cudaMemcpyAsync(m->stage, values, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->st);
+  const int s = m->sums & 1;
+  m->sums++;
+  cudaMemcpyAsync(m->stage + s * kStageDoubles, values, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->st);
   if (cudaEventRecord(m->ready, m->st) != cudaSuccess) return 1;
   if (!group_barrier(g)) return 1;
   SumArgs a;
@@ -127,13 +139,10 @@ int local_allreduce(void* user, double* values, int n) {
   a.out = values;
   for (int k = 0; k < g->n; k++) {
     cudaStreamWaitEvent(m->st, g->members[k].ready, 0);
-    a.src[k] = g->members[k].stage;
+    a.src[k] = g->members[k].stage + s * kStageDoubles;
   }
   qcd::g_kernel_launches += 1;
   local_sum_kernel<<<(n + 63) / 64, 64, 0, m->st>>>(a);
-  cudaEventRecord(m->done, m->st);
-  if (!group_barrier(g)) return 1;
-  for (int k = 0; k < g->n; k++) cudaStreamWaitEvent(m->st, g->members[k].done, 0);  // every slab read `stage`
   return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
 
@@ -149,8 +158,8 @@ void release_member(Member& m) {
   cudaFree(m.stage);
   m.stage = nullptr;
   if (m.ready) cudaEventDestroy(m.ready);
-  if (m.done) cudaEventDestroy(m.done);
-  m.ready = m.done = nullptr;
+  m.ready = nullptr;
+  m.comm = nullptr;
   m.device = -1;
   if (prev >= 0) cudaSetDevice(prev);
   cudaGetLastError();
@@ -183,8 +192,12 @@ qcd_status qcd_local_group_join(qcd_local_group* grp, int rank, qcd_ctx* ctx, qc
   if (!grp || !comm) return qcd::set_error(QCD_ERR_ARG, "null pointer");
   if (rank < 0 || rank >= grp->n) return qcd::set_error(QCD_ERR_ARG, "rank outside the group");
   if (!v.slab) return qcd::set_error(QCD_ERR_STATE, "local group members are slab contexts");
+  std::lock_guard<std::mutex> lock(grp->join_mu);
   Member& m = grp->members[rank];
   if (m.device >= 0) return qcd::set_error(QCD_ERR_STATE, "rank already joined");
+  for (const Member& o : grp->members)
+    if (o.device >= 0 && o.device != v.device)
+      return qcd::set_error(QCD_ERR_ARG, "the slabs of a local group share one device");
   size_t cap = 0;
   qcd_status s = qcd_slab_halo_bytes(ctx, 64, 8, &cap);  // the largest: FP64 passes over 8 RHS
   if (s) return s;
@@ -193,18 +206,21 @@ qcd_status qcd_local_group_join(qcd_local_group* grp, int rank, qcd_ctx* ctx, qc
   m.cap = cap;
   bool ok = true;
   for (void*& b : m.buf) ok = ok && cudaMalloc(&b, cap) == cudaSuccess;
-  ok = ok && cudaMalloc(&m.stage, sizeof(double) * kStageDoubles) == cudaSuccess;
+  ok = ok && cudaMalloc(&m.stage, sizeof(double) * 2 * kStageDoubles) == cudaSuccess;
   ok = ok && cudaEventCreateWithFlags(&m.ready, cudaEventDisableTiming) == cudaSuccess;
-  ok = ok && cudaEventCreateWithFlags(&m.done, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     release_member(m);
     return qcd::set_error(QCD_ERR_NOMEM, "local group buffers");
   }
+  // the first pass packs into set 0; the receive pointers are set by every exchange (until the first,
+  // they name this rank's set 1, which nothing reads)
   comm->send_lo = m.buf[0];
   comm->send_hi = m.buf[1];
   comm->recv_lo = m.buf[2];
   comm->recv_hi = m.buf[3];
+  m.comm = comm;
+  m.passes = m.sums = 0;
   comm->exchange = local_exchange;
   comm->allreduce = local_allreduce;
   comm->user = &m;

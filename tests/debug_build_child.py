@@ -5,7 +5,8 @@ Work: every operator of qcd_dslash in FP64, FP32 and FP16 on 13 right-hand sides
 1) of a lattice whose half volume leaves ragged blocks, a mixed FP32 and a mixed FP16 solve of three
 RHS and a plain FP64 solve of one (the single-RHS persistent kernel and the multi-RHS graphs), the
 force on the FP64 solution with the clover determinant term, a reconstruction of the odd sites, and
-the operators on two t-slabs of the lattice (halo packing and the halo hopping kernels).
+the operators on two t-slabs of the lattice through the library's in-process group (halo packing, the
+halo hopping kernels reading the neighbour's send buffers in place).
 """
 
 import json
@@ -73,7 +74,7 @@ def main():
     xe = to_np(x)
     recon_err = rel_l2(x_o[0], ref.site(ref.A_oo_inv, b_o[0] + KAPPA * ref.D_oe(xe[0])))
     # the t-slab operators against the whole-lattice context
-    grp = slab.LocalSlabGroup(2)
+    grp = slab.NativeSlabGroup(2)
     sops = []
     for r, (t0, tl) in enumerate([(0, 2), (2, 2)]):
         st = torch.cuda.Stream()
@@ -96,6 +97,7 @@ def main():
     slab_err = max(rel_l2(got[r], ref.Mhat(v[r])) for r in range(2))
     for s in sops:
         s.close()
+    grp.close()
     viol, is_debug = Q.qcd_debug_violations(op.ctx)
     Q.qcd_selftest_debug_index(op.ctx)
     probe, _ = Q.qcd_debug_violations(op.ctx)

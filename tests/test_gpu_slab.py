@@ -70,11 +70,12 @@ def lattice():
     return dims, U, b, evenodd.SchurOperator(U, KAPPA, CSW, TBC)
 
 
-def test_whole_lattice_slab_matches_the_ordinary_context(lattice):
+@pytest.mark.parametrize("kind", ["python", "native"])
+def test_whole_lattice_slab_matches_the_ordinary_context(lattice, kind):
     from paper_0910_0262_gb300 import qcd as Q
     from paper_0910_0262_gb300.qcd import CloverWilson
     dims, U, b, ref = lattice
-    grp, ops = _slabs(dims, U, [(0, 8)])
+    grp, ops = _slabs(dims, U, [(0, 8)], kind=kind)
     plain = CloverWilson(dims, TBC)
     plain.load_gauge(to_dev(U), recon12=True)
     plain.clover_build(KAPPA, CSW)
@@ -87,10 +88,9 @@ def test_whole_lattice_slab_matches_the_ordinary_context(lattice):
                 # FP64: the same kernel arithmetic; FP32 / FP16 with two RHS the ordinary context runs
                 # its one-thread-per-(site, RHS) kernel, which sums in another order
                 tol = {64: 1e-14, 32: 1e-6, 16: 5e-3}[prec]
-                assert rel_l2(got, want) <= tol, (prec, opc, dag, rel_l2(got, want))
+                assert rel_l2(got, want) <= tol, (kind, prec, opc, dag, rel_l2(got, want))
     plain.close()
-    for op in ops:
-        op.close()
+    _close(grp, ops)
 
 
 def _close(grp, ops):
