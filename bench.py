@@ -632,8 +632,9 @@ def largest_volume(dev, hbm_peak, do_errors=False):
 def slab_section(w, reps=5):
     """The time decomposition on one GPU: the step's lattice cut into two t-slabs, each a context of its
     own on a stream of its own, driven by a host thread.  The halos and sums go through the library's
-    in-process group (NativeSlabGroup: native callbacks, CUDA events between the slabs' streams, host
-    barriers only to publish them); the same solve through the Python group (LocalSlabGroup: torch
+    in-process group (NativeSlabGroup: native callbacks, CUDA events between the slabs' streams, one host
+    barrier per exchange or sum only to publish them, halos read in place); the same solve through the
+    Python group (LocalSlabGroup: torch
     copies after host synchronisation) is given beside it.  Times Mhat^dag Mhat in FP32 (four
     exchanges) and the mixed FP32 solve to 1e-8 against one context, with the halo bytes per exchange.
     Both slabs share one GPU, so this measures the halo path's cost, not a multi-GPU speed."""

@@ -9,9 +9,10 @@ ranks; the library asks for both through callbacks, which this module provides:
 
 * ``TorchHaloComm`` -- torch.distributed (NCCL for CUDA tensors across processes, gloo for CPU
   tensors): paired sends and receives to the ranks below and above, and an all-reduce;
-* ``NativeSlabGroup`` -- several slabs of one lattice in one process (for example on one GPU), each
-  driven by a host thread of its own; the library's in-process group (qcd_local_group_*) makes the
-  exchanges and sums, ordered by CUDA events between the slabs' streams, with no Python in the loop;
+* ``NativeSlabGroup`` -- several slabs of one lattice in one process on one GPU, each driven by a host
+  thread of its own; the library's in-process group (qcd_local_group_*) makes the exchanges and sums
+  (halo kernels reading the neighbours' send buffers in place, ordered by CUDA events between the
+  slabs' streams), with no Python in the loop;
 * ``LocalSlabGroup`` -- the same with the exchanges and sums written in Python (torch copies after
   host synchronisation), a reference for the native group.
 
@@ -224,9 +225,10 @@ def _run_threads(n, fns, abort):
 
 
 class NativeSlabGroup:
-    """Several slabs of one lattice in this process (for example all on one GPU): member(r) is the comm
-    of slab r, whose exchanges and sums the library's in-process group makes (qcd_local_group_*: CUDA
-    events between the slabs' streams, host barriers only to publish them, sums in slab order).  Each
+    """Several slabs of one lattice in this process, all on one GPU: member(r) is the comm of slab r,
+    whose exchanges and sums the library's in-process group makes (qcd_local_group_*: CUDA events
+    between the slabs' streams, one host barrier per exchange or sum only to publish them, halos read
+    in place from the neighbours' send buffers, sums in slab order).  Each
     slab's calls must run on a host thread of their own (run()); ctypes releases the interpreter lock
     during the calls, so the slabs' threads run side by side.  close() after the slabs' last call."""
 
