@@ -112,8 +112,10 @@ int local_exchange(void* user, size_t bytes) {
   if (!group_barrier(g)) return 1;
   const Member& up = g->members[(m->rank + 1) % g->n];
   const Member& lo = g->members[(m->rank + g->n - 1) % g->n];
-  cudaStreamWaitEvent(m->st, up.ready, 0);
-  cudaStreamWaitEvent(m->st, lo.ready, 0);
+  // (with two slabs both neighbours are the other slab; a slab alone is its own neighbour and its
+  // stream is already in order)
+  if (&up != m) cudaStreamWaitEvent(m->st, up.ready, 0);
+  if (&lo != m && &lo != &up) cudaStreamWaitEvent(m->st, lo.ready, 0);
   m->comm->recv_hi = up.buf[2 * s];      // the slab above's lower face
   m->comm->recv_lo = lo.buf[2 * s + 1];  // the slab below's upper face
   m->passes++;
@@ -138,7 +140,7 @@ int local_allreduce(void* user, double* values, int n) {
   a.n = n;
   a.out = values;
   for (int k = 0; k < g->n; k++) {
-    cudaStreamWaitEvent(m->st, g->members[k].ready, 0);
+    if (k != m->rank) cudaStreamWaitEvent(m->st, g->members[k].ready, 0);
     a.src[k] = g->members[k].stage + s * kStageDoubles;
   }
   qcd::g_kernel_launches += 1;
