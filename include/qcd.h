@@ -415,7 +415,8 @@ qcd_status qcd_slab_cg_solve(qcd_ctx* ctx, double* x, const double* b, int nrhs,
  * sums are ready, the ranks meet once per exchange or sum at a host barrier to publish them, and the
  * halo kernels and the sums (in rank order, the same bits on every rank) wait for them on the reading
  * rank's stream.  qcd_local_group_abort releases every rank waiting at the group's barrier and makes
- * this and every later call of the group fail with QCD_ERR_COMM (for a rank that will not come).
+ * this and every later call of the group fail with QCD_ERR_COMM (for a rank that will not come); a
+ * rank whose callback fails before the barrier breaks the group the same way.
  * qcd_local_group_destroy frees the buffers and the group (after the last call).
  */
 typedef struct qcd_local_group qcd_local_group;

@@ -74,6 +74,13 @@ struct qcd_local_group {
 
 namespace {
 
+// A rank whose call fails before the barrier breaks the group, so that the others fail at once
+// instead of waiting for it until the timeout.
+int fail_group(qcd_local_group* g) {
+  g->broken.store(true, std::memory_order_release);
+  return 1;
+}
+
 // All n slabs meet; false (for every later caller too) if one has not arrived within the timeout or
 // the group was aborted.  Each slab has a host thread of its own, so the waiting threads spin on the
 // generation word (yielding now and then) rather than sleep: a wake-up through the scheduler costs
@@ -106,9 +113,9 @@ bool group_barrier(qcd_local_group* g) {
 int local_exchange(void* user, size_t bytes) {
   Member* m = static_cast<Member*>(user);
   qcd_local_group* g = m->grp;
-  if (bytes > m->cap) return 1;
+  if (bytes > m->cap) return fail_group(g);
   const int s = m->passes & 1;
-  if (cudaEventRecord(m->ready, m->st) != cudaSuccess) return 1;
+  if (cudaEventRecord(m->ready, m->st) != cudaSuccess) return fail_group(g);
   if (!group_barrier(g)) return 1;
   const Member& up = g->members[(m->rank + 1) % g->n];
   const Member& lo = g->members[(m->rank + g->n - 1) % g->n];
@@ -128,12 +135,12 @@ int local_exchange(void* user, size_t bytes) {
 int local_allreduce(void* user, double* values, int n) {
   Member* m = static_cast<Member*>(user);
   qcd_local_group* g = m->grp;
-  if (n < 0 || n > kStageDoubles) return 1;
+  if (n < 0 || n > kStageDoubles) return fail_group(g);
   if (n == 0) return 0;
   const int s = m->sums & 1;
   m->sums++;
   cudaMemcpyAsync(m->stage + s * kStageDoubles, values, sizeof(double) * n, cudaMemcpyDeviceToDevice, m->st);
-  if (cudaEventRecord(m->ready, m->st) != cudaSuccess) return 1;
+  if (cudaEventRecord(m->ready, m->st) != cudaSuccess) return fail_group(g);
   if (!group_barrier(g)) return 1;
   SumArgs a;
   a.count = g->n;
