@@ -337,6 +337,15 @@ qcd_status qcd_selftest_debug_index(qcd_ctx* ctx);
 long long qcd_selftest_fastdiv(void);
 
 /*
+ * Host-only self-test of the order in which the staged FP32 multi-RHS hopping kernel takes its
+ * 32-site blocks (chunks of time slices, plane by plane; the same function, evaluated on the host):
+ * checks that it is a permutation of the blocks for every lattice with even extents X, Y, Z in 2..16
+ * and T in 2..34, and for 32^3 x 64, 32^3 x 60, 48^3 x 96, 16^4 and 8 x 8 x 16 x 16.  Returns the
+ * number of lattices where it is not (0 on success); needs no GPU and no context.
+ */
+long long qcd_selftest_site_order(void);
+
+/*
  * Time decomposition over several GPUs (one process per GPU).  The paper runs its application as MPI
  * processes that each hold part of the lattice and exchange boundary data between kernels (Sec. 4);
  * here the global lattice X x Y x Z x T is cut into slabs of consecutive time slices, one per rank.

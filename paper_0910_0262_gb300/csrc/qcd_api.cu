@@ -1711,6 +1711,41 @@ qcd_status qcd_pbp(qcd_ctx* c, const double* eta_e, const double* eta_o, int nrh
   return solve_status;
 }
 
+long long qcd_selftest_site_order(void) {
+  long long bad = 0;
+  std::vector<char> seen;
+  auto check = [&](int X, int Y, int Z, int T) {
+    Geom g{};
+    g.X = X;
+    g.Y = Y;
+    g.Z = Z;
+    g.T = T;
+    g.XY = X * Y;
+    g.XYZ = X * Y * Z;
+    g.Vh = X * Y * Z * T / 2;
+    const int nb = (g.Vh + 31) / 32;
+    seen.assign(nb, 0);
+    for (int b = 0; b < nb; b++) {
+      const int s = site_block_order(g, b);
+      if (s < 0 || s >= nb || seen[s]) {
+        bad++;
+        return;
+      }
+      seen[s] = 1;
+    }
+  };
+  for (int X = 2; X <= 16; X += 2)
+    for (int Y = 2; Y <= 16; Y += 2)
+      for (int Z = 2; Z <= 16; Z += 2)
+        for (int T = 2; T <= 34; T += 2) check(X, Y, Z, T);
+  check(32, 32, 32, 64);
+  check(32, 32, 32, 60);
+  check(48, 48, 48, 96);
+  check(16, 16, 16, 16);
+  check(8, 8, 16, 16);
+  return bad;
+}
+
 long long qcd_selftest_fastdiv(void) {
   long long bad = 0;
   unsigned long long state = 0x9E3779B97F4A7C15ULL;  // xorshift64 numerators

@@ -988,8 +988,9 @@ __global__ void __launch_bounds__(64, 8) dslash_pair64_kernel(DslashArgs A) {
 // input lines were read from DRAM twice), here 2 TC plane rows apart except across chunk boundaries
 // (8 RHS: 689.9 -> 669.4 us at 32^3 x 64, 648.8 -> 635.5 us at 32^3 x 60).  FP16, whose 8-RHS launch
 // reads every byte once in lexicographic order, keeps that order (622 against 646 us in this one).
-// The identity unless a z plane holds whole blocks and TC > 1 divides T.
-__device__ __forceinline__ int site_block_order(const Geom& g, int b) {
+// The identity unless a z plane holds whole blocks and TC > 1 divides T; a permutation of the blocks
+// either way (qcd_selftest_site_order checks it on the host).
+__host__ __device__ __forceinline__ int site_block_order(const Geom& g, int b) {
   const int plane = g.XY >> 1;  // half sites per z plane
   if (plane & 31) return b;
   int tc = 16;

@@ -88,6 +88,7 @@ _SIGNATURES = {
     "qcd_mhat_static": (ctypes.c_int, [_P, _P, _P, ctypes.c_int]),
     "qcd_selftest_barrier_timeout": (ctypes.c_int, [_P]),
     "qcd_selftest_fastdiv": (ctypes.c_longlong, []),
+    "qcd_selftest_site_order": (ctypes.c_longlong, []),
     "qcd_clover_logdet": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
     "qcd_prepare_source": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
     "qcd_reconstruct_odd": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int]),
@@ -298,6 +299,11 @@ def qcd_selftest_debug_index(ctx):
 def qcd_selftest_fastdiv():
     """Mismatches of the kernels' division by a lattice extent against integer division (host only)."""
     return lib().qcd_selftest_fastdiv()
+
+
+def qcd_selftest_site_order():
+    """Lattices on which the staged FP32 kernel's block order is not a permutation (host only)."""
+    return lib().qcd_selftest_site_order()
 
 
 def qcd_probe_fma_peak(precision=64, stream=None):

@@ -84,3 +84,10 @@ def test_extent_division_matches_integer_division(libqcd):
     """The kernels' multiply-and-shift division by X, Y, Z (host evaluation of the same expression)."""
     libqcd.qcd_selftest_fastdiv.restype = ctypes.c_longlong
     assert libqcd.qcd_selftest_fastdiv() == 0
+
+
+def test_staged_block_order_is_a_permutation(libqcd):
+    """The staged FP32 multi-RHS kernel's order of its 32-site blocks covers every block once (host
+    evaluation of the same function, on every small even lattice and the benchmark lattices)."""
+    libqcd.qcd_selftest_site_order.restype = ctypes.c_longlong
+    assert libqcd.qcd_selftest_site_order() == 0
