@@ -342,7 +342,9 @@ def run_ours(args, world, rank, local):
         "solve": {"mixed_ms": solve_mixed, "fp64_ms": solve64, "speedup_mixed_vs_fp64": None if solve64 is None else solve64 / solve_mixed,
                   "mixed_iters": iters, "fp64_iters": st64[0].iters, "reliable_updates": stats[0].reliable_updates,
                   "true_rel_resid_mixed": resid, "true_rel_resid_fp64": st64[0].true_rel_resid},
-        "dslash": {"fp32_in_solve": d32, "fp64_in_solve": d64},
+        # hopping launches of the solve by precision (FP32 only when its hops run as separate launches
+        # rather than inside the persistent kernel)
+        "dslash": {k: v for k, v in (("fp32_in_solve", d32), ("fp64_in_solve", d64)) if v["launches"]},
         "kernels_per_step": classes,
         "gpu_launches": total_launches,
         "clocks": clocks,
