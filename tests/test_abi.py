@@ -91,3 +91,18 @@ def test_staged_block_order_is_a_permutation(libqcd):
     evaluation of the same function, on every small even lattice and the benchmark lattices)."""
     libqcd.qcd_selftest_site_order.restype = ctypes.c_longlong
     assert libqcd.qcd_selftest_site_order() == 0
+
+
+def test_local_group_host_calls(libqcd):
+    """The in-process slab group's host-only calls: the group size is checked (1 to 16 slabs), and
+    abort and destroy of a group that no slab joined touch no device."""
+    from paper_0910_0262_gb300 import qcd as Q
+    for n in (0, -1, 17):
+        with pytest.raises(Q.QCDError) as e:
+            Q.qcd_local_group_create(n)
+        assert e.value.status == 1  # QCD_ERR_ARG
+    g = Q.qcd_local_group_create(2)
+    Q.qcd_local_group_abort(g)
+    Q.qcd_local_group_destroy(g)
+    assert libqcd.qcd_local_group_abort(None) == 1
+    assert libqcd.qcd_local_group_destroy(None) == 0
